@@ -1,0 +1,314 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: brute force
+over all Paulis, the stabiliser-group sum written term by term, closed forms,
+symmetries of the code, the bit-flip random-bond Ising form (Eq. 6), and
+the multilinearity of Z in the noise rows.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.mps as omps
+import synth
+
+
+def _all_syndromes(d):
+    m = d * d - 1
+    bits = ((np.arange(1 << m)[:, None] >> np.arange(m)[None, :]) & 1).astype(np.uint8)
+    return synth.pack_bits(bits)
+
+
+def _random_noise(n, seed, lo=0.01, hi=0.3):
+    rng = np.random.default_rng(seed)
+    t = rng.uniform(lo, hi, size=(n, 4))
+    t[:, 0] = rng.uniform(0.5, 0.9, size=n)
+    return t / t.sum(axis=1, keepdims=True)
+
+
+# --- brute force: Eq. 3 summed over all 4^n Paulis --------------------------
+
+@pytest.mark.parametrize("noise_kind", ["depolarizing", "random"])
+def test_dense_equals_bruteforce_d3_all_syndromes(noise_kind):
+    d, n = 3, 9
+    noise = synth.depolarizing(n, 0.1) if noise_kind == "depolarizing" else _random_noise(n, 5)
+    Z = oracle.bruteforce_table(d, noise)
+    logP, am = oracle.decode(d, noise, _all_syndromes(d))
+    np.testing.assert_allclose(logP, np.log(Z), rtol=0, atol=1e-12)
+    # the decision is unique unless two cosets tie (exact under symmetric noise);
+    # at a tie the pick must be one of the maxima
+    lz = np.log(Z)
+    top = np.sort(lz, axis=1)
+    clear = top[:, -1] - top[:, -2] > 1e-9
+    np.testing.assert_array_equal(am[clear], np.argmax(Z, axis=1)[clear])
+    assert np.all(lz[np.arange(len(am)), am] >= top[:, -1] - 1e-9)
+
+
+def test_normalisation_sum_over_syndromes_and_classes_d3():
+    d, n = 3, 9
+    noise = _random_noise(n, 11)
+    logP, _ = oracle.decode(d, noise, _all_syndromes(d))
+    assert abs(np.exp(logP).sum() - 1.0) < 1e-12
+    assert abs(oracle.bruteforce_table(d, noise).sum() - 1.0) < 1e-12
+
+
+# --- the stabiliser-group sum of Eq. 7, term by term ------------------------
+
+def test_dense_equals_group_enumeration_d5():
+    d, n = 5, 25
+    noise = _random_noise(n, 3, 0.02, 0.2)
+    E = synth.sample_errors(d, noise, 3, seed=21)
+    reps = oracle.representatives(d, synth.syndromes_of(d, E))
+    dense = oracle.coset_logz(d, noise, reps.reshape(-1, n))
+    for k, rep in enumerate(reps.reshape(-1, n)):
+        g = oracle.group_logz(d, noise, rep)
+        assert abs(g - dense[k]) < 1e-11 * max(1.0, abs(g))
+
+
+# --- closed forms -----------------------------------------------------------
+
+@pytest.mark.parametrize("d", [3, 5, 7])
+def test_fully_depolarized_closed_form(d):
+    """p_I = p_X = p_Y = p_Z = 1/4: every coset holds 2^(n-1) Paulis of
+    weight 4^-n, so ln Z = -(n+1) ln 2 for every syndrome and class."""
+    n = d * d
+    noise = np.full((n, 4), 0.25)
+    E = synth.sample_errors(d, noise, 8, seed=2)
+    logP, _ = oracle.decode(d, noise, synth.syndromes_of(d, E))
+    np.testing.assert_allclose(logP, -(n + 1) * math.log(2.0), rtol=0, atol=1e-12)
+
+
+def test_zero_noise_limit():
+    """p = 0: only the identity has weight; Z_I(0) = 1, all other Z vanish."""
+    d, n = 5, 25
+    noise = synth.depolarizing(n, 0.0)
+    syn = np.zeros((1, synth.syn_words(d)), np.uint64)
+    logP, am = oracle.decode(d, noise, syn)
+    assert logP[0, 0] == 0.0 and np.all(np.isneginf(logP[0, 1:])) and am[0] == 0
+
+
+def test_small_p_limit_minimum_weight_d3():
+    """p -> 0: ln Z_l(s) = ln N_min + w_min ln(p/3) + (n-w_min) ln(1-p) + O(p),
+    with (w_min, N_min) the minimum weight and its multiplicity in the coset,
+    found by enumerating all 4^n Paulis."""
+    d, n = 3, 9
+    codes = ((np.arange(4 ** n)[:, None] >> (2 * np.arange(n))[None, :]) & 3).astype(np.uint8)
+    bits, cls = oracle.syndrome_class(d, codes)
+    sidx = oracle.syndrome_index(bits).astype(np.int64)
+    w = (codes != 0).sum(axis=1)
+    key = sidx * 4 + cls
+    wmin = np.full(4 << (n - 1), 99)
+    np.minimum.at(wmin, key, w)
+    nmin = np.zeros(4 << (n - 1), np.int64)
+    np.add.at(nmin, key, (w == wmin[key]).astype(np.int64))
+    p = 1e-7
+    logP, am = oracle.decode(d, synth.depolarizing(n, p), _all_syndromes(d))
+    expect = np.log(nmin) + wmin * math.log(p / 3) + (n - wmin) * math.log(1 - p)
+    np.testing.assert_allclose(logP.reshape(-1), expect, rtol=0, atol=1e-4)
+    # the decision is the coset of minimum weight whenever that is unique
+    W = wmin.reshape(-1, 4)
+    uniq = (W == W.min(axis=1, keepdims=True)).sum(axis=1) == 1
+    np.testing.assert_array_equal(am[uniq], W.argmin(axis=1)[uniq])
+
+
+def test_low_weight_errors_decode_to_their_class_d5():
+    """Every error of weight <= (d-1)/2 is corrected by MLD at small p."""
+    d, n = 5, 25
+    errs = []
+    for qs in itertools.chain(itertools.combinations(range(n), 1), itertools.combinations(range(n), 2)):
+        for ps in itertools.product((1, 2, 3), repeat=len(qs)):
+            e = np.zeros(n, np.uint8)
+            e[list(qs)] = ps
+            errs.append(e)
+    E = np.array(errs)
+    _, am = oracle.decode(d, synth.depolarizing(n, 1e-3), synth.syndromes_of(d, E))
+    np.testing.assert_array_equal(am, synth.true_class(d, E))
+
+
+# --- destabilisers, representatives and gauge invariance --------------------
+
+@pytest.mark.parametrize("d", [3, 5, 9, 13])
+def test_destabilisers_and_representatives(d):
+    n, m, _ = oracle.code_info(d)
+    T = oracle.destabilisers(d)
+    bits = ((synth.syndromes_of(d, T)[:, :, None] >> np.arange(64, dtype=np.uint64)) & np.uint64(1))
+    bits = bits.reshape(m, -1)[:, :m].astype(np.uint8)
+    np.testing.assert_array_equal(bits, np.eye(m, dtype=np.uint8))
+    assert not synth.true_class(d, T).any()
+    E = synth.sample_errors(d, synth.depolarizing(n, 0.15), 64, seed=d)
+    syn = synth.syndromes_of(d, E)
+    reps = oracle.representatives(d, syn)
+    for l in range(4):
+        np.testing.assert_array_equal(synth.syndromes_of(d, reps[:, l]), syn)
+        assert (synth.true_class(d, reps[:, l]) == l).all()
+
+
+def _stabiliser_product(d, alpha):
+    E = np.zeros(d * d, np.uint8)
+    for a, (t, qs) in zip(alpha, synth.stabilizers(d)):
+        if a:
+            E[qs] ^= 1 if t == 0 else 2
+    return E
+
+
+@pytest.mark.parametrize("d", [5, 7])
+def test_gauge_invariance_and_true_coset(d):
+    """Z depends only on the coset: E and E*S give the same value, and the
+    representative built from (syndrome, class) of E lies in E's coset."""
+    n = d * d
+    noise = _random_noise(n, d, 0.01, 0.15)
+    rng = np.random.default_rng(d)
+    E = synth.sample_errors(d, noise, 6, seed=99)
+    ES = np.array([e ^ _stabiliser_product(d, rng.integers(0, 2, n - 1)) for e in E])
+    z1 = oracle.coset_logz(d, noise, E)
+    z2 = oracle.coset_logz(d, noise, ES)
+    np.testing.assert_allclose(z1, z2, rtol=0, atol=1e-11)
+    reps = oracle.representatives(d, synth.syndromes_of(d, E))
+    cls = synth.true_class(d, E)
+    z3 = oracle.coset_logz(d, noise, reps[np.arange(len(E)), cls])
+    np.testing.assert_allclose(z1, z3, rtol=0, atol=1e-11)
+
+
+# --- symmetries of the patch -------------------------------------------------
+
+def _swap_xz_codes(E):
+    return ((E & 1) << 1) | ((E >> 1) & 1)
+
+
+def _rotate(d, E, noise, quarter):
+    """Map qubit (r,c) to (c, d-1-r) (quarter turn, with X<->Z) or to
+    (d-1-r, d-1-c) (half turn); both map the stabiliser group onto itself."""
+    E2 = np.zeros_like(E)
+    N2 = np.zeros_like(noise)
+    for r in range(d):
+        for c in range(d):
+            q = r * d + c
+            q2 = (c * d + (d - 1 - r)) if quarter else ((d - 1 - r) * d + (d - 1 - c))
+            E2[..., q2] = _swap_xz_codes(E[..., q]) if quarter else E[..., q]
+            N2[q2] = noise[q][[0, 3, 2, 1]] if quarter else noise[q]
+    return E2, N2
+
+
+@pytest.mark.parametrize("quarter", [True, False])
+def test_rotation_symmetry(quarter):
+    d, n = 7, 49
+    noise = _random_noise(n, 17, 0.01, 0.12)
+    E = synth.sample_errors(d, noise, 6, seed=5)
+    E2, N2 = _rotate(d, E, noise, quarter)
+    np.testing.assert_allclose(oracle.coset_logz(d, noise, E), oracle.coset_logz(d, N2, E2),
+                               rtol=0, atol=1e-11)
+
+
+# --- independent X/Z noise and the bit-flip RBIM (Eq. 6) --------------------
+
+def test_independent_xz_noise_factorises():
+    """P(X^u Z^v) = q_x(u) q_z(v) makes Z_l = Z^x_{l_X} Z^z_{l_Z}, hence
+    ln Z_I + ln Z_Y = ln Z_X + ln Z_Z."""
+    d, n = 7, 49
+    rng = np.random.default_rng(4)
+    qx = rng.uniform(0.02, 0.2, n)
+    qz = rng.uniform(0.02, 0.2, n)
+    noise = np.stack([(1 - qx) * (1 - qz), qx * (1 - qz), qx * qz, (1 - qx) * qz], axis=1)
+    E = synth.sample_errors(d, noise, 16, seed=8)
+    lp, _ = oracle.decode(d, noise, synth.syndromes_of(d, E))
+    np.testing.assert_allclose(lp[:, 0] + lp[:, 3], lp[:, 1] + lp[:, 2], rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("d", [3, 5])
+def test_bitflip_random_bond_ising(d):
+    """Bit-flip noise: Z of the coset of E equals (p(1-p))^{n/2} times the RBIM
+    partition function sum_sigma prod_q exp(K eta_q prod_{f ni q} sigma_f) over
+    spins on the X-type plaquettes, K = ln((1-p)/p)/2, eta_q = (-1)^{x_q}
+    (Eq. 6); cosets that need a Z component have Z = 0."""
+    n = d * d
+    p = 0.08
+    noise = np.zeros((n, 4))
+    noise[:, 0], noise[:, 1] = 1 - p, p
+    xplaq = [qs for t, qs in synth.stabilizers(d) if t == 0]
+    E = synth.sample_errors(d, noise, 4, seed=13)
+    K = 0.5 * math.log((1 - p) / p)
+    for e in E:
+        eta = np.where(e & 1, -1.0, 1.0)
+        total = 0.0
+        for spins in itertools.product((1, -1), repeat=len(xplaq)):
+            prod = np.ones(n)
+            for s, qs in zip(spins, xplaq):
+                prod[qs] *= s
+            total += math.exp(K * float((eta * prod).sum()))
+        expect = 0.5 * n * math.log(p * (1 - p)) + math.log(total)
+        got = oracle.coset_logz(d, noise, e[None])[0]
+        assert abs(got - expect) < 1e-10
+        zl = e.copy()
+        zl[:d] ^= 2                      # times Z_L (row 0): needs a Z component
+        assert np.isneginf(oracle.coset_logz(d, noise, zl[None])[0])
+
+
+# --- derivatives --------------------------------------------------------------
+
+@pytest.mark.parametrize("d", [3, 5])
+def test_derivatives_finite_differences_and_euler(d):
+    """dZ/dp_{q,P} against central differences, and the Euler identity
+    sum_P p_{q,P} d ln Z/d p_{q,P} = 1 (Z is linear in each row)."""
+    n = d * d
+    noise = _random_noise(n, 31 + d, 0.02, 0.2)
+    E = synth.sample_errors(d, noise, 2, seed=3)
+    lz, g = oracle.coset_dlogz(d, noise, E)
+    np.testing.assert_allclose((g * noise[None]).sum(axis=2), 1.0, rtol=0, atol=1e-11)
+    h = 1e-6
+    rng = np.random.default_rng(d)
+    for q in rng.choice(n, 4, replace=False):
+        for P in range(4):
+            up = noise.copy(); up[q, P] += h
+            dn = noise.copy(); dn[q, P] -= h
+            fd = (oracle.coset_logz(d, up, E) - oracle.coset_logz(d, dn, E)) / (2 * h)
+            np.testing.assert_allclose(g[:, q, P], fd, rtol=1e-6, atol=1e-8)
+
+
+# --- the FP64 boundary-MPS mode at exact bond dimension ----------------------
+
+@pytest.mark.parametrize("d,chi", [(3, 2), (5, 4), (7, 8), (9, 16)])
+def test_mps_mode_exact_at_full_bond(d, chi):
+    """With chi >= 2^floor(d/2) no singular value is discarded and the
+    boundary-MPS sweep equals the exact contraction."""
+    n = d * d
+    noise = synth.depolarizing(n, 0.15)
+    syn = synth.syndromes_of(d, synth.sample_errors(d, noise, 2, seed=1))
+    ref, _ = oracle.decode(d, noise, syn)
+    np.testing.assert_allclose(omps.decode_mps(d, noise, syn, chi), ref, rtol=0, atol=1e-9)
+
+
+def test_mps_mode_truncation_converges():
+    """Below the exact bond the error shrinks as chi grows (Sec. 3.2.1)."""
+    d, n = 9, 81
+    noise = synth.depolarizing(n, 0.15)
+    syn = synth.syndromes_of(d, synth.sample_errors(d, noise, 2, seed=3))
+    ref, _ = oracle.decode(d, noise, syn)
+    errs = [np.abs(omps.decode_mps(d, noise, syn, chi) - ref).max() for chi in (2, 4, 8, 16)]
+    assert errs[0] > errs[1] > errs[2] > errs[3] and errs[3] < 1e-9
+
+
+# --- stored expected values (written by tests/golden/make_golden.py) ----------
+
+def _golden(name):
+    import os
+    rows = [l.split() for l in open(os.path.join(os.path.dirname(__file__), "golden", name))
+            if not l.startswith("#")]
+    return rows
+
+
+def test_golden_d3_bruteforce_table():
+    rows = _golden("d3_p010_bruteforce.txt")
+    ref = np.array([[float(v) for v in r[1:5]] for r in rows])
+    logP, _ = oracle.decode(3, synth.depolarizing(9, 0.10), _all_syndromes(3))
+    np.testing.assert_allclose(logP, ref, rtol=0, atol=1e-12)
+
+
+def test_golden_d5_group_enumeration():
+    rows = _golden("d5_group_enum.txt")
+    syn = np.array([[int(r[0])] for r in rows], dtype=np.uint64)
+    ref = np.array([[float(v) for v in r[1:5]] for r in rows])
+    logP, _ = oracle.decode(5, synth.depolarizing(25, 0.12), syn)
+    np.testing.assert_allclose(logP, ref, rtol=0, atol=1e-11)
