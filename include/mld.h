@@ -1,0 +1,142 @@
+/*
+ * mld.h - C ABI of the GB300 (sm_103a) tensor-network maximum-likelihood
+ * decoder for the rotated surface code under independent Pauli noise.
+ *
+ * Method (arxiv 2605.17230): for each syndrome s and logical class l the
+ * coset partition function Z_l(s) = sum_{E in C_l(s)} Pr(E) (Eq. 3, Sec. 2.3)
+ * is computed in the generator picture (Eq. 7, Sec. 3.2.1) by a boundary-MPS
+ * sweep over the corner columns of the patch, compressed to bond dimension
+ * chi after every column; the decision is argmax_l Z_l(s) (Eq. 4).
+ *
+ * Conventions (the paper's lattice figure is not available; this is the
+ * layout adopted, exported by mld_code_layout):
+ *  - d odd, 3 <= d <= 25; n = d*d data qubits, qubit (r,c) has index r*d+c.
+ *  - Plaquette (i,j), 0 <= i,j <= d, acts on qubits (i-1,j-1),(i-1,j),(i,j-1),
+ *    (i,j) inside the patch; it is X-type if i+j is even, Z-type if odd.
+ *    Interior plaquettes are all checks; rows 0 and d keep only the X-type
+ *    weight-2 ones, columns 0 and d only the Z-type weight-2 ones: n-1 checks.
+ *  - Stabiliser index = column-major order (j outer, i inner) of the checks.
+ *    Syndrome bit k lives in word k/64, bit k%64 of a uint64 row of
+ *    syn_words = ceil((n-1)/64) words.
+ *  - Logical operators: Z_L = Z on row 0, X_L = X on column 0. The class of
+ *    an error E is l = l_X + 2 l_Z with l_X = <E,Z_L>, l_Z = <E,X_L>, i.e. the
+ *    output order is I, X, Z, Y.
+ *  - Noise (independent Pauli noise, Sec. 3.1.1): float rows
+ *    (p_I, p_X, p_Y, p_Z) per qubit, or one depolarizing strength p per
+ *    syndrome (p_I = 1-p, p_X = p_Y = p_Z = p/3, Sec. 2.2).
+ *
+ * Errors: every call returns an mld_status; nothing is thrown across the
+ * ABI. Device-side failures (a Jacobi sweep that hits its iteration bound,
+ * a non-finite value) are reported through a library-owned status word that
+ * is read when the call synchronises (mld_decode_host, or
+ * mld_decode_status after the caller has synchronised the stream).
+ */
+#ifndef MLD_H
+#define MLD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mld_code mld_code;   /* opaque, owned by the library */
+
+typedef enum {
+    MLD_OK = 0,
+    MLD_ERR_INVALID_ARG = 1,   /* bad d, chi < 1, B < 0, NULL pointer, bad mode */
+    MLD_ERR_UNSUPPORTED = 2,   /* valid request this build cannot run (e.g. too
+                                  much on-chip memory for this d and chi) */
+    MLD_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+    MLD_ERR_NOMEM = 4,         /* device or host allocation failed */
+    MLD_ERR_TIMEOUT = 5,       /* a bounded device loop hit its limit */
+    MLD_ERR_NUMERIC = 6        /* a non-finite value appeared on the device */
+} mld_status;
+
+typedef enum {
+    MLD_FP32 = 0,              /* FP32 storage and arithmetic (FP64 only in the
+                                  Jacobi rotation parameters and the log-norm) */
+    MLD_MIXED_BF16 = 1,        /* MPO.MPS products from BF16 operands, FP32
+                                  accumulate, power-of-two column scaling */
+    MLD_MIXED_TF32 = 2         /* the same with TF32 operands */
+} mld_precision;
+
+typedef enum {
+    MLD_NOISE_TABLE = 0,       /* noise = float[n][4] shared by the batch */
+    MLD_NOISE_DEPOL = 1        /* noise = float[B], depolarizing p per syndrome */
+} mld_noise_mode;
+
+/* Build the rotated distance-d code: check supports, logical operators and a
+ * destabiliser table (for each check k a Pauli T_k that anticommutes with
+ * check k only and commutes with X_L and Z_L), from which the pure error of
+ * a syndrome, f(s) = prod_{s_k=1} T_k, is formed (Sec. 3.2.1, the fixed
+ * representative E_{l,s}). Host-only: device copies are made by the first
+ * decode call. *out is owned by the caller and released with
+ * mld_code_destroy. MLD_ERR_INVALID_ARG unless d is odd and 3 <= d <= 25. */
+mld_status mld_code_create_rotated(int d, mld_code** out);
+
+/* Host-side pure errors: reps[B][4][n] receives the Pauli codes (x + 2z) of
+ * the representatives E_{l,s} = f(s) * X_L^{l_X} * Z_L^{l_Z}, l = I, X, Z, Y,
+ * for B host syndromes (Sec. 3.2.1: the fixed representative whose coset the
+ * generator-picture sum runs over). Needs no GPU. */
+mld_status mld_code_representatives(const mld_code* code, const uint64_t* syndromes, int64_t B,
+                                    uint8_t* reps);
+
+/* Release a code and every device buffer it owns. NULL is allowed. */
+void mld_code_destroy(mld_code* code);
+
+/* n_qubits = d*d, n_stabs = d*d-1, syn_words = ceil(n_stabs/64). Any output
+ * pointer may be NULL. */
+mld_status mld_code_info(const mld_code* code, int* n_qubits, int* n_stabs, int* syn_words);
+
+/* Host arrays: stab_type[n_stabs] (0 = X-type, 1 = Z-type),
+ * stab_qubits[n_stabs][4] (qubit indices, -1 padded), logical_x[n] (1 on the
+ * support of X_L), logical_z[n] (1 on the support of Z_L). Any may be NULL. */
+mld_status mld_code_layout(const mld_code* code, int32_t* stab_type, int32_t* stab_qubits,
+                           uint8_t* logical_x, uint8_t* logical_z);
+
+/* Decode B syndromes on the GPU (Eq. 3, 4 and 7; boundary MPS of Sec. 3.2.1).
+ *   noise      device pointer: float[n][4] (MLD_NOISE_TABLE) or float[B]
+ *              (MLD_NOISE_DEPOL). Rows are (p_I, p_X, p_Y, p_Z).
+ *   syndromes  device pointer, uint64[B][syn_words].
+ *   chi        maximum bond dimension kept after each column (chi >= 1).
+ *              chi >= 2^floor(d/2) discards nothing: the result is then the
+ *              exact ln Z_l(s) up to rounding.
+ *   precision  an mld_precision value.
+ *   logP       device pointer, double[B][4]: ln Z_l(s) for l = I, X, Z, Y
+ *              (the joint log-probability ln Pr(s, l); ln Pr(l|s) is
+ *              logP - logsumexp(logP), Eq. 3). -inf when Z_l(s) = 0.
+ *   argmax     device pointer uint8[B] or NULL: argmax_l Z_l(s), ties and
+ *              all--inf rows go to the lowest class index.
+ *   stream     cudaStream_t (NULL = legacy default stream).
+ * All arrays are caller-owned device memory; the call is asynchronous and
+ * allocates nothing per call after the first call for a given (code, chi)
+ * (which uploads the column plan). Status of the device work: see
+ * mld_decode_status. B = 0 is a no-op. */
+mld_status mld_decode(const mld_code* code, const float* noise, int noise_mode,
+                      const uint64_t* syndromes, int64_t B, int chi, int precision,
+                      double* logP, uint8_t* argmax, void* stream);
+
+/* The same with HOST pointers: copies the inputs to the device, decodes,
+ * copies the results back and synchronises. Device buffers are cached in the
+ * code object and grown on demand. argmax may be NULL. */
+mld_status mld_decode_host(const mld_code* code, const float* noise, int noise_mode,
+                           const uint64_t* syndromes, int64_t B, int chi, int precision,
+                           double* logP, uint8_t* argmax);
+
+/* Read and clear the device status word written by earlier mld_decode calls
+ * on this code (the caller must have synchronised their streams):
+ * MLD_OK, MLD_ERR_TIMEOUT or MLD_ERR_NUMERIC. */
+mld_status mld_decode_status(const mld_code* code);
+
+/* Number of kernel launches one mld_decode call makes (for accounting). */
+int mld_decode_launches(void);
+
+/* Static description of a status code. */
+const char* mld_status_string(mld_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLD_H */

@@ -1,0 +1,196 @@
+"""GB300 (sm_103a) tensor-network maximum-likelihood decoder for the rotated
+surface code: thin Python binding of the C ABI in ``include/mld.h``.
+
+Every step of the decoding path runs in the CUDA library ``libmld.so``; this
+module only marshals arguments (device pointers of torch tensors, the current
+CUDA stream, host numpy buffers). There is no CPU fallback: if the library
+cannot be loaded, the calls raise.
+
+Names follow the C ABI: ``mld_code_create_rotated``, ``mld_decode``,
+``mld_decode_host`` ...; ``Code`` wraps a code handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["MLD_OK", "MLD_FP32", "MLD_MIXED_BF16", "MLD_MIXED_TF32", "MLD_NOISE_TABLE",
+           "MLD_NOISE_DEPOL", "MldError", "Code", "load", "library_path", "mld_code_create_rotated",
+           "mld_decode", "mld_decode_host", "mld_decode_status", "mld_decode_launches",
+           "mld_status_string", "EXPORTED_SYMBOLS"]
+
+MLD_OK = 0
+MLD_FP32, MLD_MIXED_BF16, MLD_MIXED_TF32 = 0, 1, 2
+MLD_NOISE_TABLE, MLD_NOISE_DEPOL = 0, 1
+
+EXPORTED_SYMBOLS = ["mld_code_create_rotated", "mld_code_destroy", "mld_code_info", "mld_code_layout",
+                    "mld_code_representatives",
+                    "mld_decode", "mld_decode_host", "mld_decode_status", "mld_decode_launches",
+                    "mld_status_string"]
+
+_lib = None
+
+
+class MldError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {mld_status_string(status)} (status {status})")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libmld.so (building it with nvcc first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"decoder library not built: {path}")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P, I, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    lib.mld_code_create_rotated.argtypes = [I, ctypes.POINTER(P)]
+    lib.mld_code_create_rotated.restype = I
+    lib.mld_code_destroy.argtypes = [P]
+    lib.mld_code_destroy.restype = None
+    lib.mld_code_info.argtypes = [P, P, P, P]
+    lib.mld_code_info.restype = I
+    lib.mld_code_layout.argtypes = [P, P, P, P, P]
+    lib.mld_code_layout.restype = I
+    lib.mld_code_representatives.argtypes = [P, P, L, P]
+    lib.mld_code_representatives.restype = I
+    lib.mld_decode.argtypes = [P, P, I, P, L, I, I, P, P, P]
+    lib.mld_decode.restype = I
+    lib.mld_decode_host.argtypes = [P, P, I, P, L, I, I, P, P]
+    lib.mld_decode_host.restype = I
+    lib.mld_decode_status.argtypes = [P]
+    lib.mld_decode_status.restype = I
+    lib.mld_decode_launches.argtypes = []
+    lib.mld_decode_launches.restype = I
+    lib.mld_status_string.argtypes = [I]
+    lib.mld_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def mld_status_string(status: int) -> str:
+    return load().mld_status_string(int(status)).decode()
+
+
+def _check(status, what):
+    if status != MLD_OK:
+        raise MldError(status, what)
+
+
+def mld_code_create_rotated(d: int) -> int:
+    h = ctypes.c_void_p()
+    _check(load().mld_code_create_rotated(int(d), ctypes.byref(h)), "mld_code_create_rotated")
+    return h.value
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def mld_decode(code, noise, noise_mode, syndromes, B, chi, precision, logP, argmax=None, stream=None):
+    """C-ABI mld_decode on torch CUDA tensors (asynchronous on ``stream``,
+    default: torch's current stream)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    st = load().mld_decode(ctypes.c_void_p(code), _ptr(noise), int(noise_mode), _ptr(syndromes), int(B),
+                           int(chi), int(precision), _ptr(logP), _ptr(argmax), ctypes.c_void_p(int(stream)))
+    _check(st, "mld_decode")
+
+
+def mld_decode_host(code, noise, noise_mode, syndromes, B, chi, precision, logP, argmax=None):
+    """C-ABI mld_decode_host on contiguous numpy arrays (synchronous)."""
+    f = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a is not None else ctypes.c_void_p(0)
+    st = load().mld_decode_host(ctypes.c_void_p(code), f(noise), int(noise_mode), f(syndromes), int(B),
+                                int(chi), int(precision), f(logP), f(argmax))
+    _check(st, "mld_decode_host")
+
+
+def mld_decode_status(code) -> int:
+    return load().mld_decode_status(ctypes.c_void_p(code))
+
+
+def mld_decode_launches() -> int:
+    return load().mld_decode_launches()
+
+
+class Code:
+    """Rotated distance-d code handle (owns the library object)."""
+
+    def __init__(self, d: int):
+        self.d = int(d)
+        self.handle = mld_code_create_rotated(self.d)
+        n, m, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(load().mld_code_info(ctypes.c_void_p(self.handle), ctypes.byref(n), ctypes.byref(m),
+                                    ctypes.byref(w)), "mld_code_info")
+        self.n, self.m, self.words = n.value, m.value, w.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().mld_code_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def layout(self):
+        t = np.zeros(self.m, np.int32)
+        s = np.zeros((self.m, 4), np.int32)
+        lx = np.zeros(self.n, np.uint8)
+        lz = np.zeros(self.n, np.uint8)
+        f = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(load().mld_code_layout(ctypes.c_void_p(self.handle), f(t), f(s), f(lx), f(lz)), "mld_code_layout")
+        return t, s, lx, lz
+
+    def representatives(self, syndromes):
+        """Pauli codes of E_{l,s} for l = I, X, Z, Y: uint8 [B][4][n] (host)."""
+        syn = np.ascontiguousarray(syndromes, dtype=np.uint64).reshape(-1, self.words)
+        out = np.zeros((syn.shape[0], 4, self.n), np.uint8)
+        f = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(load().mld_code_representatives(ctypes.c_void_p(self.handle), f(syn), syn.shape[0], f(out)),
+               "mld_code_representatives")
+        return out
+
+    def decode(self, noise, syndromes, chi, precision=MLD_FP32, with_argmax=True, stream=None):
+        """Decode torch CUDA tensors. noise: float32 [n][4] table or [B]
+        depolarizing strengths; syndromes: uint64/int64 [B][words].
+        Returns (logP float64 [B][4], argmax uint8 [B] or None)."""
+        import torch
+        B = syndromes.shape[0]
+        mode = MLD_NOISE_TABLE if noise.dim() == 2 else MLD_NOISE_DEPOL
+        dev = syndromes.device
+        logP = torch.empty((B, 4), dtype=torch.float64, device=dev)
+        am = torch.empty((B,), dtype=torch.uint8, device=dev) if with_argmax else None
+        mld_decode(self.handle, noise.contiguous(), mode, syndromes.contiguous(), B, chi, precision, logP, am,
+                   stream)
+        return logP, am
+
+    def decode_host(self, noise, syndromes, chi, precision=MLD_FP32):
+        """Decode numpy host arrays through the host-buffer entry point."""
+        noise = np.ascontiguousarray(noise, dtype=np.float32)
+        syn = np.ascontiguousarray(syndromes, dtype=np.uint64).reshape(-1, self.words)
+        B = syn.shape[0]
+        mode = MLD_NOISE_TABLE if noise.ndim == 2 else MLD_NOISE_DEPOL
+        logP = np.zeros((B, 4), np.float64)
+        am = np.zeros(B, np.uint8)
+        mld_decode_host(self.handle, noise, mode, syn, B, chi, precision, logP, am)
+        return logP, am
+
+    def status(self) -> int:
+        return mld_decode_status(self.handle)

@@ -1,0 +1,800 @@
+// Boundary-MPS coset contraction on sm_103a (FP32 path) and the C-ABI.
+//
+// One warp owns one (syndrome, class) unit and keeps its whole state in
+// shared memory: the per-qubit weights, the boundary MPS, two carry buffers
+// and the Householder store. A unit runs, for every qubit column c
+// (Sec. 3.2.1, boundary MPS of the generator-picture network, Eq. 7):
+//   left sweep   site i = 0..d: contract carry x old site x qubit factor into
+//                one block per beta_i (the MPO.MPS product), rescale by a
+//                power of two, Householder-QR the block if it is tall;
+//   right sweep  site i = d..0: form the bond matrix T = Q [carry; 0] and
+//                factor it: identity site, dense site, or (when chi is below
+//                min(rows, cols)) a one-sided Jacobi SVD that keeps the chi
+//                largest singular values.
+// After the last column the MPS is contracted with all-ones vectors, giving
+// Z_l(s) (Eq. 3) up to the accumulated power of two; ln Z is formed in FP64.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "mld_internal.h"
+
+extern "C" mld_status mld_code_build_host(int d, mld_code** out);
+
+namespace mld {
+
+constexpr int kMaxWarpsPerBlock = 8;
+constexpr int kMaxJacobiSweeps = 40;
+constexpr float kJacobiTol = 1.0e-5f;   // above the ~L*eps noise floor of FP32 dot products
+
+struct DecodeArgs {
+    const SiteStep* steps;
+    const uint64_t* dmask;     // [n][2][words]
+    const float* noise;
+    const uint64_t* syn;
+    double* logP;
+    int* status;
+    int64_t B;
+    int d, n, words, noise_mode;
+    int off_w, off_mps, off_buf0, off_buf1, off_q, off_svd, per_warp;
+    int init_sizes[kMaxD + 1];
+};
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+// sum over aligned groups of G lanes (G a power of two <= 32)
+__device__ __forceinline__ float group_sum(float v, int G) {
+    for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float pow2f(int e) {   // exact 2^e for -126 <= e <= 127
+    return __int_as_float((e + 127) << 23);
+}
+
+// weight of qubit factor at this step: w(a, a', b, b') = p_q[E_q xor X^u Z^v]
+__device__ __forceinline__ float qweight(const float* wq, int parity, int a, int ap, int b, int bp) {
+    int u, v;
+    if (parity == 0) { u = a ^ bp; v = ap ^ b; }
+    else { u = ap ^ b; v = a ^ bp; }
+    return wq[u + 2 * v];
+}
+
+// ---------------------------------------------------------------- left sweep
+// M^{b'}[k][col] = sum_a w(a, a'(col), beta(k), b') sum_r C[k][a*Dl + r] A[r][col]
+// When the incoming carry is an identity (st.cid: first site, or after a tall
+// block kept as a site), row k = (beta, j) selects j = a*Dl + r and the
+// product is elementwise: M^{b'}[k][col] = w(a, a', beta, b') A[r][col].
+__device__ void apply_site(const SiteStep& st, const float* __restrict__ C,
+                           const float* __restrict__ A, float* __restrict__ M,
+                           const float* __restrict__ wts, int lane, bool last) {
+    const int K = st.K, pam = st.pam, pa = st.pa, pb = st.pb, Dl = st.Dl, Dr = st.Dr;
+    const int ncolA = pa * Dr, ncol = st.ncol, kqp = st.kq_prev, par = st.parity;
+    const float* wq = st.qubit >= 0 ? wts + 4 * st.qubit : nullptr;
+    const int ldc = pam * Dl;
+    if (st.cid) {
+        if (last) {
+            for (int k = lane; k < K; k += 32) {
+                const int beta = k / kqp, j = k - beta * kqp, a = j / Dl, r = j - a * Dl;
+                for (int bp = 0; bp < pb; ++bp) {
+                    float s = 0.f;
+                    for (int ap = 0; ap < pa; ++ap)
+                        s = fmaf(wq ? qweight(wq, par, a, ap, beta, bp) : 1.f, A[r * ncolA + ap], s);
+                    M[bp * K + k] = s;
+                }
+            }
+            return;
+        }
+        if ((ncolA & 3) == 0 && (Dr & 3) == 0) {
+            const int q4 = ncolA >> 2;
+            for (int tI = lane; tI < K * q4; tI += 32) {
+                const int k = tI / q4, col = (tI - k * q4) * 4, ap = col / Dr;
+                const int beta = k / kqp, j = k - beta * kqp, a = j / Dl, r = j - a * Dl;
+                const float4 av = *reinterpret_cast<const float4*>(A + r * ncolA + col);
+                for (int bp = 0; bp < pb; ++bp) {
+                    const float w = wq ? qweight(wq, par, a, ap, beta, bp) : 1.f;
+                    *reinterpret_cast<float4*>(M + (bp * K + k) * ncol + col) =
+                        make_float4(w * av.x, w * av.y, w * av.z, w * av.w);
+                }
+            }
+            return;
+        }
+        for (int e = lane; e < K * ncolA; e += 32) {
+            const int k = e / ncolA, col = e - k * ncolA, ap = col / Dr;
+            const int beta = k / kqp, j = k - beta * kqp, a = j / Dl, r = j - a * Dl;
+            const float av = A[r * ncolA + col];
+            for (int bp = 0; bp < pb; ++bp)
+                M[(bp * K + k) * ncol + col] = (wq ? qweight(wq, par, a, ap, beta, bp) : 1.f) * av;
+        }
+        return;
+    }
+    if (last) {
+        // alpha_d has no factor to its right: sum it here (Dr = 1, ncol = 1)
+        for (int k = lane; k < K; k += 32) {
+            const int beta = k / kqp;
+            float t[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+            for (int a = 0; a < pam; ++a)
+                for (int ap = 0; ap < pa; ++ap) {
+                    float s = 0.f;
+                    for (int r = 0; r < Dl; ++r) s = fmaf(C[k * ldc + a * Dl + r], A[r * ncolA + ap], s);
+                    t[a][ap] = s;
+                }
+            for (int bp = 0; bp < pb; ++bp) {
+                float s = 0.f;
+                for (int a = 0; a < pam; ++a)
+                    for (int ap = 0; ap < pa; ++ap)
+                        s = fmaf(wq ? qweight(wq, par, a, ap, beta, bp) : 1.f, t[a][ap], s);
+                M[bp * K + k] = s;
+            }
+        }
+        return;
+    }
+    if ((ncolA & 3) == 0 && (Dr & 3) == 0) {
+        // four consecutive columns share a' (Dr % 4 == 0)
+        const int q4 = ncolA >> 2;
+        for (int tI = lane; tI < K * q4; tI += 32) {
+            const int k = tI / q4, col = (tI - k * q4) * 4, ap = col / Dr;
+            float4 t0 = make_float4(0.f, 0.f, 0.f, 0.f), t1 = t0;
+            const float* c0 = C + k * ldc;
+            const float* c1 = c0 + Dl;
+            for (int r = 0; r < Dl; ++r) {
+                const float4 av = *reinterpret_cast<const float4*>(A + r * ncolA + col);
+                const float x0 = c0[r];
+                t0.x = fmaf(x0, av.x, t0.x); t0.y = fmaf(x0, av.y, t0.y);
+                t0.z = fmaf(x0, av.z, t0.z); t0.w = fmaf(x0, av.w, t0.w);
+                if (pam == 2) {
+                    const float x1 = c1[r];
+                    t1.x = fmaf(x1, av.x, t1.x); t1.y = fmaf(x1, av.y, t1.y);
+                    t1.z = fmaf(x1, av.z, t1.z); t1.w = fmaf(x1, av.w, t1.w);
+                }
+            }
+            const int beta = k / kqp;
+            for (int bp = 0; bp < pb; ++bp) {
+                const float w0 = wq ? qweight(wq, par, 0, ap, beta, bp) : 1.f;
+                const float w1 = (wq && pam == 2) ? qweight(wq, par, 1, ap, beta, bp) : 0.f;
+                float4 o;
+                o.x = fmaf(w0, t0.x, w1 * t1.x); o.y = fmaf(w0, t0.y, w1 * t1.y);
+                o.z = fmaf(w0, t0.z, w1 * t1.z); o.w = fmaf(w0, t0.w, w1 * t1.w);
+                *reinterpret_cast<float4*>(M + (bp * K + k) * ncol + col) = o;
+            }
+        }
+        return;
+    }
+    for (int e = lane; e < K * ncolA; e += 32) {
+        const int k = e / ncolA, col = e - k * ncolA, ap = col / Dr;
+        float t0 = 0.f, t1 = 0.f;
+        const float* c0 = C + k * ldc;
+        for (int r = 0; r < Dl; ++r) {
+            const float av = A[r * ncolA + col];
+            t0 = fmaf(c0[r], av, t0);
+            if (pam == 2) t1 = fmaf(c0[Dl + r], av, t1);
+        }
+        const int beta = k / kqp;
+        for (int bp = 0; bp < pb; ++bp) {
+            const float w0 = wq ? qweight(wq, par, 0, ap, beta, bp) : 1.f;
+            const float w1 = (wq && pam == 2) ? qweight(wq, par, 1, ap, beta, bp) : 0.f;
+            M[(bp * K + k) * ncol + col] = fmaf(w0, t0, w1 * t1);
+        }
+    }
+}
+
+// Rescale M (len floats) by 2^-e with e the exponent of max|M|; returns e.
+// Sets *zero when M vanishes, *bad when it is not finite.
+__device__ int renormalise(float* M, int len, int lane, bool* zero, bool* bad) {
+    float mx = 0.f;
+    for (int e = lane; e < len; e += 32) mx = fmaxf(mx, fabsf(M[e]));
+    mx = warp_max(mx);
+    if (!(mx < INFINITY)) { *bad = true; return 0; }    // inf or NaN
+    if (mx == 0.f) { *zero = true; return 0; }
+    int ex;
+    frexpf(mx, &ex);
+    if (ex > 126 || ex < -125) { *bad = true; return 0; }
+    const float s = pow2f(-ex);
+    __syncwarp();
+    for (int e = lane; e < len; e += 32) M[e] *= s;
+    return ex;
+}
+
+// Householder QR of the K x n block (row-major, ld = n), K > n, in place:
+// R on and above the diagonal, reflector tails below, tau[j] beside. Run by
+// a group of G lanes (g = lane index in the group). LAPACK sign convention.
+__device__ void qr_block(float* M, float* tau, int K, int n, int g, int G) {
+    for (int j = 0; j < n; ++j) {
+        float ss = 0.f;
+        for (int r = j + 1 + g; r < K; r += G) { const float x = M[r * n + j]; ss = fmaf(x, x, ss); }
+        ss = group_sum(ss, G);
+        const float x0 = M[j * n + j];
+        float tj = 0.f, beta = x0, scal = 0.f;
+        if (ss > 0.f) {
+            const float nrm = sqrtf(fmaf(x0, x0, ss));
+            beta = -copysignf(nrm, x0);
+            tj = (beta - x0) / beta;
+            scal = 1.f / (x0 - beta);
+        }
+        __syncwarp();
+        if (tj != 0.f)
+            for (int r = j + 1 + g; r < K; r += G) M[r * n + j] *= scal;
+        if (g == 0) { M[j * n + j] = beta; tau[j] = tj; }
+        __syncwarp();
+        if (tj != 0.f) {
+            for (int cc = j + 1 + g; cc < n; cc += G) {
+                float w = M[j * n + cc];
+                for (int r = j + 1; r < K; ++r) w = fmaf(M[r * n + j], M[r * n + cc], w);
+                w *= tj;
+                M[j * n + cc] -= w;
+                for (int r = j + 1; r < K; ++r) M[r * n + cc] = fmaf(-M[r * n + j], w, M[r * n + cc]);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Y (K x S, leading dim ldy) <- Q [Y0; 0] with Q = H_0 ... H_{n-1} from qr_block.
+// The caller has written Y0 into rows 0..n-1 and zeros below. Lanes of a
+// group of G split the columns.
+__device__ void apply_q(const float* Mq, const float* tau, int K, int n, float* Y, int ldy, int S,
+                        int g, int G) {
+    for (int j = n - 1; j >= 0; --j) {
+        const float tj = tau[j];
+        if (tj != 0.f) {
+            for (int s = g; s < S; s += G) {
+                float w = Y[j * ldy + s];
+                for (int r = j + 1; r < K; ++r) w = fmaf(Mq[r * n + j], Y[r * ldy + s], w);
+                w *= tj;
+                Y[j * ldy + s] -= w;
+                for (int r = j + 1; r < K; ++r) Y[r * ldy + s] = fmaf(-Mq[r * n + j], w, Y[r * ldy + s]);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// One-sided Jacobi on the nv columns (length L, ld = ldx) of X, accumulating
+// the rotations into acc (nv x nv, starts at I). Rotation parameters in
+// FP64 from FP32 dot products; cyclic round-robin order; bounded sweeps.
+// A pair is rotated only if both columns lie above the FP32 noise floor of
+// the block (squared norm > 1e-12 of the squared Frobenius norm): below it
+// a column is rounding noise and rotating such columns does not settle.
+// Returns false if the sweep bound was hit.
+__device__ bool jacobi(float* X, int L, int ldx, int nv, float* acc, int lane) {
+    float fro2 = 0.f;
+    for (int e = lane; e < L * nv; e += 32) {
+        const float x = X[(e / nv) * ldx + (e % nv)];
+        fro2 = fmaf(x, x, fro2);
+    }
+    const float floor2 = 1e-12f * warp_sum(fro2);
+    for (int e = lane; e < nv * nv; e += 32) acc[e] = (e / nv == e % nv) ? 1.f : 0.f;
+    __syncwarp();
+    const int nvp = nv + (nv & 1);
+    const int npairs = nvp / 2;
+    int G = 32;
+    while (G > 1 && npairs * G > 32) G >>= 1;
+    const int groups = 32 / G;
+    const int grp = lane / G, g = lane % G;
+    for (int sweep = 0; sweep < kMaxJacobiSweeps; ++sweep) {
+        int rotated = 0;
+        for (int round = 0; round < nvp - 1; ++round) {
+            for (int base = 0; base < npairs; base += groups) {
+                const int k = base + grp;
+                int p = -1, q = -1;
+                if (k < npairs) {
+                    if (k == 0) { p = round; q = nvp - 1; }
+                    else { p = (round + k) % (nvp - 1); q = (round - k + (nvp - 1)) % (nvp - 1); }
+                    if (p >= nv || q >= nv) p = q = -1;
+                }
+                float al = 0.f, be = 0.f, ga = 0.f;
+                if (p >= 0)
+                    for (int r = g; r < L; r += G) {
+                        const float xp = X[r * ldx + p], xq = X[r * ldx + q];
+                        al = fmaf(xp, xp, al); be = fmaf(xq, xq, be); ga = fmaf(xp, xq, ga);
+                    }
+                al = group_sum(al, G); be = group_sum(be, G); ga = group_sum(ga, G);
+                if (p >= 0 && ga != 0.f && fminf(al, be) > floor2 &&
+                    fabsf(ga) > kJacobiTol * sqrtf(al) * sqrtf(be)) {
+                    const double zeta = ((double)be - (double)al) / (2.0 * (double)ga);
+                    const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                    const double cd = 1.0 / sqrt(1.0 + t * t);
+                    const float cs = (float)cd, sn = (float)(cd * t);
+                    for (int r = g; r < L; r += G) {
+                        const float xp = X[r * ldx + p], xq = X[r * ldx + q];
+                        X[r * ldx + p] = cs * xp - sn * xq;
+                        X[r * ldx + q] = sn * xp + cs * xq;
+                    }
+                    for (int r = g; r < nv; r += G) {
+                        const float xp = acc[r * nv + p], xq = acc[r * nv + q];
+                        acc[r * nv + p] = cs * xp - sn * xq;
+                        acc[r * nv + q] = sn * xp + cs * xq;
+                    }
+                    rotated = 1;
+                }
+                __syncwarp();
+            }
+        }
+        if (!__any_sync(0xffffffffu, rotated)) return true;
+    }
+    return false;
+}
+
+// ------------------------------------------------------------------ kernel
+__global__ void __launch_bounds__(32 * kMaxWarpsPerBlock)
+decode_fp32_kernel(DecodeArgs a) {
+    extern __shared__ float4 smem4[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t unit = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (unit >= 4 * a.B) return;
+    const int64_t b = unit >> 2;
+    const int cls = (int)(unit & 3);
+    const int d = a.d, n = a.n;
+    float* ws = reinterpret_cast<float*>(smem4) + (size_t)warp * a.per_warp;
+    float* wts = ws + a.off_w;
+    float* mps = ws + a.off_mps;
+    float* qst = ws + a.off_q;
+    float* svd = ws + a.off_svd;
+    float* bufA = ws + a.off_buf0;
+    float* bufB = ws + a.off_buf1;
+
+    // pure error f(s) = prod_{s_k=1} T_k (per-qubit parity of s & mask),
+    // representative E_{l,s} = f * X_L^{l_X} * Z_L^{l_Z}, factor weights
+    uint64_t sw[kMaxSynWords];
+    for (int w = 0; w < a.words; ++w) sw[w] = a.syn[b * a.words + w];
+    for (int q = lane; q < n; q += 32) {
+        int x = 0, z = 0;
+        const uint64_t* mk = a.dmask + (size_t)q * 2 * a.words;
+        for (int w = 0; w < a.words; ++w) {
+            x ^= __popcll(sw[w] & mk[w]) & 1;
+            z ^= __popcll(sw[w] & mk[a.words + w]) & 1;
+        }
+        const int r = q / d, c = q - r * d;
+        if ((cls & 1) && c == 0) x ^= 1;
+        if ((cls & 2) && r == 0) z ^= 1;
+        float row[4];
+        if (a.noise_mode == MLD_NOISE_TABLE) {
+            const float4 v = *reinterpret_cast<const float4*>(a.noise + 4 * (size_t)q);
+            row[0] = v.x; row[1] = v.y; row[2] = v.z; row[3] = v.w;
+        } else {
+            const float p = a.noise[b];
+            row[0] = 1.f - p; row[1] = row[2] = row[3] = p * (1.f / 3.f);
+        }
+        for (int uv = 0; uv < 4; ++uv) {
+            const int xx = x ^ (uv & 1), zz = z ^ (uv >> 1);
+            const int pidx = (!xx && !zz) ? 0 : (xx && !zz) ? 1 : (xx && zz) ? 2 : 3;
+            wts[4 * q + uv] = row[pidx];
+        }
+    }
+    // initial boundary MPS: all-ones product state over corner column 0
+    {
+        int o = 0;
+        for (int i = 0; i <= d; ++i) {
+            const int sz = a.init_sizes[i];
+            if (lane < sz) mps[o + lane] = 1.f;
+            o += (sz + 3) & ~3;
+        }
+    }
+    __syncwarp();
+
+    int e2 = 0;
+    bool zero = false, bad = false, timeout = false;
+    for (int c = 0; c < d && !zero && !bad; ++c) {
+        const SiteStep* S = a.steps + (size_t)c * (d + 1);
+        float* cin = bufA;
+        float* cout = bufB;
+        // ---- left sweep
+        for (int i = 0; i <= d; ++i) {
+            const SiteStep st = S[i];
+            const int K = st.K, ncol = st.ncol, pb = st.pb;
+            float* M = st.tall ? qst + st.offQ : cout;
+            apply_site(st, cin, mps + st.offA, M, wts, lane, i == d);
+            __syncwarp();
+            e2 += renormalise(M, pb * K * ncol, lane, &zero, &bad);
+            __syncwarp();
+            if (zero || bad) break;
+            if (st.tall && st.canon) {
+                float* tau = qst + st.offQ + pb * K * ncol;
+                if (pb == 2) {
+                    const int hb = lane >> 4;
+                    qr_block(M + hb * K * ncol, tau + hb * ncol, K, ncol, lane & 15, 16);
+                } else {
+                    qr_block(M, tau, K, ncol, lane, 32);
+                }
+                // R blocks -> carry rows b*kq .. (kq = ncol)
+                for (int e = lane; e < pb * ncol * ncol; e += 32) {
+                    const int bb = e / (ncol * ncol), rem = e - bb * ncol * ncol;
+                    const int j = rem / ncol, cc = rem - j * ncol;
+                    cout[e] = cc >= j ? M[bb * K * ncol + j * ncol + cc] : 0.f;
+                }
+                __syncwarp();
+            }
+            float* t = cin; cin = cout; cout = t;
+        }
+        if (zero || bad) break;
+        // ---- right sweep; carry g (rows x S), T into t. A tall last block
+        // kept as the site leaves an identity carry (pb x 1 of ones).
+        float* g = cin;
+        float* t = cout;
+        if (S[d].tall && !S[d].canon) {
+            if (lane < S[d].pb) g[lane] = 1.f;
+            __syncwarp();
+        }
+        for (int i = d; i >= 0; --i) {
+            const SiteStep st = S[i];
+            const int rows = st.K, Sr = st.S, pb = st.pb, cols = pb * Sr, kq = st.kq;
+            // T^b = Q^b [G^b; 0] (canonical column), M^b G^b (tall block kept
+            // as the site), or G^b (wide block, Q = I)
+            if (st.tall && !st.canon) {
+                const float* Mb = qst + st.offQ;
+                const int nc = st.ncol;
+                for (int e = lane; e < rows * cols; e += 32) {
+                    const int r = e / cols, cc = e - r * cols, bb = cc / Sr, s = cc - bb * Sr;
+                    const float* mrow = Mb + (bb * rows + r) * nc;
+                    const float* gcol = g + (bb * kq) * Sr + s;
+                    float acc = 0.f;
+                    for (int j = 0; j < nc; ++j) acc = fmaf(mrow[j], gcol[j * Sr], acc);
+                    t[e] = acc;
+                }
+                __syncwarp();
+            } else if (st.tall) {
+                for (int e = lane; e < rows * cols; e += 32) {
+                    const int r = e / cols, cc = e - r * cols, bb = cc / Sr, s = cc - bb * Sr;
+                    t[e] = r < kq ? g[(bb * kq + r) * Sr + s] : 0.f;
+                }
+                __syncwarp();
+                const float* Mq = qst + st.offQ;
+                const float* tau = Mq + pb * rows * st.ncol;
+                if (pb == 2) {
+                    const int hb = lane >> 4;
+                    apply_q(Mq + hb * rows * st.ncol, tau + hb * st.ncol, rows, st.ncol,
+                            t + hb * Sr, cols, Sr, lane & 15, 16);
+                } else {
+                    apply_q(Mq, tau, rows, st.ncol, t, cols, Sr, lane, 32);
+                }
+            } else {
+                for (int e = lane; e < rows * cols; e += 32) {
+                    const int r = e / cols, cc = e - r * cols, bb = cc / Sr, s = cc - bb * Sr;
+                    t[e] = g[(bb * rows + r) * Sr + s];
+                }
+                __syncwarp();
+            }
+            float* site = mps + st.offN;
+            const int Sl = st.Sl;
+            if (st.rmode == R_IDENT) {
+                for (int e = lane; e < cols * cols; e += 32) site[e] = (e / cols == e % cols) ? 1.f : 0.f;
+                float* tmp = g; g = t; t = tmp;        // carry = T (rows x cols)
+            } else if (st.rmode == R_DENSE) {
+                for (int e = lane; e < rows * cols; e += 32) site[e] = t[e];
+                for (int e = lane; e < rows * rows; e += 32) g[e] = (e / rows == e % rows) ? 1.f : 0.f;
+            } else {
+                // truncated SVD of T keeping Sl singular values
+                const int nv = rows < cols ? rows : cols;
+                float* acc = svd;
+                float* sig = svd + nv * nv;
+                int* perm = reinterpret_cast<int*>(sig + nv);
+                const bool tallT = rows >= cols;
+                float* X;
+                int L;
+                if (tallT) { X = t; L = rows; }
+                else {
+                    X = g; L = cols;                   // X = T^T (cols x rows)
+                    for (int e = lane; e < rows * cols; e += 32) {
+                        const int r = e / cols, cc = e - r * cols;
+                        X[cc * rows + r] = t[e];
+                    }
+                }
+                __syncwarp();
+                if (!jacobi(X, L, nv, nv, acc, lane)) timeout = true;
+                for (int k = lane; k < nv; k += 32) {
+                    float s2 = 0.f;
+                    for (int r = 0; r < L; ++r) s2 = fmaf(X[r * nv + k], X[r * nv + k], s2);
+                    sig[k] = sqrtf(s2);
+                }
+                __syncwarp();
+                for (int k = lane; k < nv; k += 32) {
+                    int rank = 0;
+                    const float sk = sig[k];
+                    for (int j = 0; j < nv; ++j) rank += (sig[j] > sk) || (sig[j] == sk && j < k);
+                    if (rank < Sl) perm[rank] = k;
+                }
+                __syncwarp();
+                if (tallT) {
+                    // T = X V^T: site = V[:, top]^T (Sl x cols), carry = X[:, top]
+                    for (int e = lane; e < Sl * cols; e += 32) {
+                        const int s = e / cols, cc = e - s * cols;
+                        site[e] = acc[cc * nv + perm[s]];
+                    }
+                    for (int e = lane; e < rows * Sl; e += 32) {
+                        const int r = e / Sl, s = e - r * Sl;
+                        g[e] = X[r * nv + perm[s]];
+                    }
+                } else {
+                    // T = U X^T: site = X[:, top]^T / sigma, carry = U[:, top] sigma
+                    for (int e = lane; e < Sl * cols; e += 32) {
+                        const int s = e / cols, cc = e - s * cols;
+                        const float sg = sig[perm[s]];
+                        site[e] = sg > 0.f ? X[cc * nv + perm[s]] / sg : 0.f;
+                    }
+                    for (int e = lane; e < rows * Sl; e += 32) {
+                        const int r = e / Sl, s = e - r * Sl;
+                        t[e] = acc[r * nv + perm[s]] * sig[perm[s]];
+                    }
+                    float* tmp = g; g = t; t = tmp;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    double logz;
+    if (zero) {
+        logz = -INFINITY;
+    } else {
+        // contract the final MPS with all-ones vectors
+        const SiteStep* S = a.steps + (size_t)(d - 1) * (d + 1);
+        float* v = bufA;
+        float* vn = bufB;
+        if (lane == 0) v[0] = 1.f;
+        __syncwarp();
+        for (int i = 0; i <= d; ++i) {
+            const SiteStep st = S[i];
+            const float* site = mps + st.offN;
+            for (int s = lane; s < st.S; s += 32) {
+                float acc = 0.f;
+                for (int sl = 0; sl < st.Sl; ++sl)
+                    for (int bb = 0; bb < st.pb; ++bb) acc = fmaf(v[sl], site[(sl * st.pb + bb) * st.S + s], acc);
+                vn[s] = acc;
+            }
+            __syncwarp();
+            float* tmp = v; v = vn; vn = tmp;
+        }
+        const float z = v[0];
+        logz = z > 0.f ? log((double)z) + (double)e2 * 0.69314718055994530942 : -INFINITY;
+        if (!(z == z)) bad = true;
+    }
+    if (lane == 0) {
+        a.logP[b * 4 + cls] = logz;
+        if (bad) atomicOr(a.status, 1 << MLD_ERR_NUMERIC);
+        if (timeout) atomicOr(a.status, 1 << MLD_ERR_TIMEOUT);
+    }
+}
+
+__global__ void argmax_kernel(const double* __restrict__ logP, uint8_t* __restrict__ am, int64_t B) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const double* l = logP + 4 * b;
+    int best = 0;
+    for (int k = 1; k < 4; ++k)
+        if (l[k] > l[best]) best = k;
+    am[b] = (uint8_t)best;
+}
+
+}  // namespace mld
+
+// =================================================================== C-ABI
+
+namespace {
+
+std::mutex g_plan_mutex;
+
+// Device copies of the code tables, made on first use (the host-side
+// construction needs no GPU).
+mld_status ensure_device(mld_code* C) {
+    if (C->d_dmask) return MLD_OK;
+    const size_t mb = C->dmask.size() * sizeof(uint64_t);
+    uint64_t* dm = nullptr;
+    int* ds = nullptr;
+    if (cudaMalloc(&dm, mb) != cudaSuccess) return MLD_ERR_NOMEM;
+    if (cudaMalloc(&ds, sizeof(int)) != cudaSuccess) { cudaFree(dm); return MLD_ERR_NOMEM; }
+    if (cudaMemcpy(dm, C->dmask.data(), mb, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(ds, 0, sizeof(int)) != cudaSuccess) {
+        cudaFree(dm);
+        cudaFree(ds);
+        return MLD_ERR_CUDA;
+    }
+    C->d_status = ds;
+    C->d_dmask = dm;
+    return MLD_OK;
+}
+
+const mld_code::PlanDev* get_plan(mld_code* C, int chi, mld_status* st) {
+    std::lock_guard<std::mutex> lock(g_plan_mutex);
+    if ((*st = ensure_device(C)) != MLD_OK) return nullptr;
+    for (auto& p : C->plans)
+        if (p.chi == chi) return &p;
+    mld_code::PlanDev pd;
+    pd.chi = chi;
+    pd.plan = mld::make_plan(C->d, chi);
+    pd.d_steps = nullptr;
+    const size_t bytes = pd.plan.steps.size() * sizeof(mld::SiteStep);
+    if (cudaMalloc(&pd.d_steps, bytes) != cudaSuccess) { *st = MLD_ERR_NOMEM; return nullptr; }
+    if (cudaMemcpy(pd.d_steps, pd.plan.steps.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(pd.d_steps);
+        *st = MLD_ERR_CUDA;
+        return nullptr;
+    }
+    C->plans.push_back(pd);
+    return &C->plans.back();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mld_status_string(mld_status s) {
+    switch (s) {
+        case MLD_OK: return "ok";
+        case MLD_ERR_INVALID_ARG: return "invalid argument";
+        case MLD_ERR_UNSUPPORTED: return "unsupported configuration";
+        case MLD_ERR_CUDA: return "CUDA runtime error";
+        case MLD_ERR_NOMEM: return "out of memory";
+        case MLD_ERR_TIMEOUT: return "bounded device loop hit its limit";
+        case MLD_ERR_NUMERIC: return "non-finite value on the device";
+    }
+    return "unknown status";
+}
+
+mld_status mld_code_create_rotated(int d, mld_code** out) {
+    return mld_code_build_host(d, out);
+}
+
+void mld_code_destroy(mld_code* C) {
+    if (!C) return;
+    if (C->d_dmask) {
+        for (auto& p : C->plans) cudaFree(p.d_steps);
+        cudaFree(C->d_dmask);
+        cudaFree(C->d_status);
+        cudaFree(C->h_stage_dev);
+    }
+    delete C;
+}
+
+mld_status mld_code_info(const mld_code* C, int* n, int* m, int* w) {
+    if (!C) return MLD_ERR_INVALID_ARG;
+    if (n) *n = C->n;
+    if (m) *m = C->m;
+    if (w) *w = C->words;
+    return MLD_OK;
+}
+
+mld_status mld_code_layout(const mld_code* C, int32_t* type, int32_t* sup, uint8_t* lx, uint8_t* lz) {
+    if (!C) return MLD_ERR_INVALID_ARG;
+    for (int k = 0; k < C->m; ++k) {
+        if (type) type[k] = C->stab_type[k];
+        if (sup)
+            for (int u = 0; u < 4; ++u) sup[4 * k + u] = C->stab_qubits[4 * k + u];
+    }
+    for (int q = 0; q < C->n; ++q) {
+        if (lx) lx[q] = C->lx[q];
+        if (lz) lz[q] = C->lz[q];
+    }
+    return MLD_OK;
+}
+
+int mld_decode_launches(void) { return 2; }
+
+mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, const uint64_t* syn,
+                      int64_t B, int chi, int precision, double* logP, uint8_t* argmax, void* stream) {
+    mld_code* C = const_cast<mld_code*>(Cc);
+    if (!C || B < 0 || chi < 1) return MLD_ERR_INVALID_ARG;
+    if (noise_mode != MLD_NOISE_TABLE && noise_mode != MLD_NOISE_DEPOL) return MLD_ERR_INVALID_ARG;
+    if (precision != MLD_FP32 && precision != MLD_MIXED_BF16 && precision != MLD_MIXED_TF32)
+        return MLD_ERR_INVALID_ARG;
+    if (precision != MLD_FP32) return MLD_ERR_UNSUPPORTED;
+    if (B == 0) return MLD_OK;
+    if (!noise || !syn || !logP) return MLD_ERR_INVALID_ARG;
+    if (noise_mode == MLD_NOISE_TABLE && (reinterpret_cast<uintptr_t>(noise) & 15)) return MLD_ERR_INVALID_ARG;
+    mld_status st = MLD_OK;
+    const mld_code::PlanDev* pd = get_plan(C, chi, &st);
+    if (!pd) return st;
+    const mld::Plan& P = pd->plan;
+    mld::DecodeArgs a;
+    a.steps = pd->d_steps;
+    a.dmask = C->d_dmask;
+    a.noise = noise;
+    a.syn = syn;
+    a.logP = logP;
+    a.status = C->d_status;
+    a.B = B;
+    a.d = C->d;
+    a.n = C->n;
+    a.words = C->words;
+    a.noise_mode = noise_mode;
+    a.off_w = P.off_w;
+    a.off_mps = P.off_mps;
+    a.off_buf0 = P.off_buf0;
+    a.off_buf1 = P.off_buf1;
+    a.off_q = P.off_q;
+    a.off_svd = P.off_svd;
+    a.per_warp = P.floats_per_warp;
+    for (int i = 0; i <= mld::kMaxD; ++i) a.init_sizes[i] = i <= C->d ? P.init_sizes[i] : 0;
+    int dev = 0, max_optin = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
+        return MLD_ERR_CUDA;
+    const size_t pw = (size_t)P.floats_per_warp * sizeof(float);
+    if (pw > (size_t)max_optin) return MLD_ERR_UNSUPPORTED;
+    // warps per CTA: the most resident warps per SM (32 CTAs and 64 warps
+    // per SM at most, 1 KB of shared memory reserved per CTA), fewest warps
+    // per CTA on ties
+    int W = 1, best = 0;
+    for (int w = 1; w <= mld::kMaxWarpsPerBlock; ++w) {
+        if (pw * w > (size_t)max_optin) break;
+        int ctas = (int)((size_t)per_sm / (pw * w + 1024));
+        ctas = ctas < 32 ? ctas : 32;
+        int warps = ctas * w < 64 ? ctas * w : 64;
+        if (warps > best) { best = warps; W = w; }
+    }
+    const size_t smem = pw * W;
+    if (cudaFuncSetAttribute(mld::decode_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return MLD_ERR_CUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t units = 4 * B;
+    const int64_t blocks = (units + W - 1) / W;
+    if (blocks > 0x7fffffff) return MLD_ERR_UNSUPPORTED;
+    mld::decode_fp32_kernel<<<(unsigned)blocks, 32 * W, smem, s>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return MLD_ERR_CUDA;
+    if (argmax) {
+        mld::argmax_kernel<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(logP, argmax, B);
+        if (cudaGetLastError() != cudaSuccess) return MLD_ERR_CUDA;
+    }
+    return MLD_OK;
+}
+
+mld_status mld_decode_status(const mld_code* C) {
+    if (!C) return MLD_ERR_INVALID_ARG;
+    if (!C->d_status) return MLD_OK;
+    int h = 0;
+    if (cudaMemcpy(&h, C->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MLD_ERR_CUDA;
+    if (cudaMemset(C->d_status, 0, sizeof(int)) != cudaSuccess) return MLD_ERR_CUDA;
+    if (h & (1 << MLD_ERR_NUMERIC)) return MLD_ERR_NUMERIC;
+    if (h & (1 << MLD_ERR_TIMEOUT)) return MLD_ERR_TIMEOUT;
+    return MLD_OK;
+}
+
+mld_status mld_decode_host(const mld_code* Cc, const float* noise, int noise_mode, const uint64_t* syn,
+                           int64_t B, int chi, int precision, double* logP, uint8_t* argmax) {
+    mld_code* C = const_cast<mld_code*>(Cc);
+    if (!C || B < 0) return MLD_ERR_INVALID_ARG;
+    if (B == 0) return MLD_OK;
+    if (!noise || !syn || !logP) return MLD_ERR_INVALID_ARG;
+    const size_t nb = noise_mode == MLD_NOISE_TABLE ? (size_t)C->n * 4 * sizeof(float) : (size_t)B * sizeof(float);
+    const size_t sb = (size_t)B * C->words * sizeof(uint64_t);
+    const size_t lb = (size_t)B * 4 * sizeof(double);
+    const size_t ab = (size_t)B;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t need = al(nb) + al(sb) + al(lb) + al(ab);
+    if (need > C->h_stage_bytes) {
+        cudaFree(C->h_stage_dev);
+        C->h_stage_dev = nullptr;
+        C->h_stage_bytes = 0;
+        if (cudaMalloc(&C->h_stage_dev, need) != cudaSuccess) return MLD_ERR_NOMEM;
+        C->h_stage_bytes = need;
+    }
+    char* base = static_cast<char*>(C->h_stage_dev);
+    float* dn = reinterpret_cast<float*>(base);
+    uint64_t* ds = reinterpret_cast<uint64_t*>(base + al(nb));
+    double* dl = reinterpret_cast<double*>(base + al(nb) + al(sb));
+    uint8_t* da = reinterpret_cast<uint8_t*>(base + al(nb) + al(sb) + al(lb));
+    cudaStream_t s = 0;
+    if (cudaMemcpyAsync(dn, noise, nb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(ds, syn, sb, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return MLD_ERR_CUDA;
+    mld_status st = mld_decode(C, dn, noise_mode, ds, B, chi, precision, dl, argmax ? da : nullptr, s);
+    if (st != MLD_OK) return st;
+    if (cudaMemcpyAsync(logP, dl, lb, cudaMemcpyDeviceToHost, s) != cudaSuccess) return MLD_ERR_CUDA;
+    if (argmax && cudaMemcpyAsync(argmax, da, ab, cudaMemcpyDeviceToHost, s) != cudaSuccess) return MLD_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MLD_ERR_CUDA;
+    return mld_decode_status(C);
+}
+
+}  // extern "C"

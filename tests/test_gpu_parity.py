@@ -1,0 +1,211 @@
+"""Parity of the CUDA decoder (through the C ABI) with the FP64 oracle.
+
+Tolerances: |ln Z_gpu - ln Z_oracle| <= 1e-5 for the FP32 path at exact bond
+dimension (chi >= 2^floor(d/2)); argmax decisions must agree except where the
+oracle's two best cosets are within 1e-4 in log (a tie at FP32 resolution).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.mps as omps
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+TIE = 1e-4
+
+
+@pytest.fixture(scope="module")
+def mld():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_17230_gb300 as m
+    m.load()
+    return m
+
+
+_codes = {}
+
+
+def code(mld, d):
+    if d not in _codes:
+        _codes[d] = mld.Code(d)
+    return _codes[d]
+
+
+def gpu_decode(mld, d, noise, syn, chi, precision=0):
+    C = code(mld, d)
+    nz = torch.tensor(np.asarray(noise, np.float32), device="cuda")
+    sy = torch.tensor(np.asarray(syn).view(np.int64), device="cuda")
+    lp, am = C.decode(nz, sy, chi, precision)
+    torch.cuda.synchronize()
+    assert C.status() == 0
+    return lp.cpu().numpy(), am.cpu().numpy()
+
+
+def check_argmax(am, ref):
+    top = np.sort(ref, axis=1)
+    clear = top[:, -1] - top[:, -2] > TIE
+    np.testing.assert_array_equal(am[clear], np.argmax(ref, axis=1)[clear])
+    # at near-ties the pick must still be one of the near-best classes
+    picked = ref[np.arange(len(am)), am]
+    assert np.all(picked >= top[:, -1] - TIE)
+
+
+def test_d3_all_syndromes_vs_bruteforce(mld):
+    d, n = 3, 9
+    m = d * d - 1
+    bits = ((np.arange(1 << m)[:, None] >> np.arange(m)[None, :]) & 1).astype(np.uint8)
+    syn = synth.pack_bits(bits)
+    noise = synth.depolarizing(n, 0.10)
+    ref = np.log(oracle.bruteforce_table(d, noise))
+    lp, am = gpu_decode(mld, d, noise.astype(np.float32), syn, 8)
+    np.testing.assert_allclose(lp, ref, rtol=0, atol=TOL)
+    check_argmax(am, ref)
+
+
+def test_config_d3_1024_seed0(mld):
+    d, n = 3, 9
+    noise = synth.depolarizing(n, 0.10).astype(np.float32)
+    E = synth.sample_errors(d, noise, 1024, seed=0)
+    syn = synth.syndromes_of(d, E)
+    ref, _ = oracle.decode(d, noise, syn)
+    lp, am = gpu_decode(mld, d, noise, syn, 8)
+    np.testing.assert_allclose(lp, ref, rtol=0, atol=TOL)
+    check_argmax(am, ref)
+
+
+@pytest.mark.parametrize("d", [5, 7, 9])
+@pytest.mark.parametrize("p", [0.05, 0.10, 0.15, 0.19])
+def test_exact_chi_vs_dense_oracle(mld, d, p):
+    n = d * d
+    chi = {5: 4, 7: 8, 9: 32}[d]
+    noise = synth.depolarizing(n, p).astype(np.float32)
+    B = 300 if d < 9 else 200           # several CTAs and a ragged tail
+    E = synth.sample_errors(d, noise, B, seed=synth.config_seed(1, d, p))
+    syn = synth.syndromes_of(d, E)
+    ref, _ = oracle.decode(d, noise, syn)
+    lp, am = gpu_decode(mld, d, noise, syn, chi)
+    np.testing.assert_allclose(lp, ref, rtol=0, atol=TOL)
+    check_argmax(am, ref)
+
+
+@pytest.mark.parametrize("d,chi", [(5, 16), (7, 32), (9, 16), (11, 32)])
+def test_more_chi_values_exact(mld, d, chi):
+    n = d * d
+    noise = synth.depolarizing(n, 0.12).astype(np.float32)
+    E = synth.sample_errors(d, noise, 64, seed=7)
+    syn = synth.syndromes_of(d, E)
+    ref, _ = oracle.decode(d, noise, syn)
+    lp, _ = gpu_decode(mld, d, noise, syn, chi)
+    np.testing.assert_allclose(lp, ref, rtol=0, atol=TOL)
+
+
+@pytest.mark.parametrize("d,chi", [(9, 8), (9, 4), (7, 4)])
+def test_truncated_chi_vs_fp64_mps(mld, d, chi):
+    """Below the exact bond the value is the boundary-MPS approximation: the
+    FP32 kernel must match the FP64 boundary-MPS oracle with the same rule.
+    Truncating columns are QR-canonicalised, and in an orthogonal gauge FP32
+    rounding (relative to the state's norm) reaches ln Z_l as
+    ~eps * Z_max / Z_l; the bar is therefore set on the leading coset's ln Z
+    and on the posterior Pr(l|s) = Z_l / sum Z."""
+    n = d * d
+    noise = synth.depolarizing(n, 0.12).astype(np.float32)
+    E = synth.sample_errors(d, noise, 6, seed=11)
+    syn = synth.syndromes_of(d, E)
+    ref = omps.decode_mps(d, noise.astype(np.float64), syn, chi)
+    lp, _ = gpu_decode(mld, d, noise, syn, chi)
+    best = np.argmax(ref, axis=1)
+    np.testing.assert_allclose(lp[np.arange(len(ref)), best], ref[np.arange(len(ref)), best], rtol=0, atol=1e-4)
+    post = lambda x: np.exp(x - x.max(axis=1, keepdims=True)) / np.exp(x - x.max(axis=1, keepdims=True)).sum(1, keepdims=True)
+    np.testing.assert_allclose(post(lp), post(ref), rtol=0, atol=1e-4)
+
+
+def test_per_syndrome_depolarizing(mld):
+    d = 7
+    B = 257
+    p = synth.per_syndrome_depolarizing(B, seed=3, lo=0.02, hi=0.18).astype(np.float32)
+    E = synth.sample_errors(d, p.astype(np.float64), B, seed=3)
+    syn = synth.syndromes_of(d, E)
+    ref, _ = oracle.decode(d, p.astype(np.float64), syn)
+    lp, am = gpu_decode(mld, d, p, syn, 8)
+    np.testing.assert_allclose(lp, ref, rtol=0, atol=TOL)
+    check_argmax(am, ref)
+
+
+def test_nonuniform_biased_noise_table(mld):
+    d, n = 7, 49
+    noise = synth.lognormal_biased(n, seed=4).astype(np.float32)
+    E = synth.sample_errors(d, noise, 128, seed=5)
+    syn = synth.syndromes_of(d, E)
+    ref, _ = oracle.decode(d, noise.astype(np.float64), syn)
+    lp, am = gpu_decode(mld, d, noise, syn, 32)
+    np.testing.assert_allclose(lp, ref, rtol=0, atol=TOL)
+    check_argmax(am, ref)
+
+
+def test_edge_cases(mld):
+    d, n = 5, 25
+    noise = synth.depolarizing(n, 0.1).astype(np.float32)
+    C = code(mld, d)
+    # B = 0 is a no-op
+    nz = torch.tensor(noise, device="cuda")
+    sy = torch.zeros((0, C.words), dtype=torch.int64, device="cuda")
+    lp, am = C.decode(nz, sy, 4)
+    assert lp.shape == (0, 4)
+    # the trivial syndrome and a single syndrome
+    syn = np.zeros((1, C.words), np.uint64)
+    ref, _ = oracle.decode(d, noise, syn)
+    lp, am = gpu_decode(mld, d, noise, syn, 4)
+    np.testing.assert_allclose(lp, ref, rtol=0, atol=TOL)
+    # zero-probability Paulis: p_Y = p_Z = 0 gives -inf cosets
+    bf = np.zeros((n, 4), np.float32)
+    bf[:, 0], bf[:, 1] = 0.9, 0.1
+    E = synth.sample_errors(d, bf, 16, seed=1)
+    syn = synth.syndromes_of(d, E)
+    ref, _ = oracle.decode(d, bf, syn)
+    lp, am = gpu_decode(mld, d, bf, syn, 4)
+    assert np.array_equal(np.isneginf(lp), np.isneginf(ref))
+    fin = np.isfinite(ref)
+    np.testing.assert_allclose(lp[fin], ref[fin], rtol=0, atol=TOL)
+    check_argmax(am, np.where(np.isfinite(ref), ref, -1e300))
+
+
+def test_host_entry_point_matches_device(mld):
+    d, n = 9, 81
+    noise = synth.depolarizing(n, 0.15).astype(np.float32)
+    E = synth.sample_errors(d, noise, 100, seed=9)
+    syn = synth.syndromes_of(d, E)
+    lp_d, am_d = gpu_decode(mld, d, noise, syn, 32)
+    lp_h, am_h = code(mld, d).decode_host(noise, syn, 32)
+    np.testing.assert_array_equal(lp_d, lp_h)
+    np.testing.assert_array_equal(am_d, am_h)
+
+
+def test_deterministic_rerun(mld):
+    d, n = 9, 81
+    noise = synth.depolarizing(n, 0.1).astype(np.float32)
+    syn = synth.syndromes_of(d, synth.sample_errors(d, noise, 512, seed=2))
+    a, _ = gpu_decode(mld, d, noise, syn, 32)
+    b, _ = gpu_decode(mld, d, noise, syn, 32)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_full_size_bench_config_sampled(mld):
+    """The bench workload (d=9, chi=32, p=0.10, 65536 syndromes) in the same
+    launch configuration; a seeded sample of 256 rows is checked against the
+    oracle and every row against invariants (finite, argmax consistent)."""
+    d, n, B = 9, 81, 65536
+    noise = synth.depolarizing(n, 0.10).astype(np.float32)
+    E = synth.sample_errors(d, noise, B, seed=synth.config_seed(1, d, 0.10))
+    syn = synth.syndromes_of(d, E)
+    lp, am = gpu_decode(mld, d, noise, syn, 32)
+    assert np.all(np.isfinite(lp))
+    assert np.array_equal(am, np.argmax(lp, axis=1))
+    idx = np.random.default_rng(0).choice(B, 256, replace=False)
+    ref, _ = oracle.decode(d, noise, syn[idx])
+    np.testing.assert_allclose(lp[idx], ref, rtol=0, atol=TOL)
+    check_argmax(am[idx], ref)
