@@ -104,7 +104,7 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(sample=8192):
+def cpu_baseline(sample=B):
     """The FP64 oracle (exact dense contraction, OpenMP over syndromes) on
     the host cores, on a bounded sample of the same workload."""
     import oracle
@@ -115,8 +115,8 @@ def cpu_baseline(sample=8192):
     oracle.decode(D, noise, syn, threads=cores)
     dt = time.perf_counter() - t
     return {"value": sample / dt, "unit": "syndromes/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {sample} of the {B} d=9 p=0.10 syndromes, exact FP64 dense contraction, "
-                      f"{dt:.1f} s wall"}
+            "sample": f"{sample} of the {B} d=9 p=0.10 syndromes (rank 0's batch), exact FP64 dense "
+                      f"contraction, {dt:.1f} s wall on {cores} threads"}
 
 
 def run_reference(args, rank, world):
@@ -152,6 +152,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=B, help="syndromes per GPU per step (default: the "
+                    "65536 of the workload; smaller values only for profiling captures)")
     args = ap.parse_args()
     rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)
     local = _env_int("LOCAL_RANK", 0)
@@ -166,18 +168,19 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     # shard: every rank decodes its own contiguous block of syndromes (weak scaling)
-    noise, syn = workload(B, rank * B)
+    Bn = args.batch
+    noise, syn = workload(Bn, rank * Bn)
     code = mld.Code(D)
     dev = torch.device("cuda", local)
     nz = torch.tensor(noise, device=dev)
     sy = torch.tensor(syn.view(np.int64), device=dev)
-    logP = torch.empty((B, 4), dtype=torch.float64, device=dev)
-    am = torch.empty((B,), dtype=torch.uint8, device=dev)
+    logP = torch.empty((Bn, 4), dtype=torch.float64, device=dev)
+    am = torch.empty((Bn,), dtype=torch.uint8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        mld.mld_decode(code.handle, nz, mld.MLD_NOISE_TABLE, sy, B, CHI, mld.MLD_FP32, logP, am,
+        mld.mld_decode(code.handle, nz, mld.MLD_NOISE_TABLE, sy, Bn, CHI, mld.MLD_FP32, logP, am,
                        stream.cuda_stream)
 
     for _ in range(max(3, args.warmup)):
@@ -206,7 +209,7 @@ def main():
         t_max = float(t.item())
     else:
         t_max = t_local
-    value = world * B * args.steps / t_max
+    value = world * Bn * args.steps / t_max
     st = code.status()
     if st != 0:
         raise RuntimeError("device status: " + mld.mld_status_string(st))
@@ -214,13 +217,13 @@ def main():
     # end-to-end through the host-buffer entry point (pinned host memory)
     h_noise = torch.tensor(noise).pin_memory()
     h_syn = torch.tensor(syn.view(np.int64)).pin_memory()
-    h_lp = torch.empty((B, 4), dtype=torch.float64).pin_memory()
-    h_am = torch.empty((B,), dtype=torch.uint8).pin_memory()
+    h_lp = torch.empty((Bn, 4), dtype=torch.float64).pin_memory()
+    h_am = torch.empty((Bn,), dtype=torch.uint8).pin_memory()
     import ctypes
 
     def e2e_step():
         s = mld.load().mld_decode_host(ctypes.c_void_p(code.handle), ctypes.c_void_p(h_noise.data_ptr()),
-                                       mld.MLD_NOISE_TABLE, ctypes.c_void_p(h_syn.data_ptr()), B, CHI,
+                                       mld.MLD_NOISE_TABLE, ctypes.c_void_p(h_syn.data_ptr()), Bn, CHI,
                                        mld.MLD_FP32, ctypes.c_void_p(h_lp.data_ptr()),
                                        ctypes.c_void_p(h_am.data_ptr()))
         if s != 0:
@@ -234,22 +237,22 @@ def main():
     for _ in range(e2e_steps):
         e2e_step()
     e2e_dt = time.perf_counter() - t0
-    e2e_val = world * B * e2e_steps / e2e_dt if world == 1 else B * e2e_steps / e2e_dt * world
+    e2e_val = world * Bn * e2e_steps / e2e_dt
 
     # roofline of the dominant kernel (the fused decode kernel): counted flops
     # of the executed schedule / its CUDA-event time (the argmax kernel is
     # < 1% of the step and is included in the timing)
-    flops_per_coset = code_flops(D, CHI)
-    achieved = 4 * B * flops_per_coset / (min(ms) / 1e3) / 1e12
+    flops_per_syn = code.flops(CHI, mld.MLD_FP32)
+    achieved = Bn * flops_per_syn / (statistics.median(ms) / 1e3) / 1e12
     clocks = clk.summary()
     peak = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": "syndromes/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"rotated d={D}, depolarizing p={P}, chi={CHI}, {B} syndromes per GPU per step, "
+        "config": {"workload": f"rotated d={D}, depolarizing p={P}, chi={CHI}, {Bn} syndromes per GPU per step, "
                                f"4 cosets + argmax, FP32 path",
-                   "global_batch": B * world, "l2": "flushed between timed steps (256 MiB write)",
+                   "global_batch": Bn * world, "l2": "flushed between timed steps (256 MiB write)",
                    "precision": "fp32"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
@@ -267,48 +270,6 @@ def main():
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
-
-
-def code_flops(d, chi):
-    """Counted flops per (syndrome, coset) of the executed schedule, from the
-    same shape rules as the library's planner (apply, QR, Q application)."""
-    def present(i, j):
-        if 1 <= i <= d - 1 and 1 <= j <= d - 1:
-            return True
-        if i in (0, d) and 1 <= j <= d - 1 and (i + j) % 2 == 0:
-            return True
-        if j in (0, d) and 1 <= i <= d - 1 and (i + j) % 2 == 1:
-            return True
-        return False
-    Dv = [1] * (d + 2)
-    fl = 0.0
-    for c in range(d):
-        pa = [2 if present(i, c) else 1 for i in range(d + 1)]
-        pb = [2 if present(i, c + 1) else 1 for i in range(d + 1)]
-        K, st = 1, []
-        for i in range(d + 1):
-            pam = 1 if i == 0 else pa[i - 1]
-            ncolA = pa[i] * Dv[i + 1]
-            ncol = ncolA if i < d else 1
-            tall = K > ncol
-            if tall:
-                for j in range(ncol):
-                    fl += pb[i] * (2.0 * (K - j) + 4.0 * (K - j) * (ncol - 1 - j))
-            fl += 2.0 * K * pam * Dv[i] * ncolA + 2.0 * pb[i] * K * ncolA * pam
-            st.append((K, ncol, tall, pb[i]))
-            K = pb[i] * min(K, ncol)
-        S = 1
-        newD = [1] * (d + 2)
-        for i in range(d, -1, -1):
-            rows, ncol, tall, pbi = st[i]
-            if tall:
-                for j in range(ncol):
-                    fl += pbi * 4.0 * (rows - j) * S
-            keep = min(chi, rows, pbi * S)
-            newD[i] = keep
-            S = keep
-        Dv = newD
-    return fl
 
 
 if __name__ == "__main__":

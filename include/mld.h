@@ -129,6 +129,13 @@ mld_status mld_decode_host(const mld_code* code, const float* noise, int noise_m
  * MLD_OK, MLD_ERR_TIMEOUT or MLD_ERR_NUMERIC. */
 mld_status mld_decode_status(const mld_code* code);
 
+/* Counted floating-point operations per syndrome (all four classes) of the
+ * sweep schedule that mld_decode runs for this code, chi and precision: the
+ * MPO.MPS products, the QR and Q applications of truncating columns and the
+ * bond-matrix products, from the same shape plan the kernel executes. Jacobi
+ * SVD work, which depends on the data, is not included. Host only. */
+mld_status mld_decode_flops(const mld_code* code, int chi, int precision, double* flops_per_syndrome);
+
 /* Number of kernel launches one mld_decode call makes (for accounting). */
 int mld_decode_launches(void);
 

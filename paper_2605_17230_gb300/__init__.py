@@ -30,7 +30,7 @@ MLD_NOISE_TABLE, MLD_NOISE_DEPOL = 0, 1
 EXPORTED_SYMBOLS = ["mld_code_create_rotated", "mld_code_destroy", "mld_code_info", "mld_code_layout",
                     "mld_code_representatives",
                     "mld_decode", "mld_decode_host", "mld_decode_status", "mld_decode_launches",
-                    "mld_status_string"]
+                    "mld_decode_flops", "mld_status_string"]
 
 _lib = None
 
@@ -73,6 +73,8 @@ def load(build_if_missing: bool = True):
     lib.mld_decode_host.restype = I
     lib.mld_decode_status.argtypes = [P]
     lib.mld_decode_status.restype = I
+    lib.mld_decode_flops.argtypes = [P, I, I, ctypes.POINTER(ctypes.c_double)]
+    lib.mld_decode_flops.restype = I
     lib.mld_decode_launches.argtypes = []
     lib.mld_decode_launches.restype = I
     lib.mld_status_string.argtypes = [I]
@@ -191,6 +193,13 @@ class Code:
         am = np.zeros(B, np.uint8)
         mld_decode_host(self.handle, noise, mode, syn, B, chi, precision, logP, am)
         return logP, am
+
+    def flops(self, chi, precision=MLD_FP32) -> float:
+        """Counted flops per syndrome (four classes) of the executed schedule."""
+        v = ctypes.c_double()
+        _check(load().mld_decode_flops(ctypes.c_void_p(self.handle), int(chi), int(precision), ctypes.byref(v)),
+               "mld_decode_flops")
+        return v.value
 
     def status(self) -> int:
         return mld_decode_status(self.handle)

@@ -21,6 +21,7 @@
 #include <new>
 #include <vector>
 
+#include "mld_exact.h"
 #include "mld_internal.h"
 
 extern "C" mld_status mld_code_build_host(int d, mld_code** out);
@@ -73,79 +74,34 @@ __device__ __forceinline__ float qweight(const float* wq, int parity, int a, int
 }
 
 // ---------------------------------------------------------------- left sweep
-// M^{b'}[k][col] = sum_a w(a, a'(col), beta(k), b') sum_r C[k][a*Dl + r] A[r][col]
-// When the incoming carry is an identity (st.cid: first site, or after a tall
-// block kept as a site), row k = (beta, j) selects j = a*Dl + r and the
-// product is elementwise: M^{b'}[k][col] = w(a, a', beta, b') A[r][col].
+__device__ __forceinline__ int qdiv(int x, int n, int l, bool p2) { return p2 ? (x >> l) : (x / n); }
+
+// Left-sweep product of one site:
+//   M^{b'}[k][(a', r')] = sum_a w(a, a', beta(k), b') X_a[k][(a', r')],
+//   X_a[k][col] = sum_r C[k][a*Dl + r] A[r][col].
+// The bond sum collapses for identity carries (st.cid: row k = (beta, j)
+// with j = a*Dl + r picks one term) and for identity old sites (K_IDR:
+// r = a'*Dr + r'; K_IDL: r = r' - a'*Dl when that lies in [0, Dl)); only a
+// data site with a data carry is a real GEMM. At the last site alpha_d is
+// summed (Dr = 1, ncol = 1).
 __device__ void apply_site(const SiteStep& st, const float* __restrict__ C,
                            const float* __restrict__ A, float* __restrict__ M,
                            const float* __restrict__ wts, int lane, bool last) {
     const int K = st.K, pam = st.pam, pa = st.pa, pb = st.pb, Dl = st.Dl, Dr = st.Dr;
     const int ncolA = pa * Dr, ncol = st.ncol, kqp = st.kq_prev, par = st.parity;
+    const bool p2 = st.pow2;
     const float* wq = st.qubit >= 0 ? wts + 4 * st.qubit : nullptr;
+    float wr[16];                      // w(a, a', beta, b') for this qubit, index a | a'<<1 | beta<<2 | b'<<3
+#pragma unroll
+    for (int m = 0; m < 16; ++m)
+        wr[m] = wq ? qweight(wq, par, m & 1, (m >> 1) & 1, (m >> 2) & 1, (m >> 3) & 1) : 1.f;
     const int ldc = pam * Dl;
-    if (st.cid) {
-        if (last) {
-            for (int k = lane; k < K; k += 32) {
-                const int beta = k / kqp, j = k - beta * kqp, a = j / Dl, r = j - a * Dl;
-                for (int bp = 0; bp < pb; ++bp) {
-                    float s = 0.f;
-                    for (int ap = 0; ap < pa; ++ap)
-                        s = fmaf(wq ? qweight(wq, par, a, ap, beta, bp) : 1.f, A[r * ncolA + ap], s);
-                    M[bp * K + k] = s;
-                }
-            }
-            return;
-        }
-        if ((ncolA & 3) == 0 && (Dr & 3) == 0) {
-            const int q4 = ncolA >> 2;
-            for (int tI = lane; tI < K * q4; tI += 32) {
-                const int k = tI / q4, col = (tI - k * q4) * 4, ap = col / Dr;
-                const int beta = k / kqp, j = k - beta * kqp, a = j / Dl, r = j - a * Dl;
-                const float4 av = *reinterpret_cast<const float4*>(A + r * ncolA + col);
-                for (int bp = 0; bp < pb; ++bp) {
-                    const float w = wq ? qweight(wq, par, a, ap, beta, bp) : 1.f;
-                    *reinterpret_cast<float4*>(M + (bp * K + k) * ncol + col) =
-                        make_float4(w * av.x, w * av.y, w * av.z, w * av.w);
-                }
-            }
-            return;
-        }
-        for (int e = lane; e < K * ncolA; e += 32) {
-            const int k = e / ncolA, col = e - k * ncolA, ap = col / Dr;
-            const int beta = k / kqp, j = k - beta * kqp, a = j / Dl, r = j - a * Dl;
-            const float av = A[r * ncolA + col];
-            for (int bp = 0; bp < pb; ++bp)
-                M[(bp * K + k) * ncol + col] = (wq ? qweight(wq, par, a, ap, beta, bp) : 1.f) * av;
-        }
-        return;
-    }
-    if (last) {
-        // alpha_d has no factor to its right: sum it here (Dr = 1, ncol = 1)
-        for (int k = lane; k < K; k += 32) {
-            const int beta = k / kqp;
-            float t[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-            for (int a = 0; a < pam; ++a)
-                for (int ap = 0; ap < pa; ++ap) {
-                    float s = 0.f;
-                    for (int r = 0; r < Dl; ++r) s = fmaf(C[k * ldc + a * Dl + r], A[r * ncolA + ap], s);
-                    t[a][ap] = s;
-                }
-            for (int bp = 0; bp < pb; ++bp) {
-                float s = 0.f;
-                for (int a = 0; a < pam; ++a)
-                    for (int ap = 0; ap < pa; ++ap)
-                        s = fmaf(wq ? qweight(wq, par, a, ap, beta, bp) : 1.f, t[a][ap], s);
-                M[bp * K + k] = s;
-            }
-        }
-        return;
-    }
-    if ((ncolA & 3) == 0 && (Dr & 3) == 0) {
-        // four consecutive columns share a' (Dr % 4 == 0)
-        const int q4 = ncolA >> 2;
+    const int kind = st.okind;
+    if (!st.cid && kind == K_DATA && !last && (ncolA & 3) == 0 && (Dr & 3) == 0) {
+        // dense GEMM, four consecutive columns per lane (they share a')
+        const int q4 = ncolA >> 2, lq4 = st.lncol - 2;
         for (int tI = lane; tI < K * q4; tI += 32) {
-            const int k = tI / q4, col = (tI - k * q4) * 4, ap = col / Dr;
+            const int k = qdiv(tI, q4, lq4, p2), col = (tI - k * q4) * 4, ap = qdiv(col, Dr, st.lDr, p2);
             float4 t0 = make_float4(0.f, 0.f, 0.f, 0.f), t1 = t0;
             const float* c0 = C + k * ldc;
             const float* c1 = c0 + Dl;
@@ -160,10 +116,10 @@ __device__ void apply_site(const SiteStep& st, const float* __restrict__ C,
                     t1.z = fmaf(x1, av.z, t1.z); t1.w = fmaf(x1, av.w, t1.w);
                 }
             }
-            const int beta = k / kqp;
+            const int beta = qdiv(k, kqp, st.lkqp, p2);
             for (int bp = 0; bp < pb; ++bp) {
-                const float w0 = wq ? qweight(wq, par, 0, ap, beta, bp) : 1.f;
-                const float w1 = (wq && pam == 2) ? qweight(wq, par, 1, ap, beta, bp) : 0.f;
+                const float w0 = wr[(ap << 1) | (beta << 2) | (bp << 3)];
+                const float w1 = pam == 2 ? wr[1 | (ap << 1) | (beta << 2) | (bp << 3)] : 0.f;
                 float4 o;
                 o.x = fmaf(w0, t0.x, w1 * t1.x); o.y = fmaf(w0, t0.y, w1 * t1.y);
                 o.z = fmaf(w0, t0.z, w1 * t1.z); o.w = fmaf(w0, t0.w, w1 * t1.w);
@@ -172,21 +128,48 @@ __device__ void apply_site(const SiteStep& st, const float* __restrict__ C,
         }
         return;
     }
-    for (int e = lane; e < K * ncolA; e += 32) {
-        const int k = e / ncolA, col = e - k * ncolA, ap = col / Dr;
-        float t0 = 0.f, t1 = 0.f;
-        const float* c0 = C + k * ldc;
-        for (int r = 0; r < Dl; ++r) {
-            const float av = A[r * ncolA + col];
-            t0 = fmaf(c0[r], av, t0);
-            if (pam == 2) t1 = fmaf(c0[Dl + r], av, t1);
+    // general element loop (identity kinds, identity carries, odd shapes)
+    const int nout = last ? K : K * ncolA;
+    for (int e = lane; e < nout; e += 32) {
+        int k, col;
+        if (last) { k = e; col = 0; }
+        else { k = qdiv(e, ncolA, st.lncol, p2); col = e - k * ncolA; }
+        const int beta = qdiv(k, kqp, st.lkqp, p2);
+        const int j = k - beta * kqp;              // identity carry: j = a*Dl + r
+        const int ja = st.cid ? qdiv(j, Dl, st.lDl, p2) : 0;
+        const int jr = j - ja * Dl;
+        float acc[2] = {0.f, 0.f};                 // per b'
+        const int apLo = last ? 0 : qdiv(col, Dr, st.lDr, p2);
+        const int apHi = last ? pa : apLo + 1;
+        for (int ap = apLo; ap < apHi; ++ap) {
+            const int rp = last ? 0 : col - ap * Dr;
+            float X[2] = {0.f, 0.f};
+            if (st.cid) {
+                float av;
+                if (kind == K_DATA) av = A[jr * ncolA + ap * Dr + rp];
+                else if (kind == K_IDR) av = (jr == ap * Dr + rp) ? 1.f : 0.f;
+                else av = (rp == ap * Dl + jr) ? 1.f : 0.f;
+                X[ja] = av;
+            } else {
+                for (int a = 0; a < pam; ++a) {
+                    const float* crow = C + k * ldc + a * Dl;
+                    float s = 0.f;
+                    if (kind == K_DATA) {
+                        for (int r = 0; r < Dl; ++r) s = fmaf(crow[r], A[r * ncolA + ap * Dr + rp], s);
+                    } else if (kind == K_IDR) {
+                        s = crow[ap * Dr + rp];
+                    } else {
+                        const int r = rp - ap * Dl;
+                        s = (r >= 0 && r < Dl) ? crow[r] : 0.f;
+                    }
+                    X[a] = s;
+                }
+            }
+            for (int bp = 0; bp < pb; ++bp)
+                acc[bp] = fmaf(wr[(ap << 1) | (beta << 2) | (bp << 3)], X[0],
+                               fmaf(wr[1 | (ap << 1) | (beta << 2) | (bp << 3)], X[1], acc[bp]));
         }
-        const int beta = k / kqp;
-        for (int bp = 0; bp < pb; ++bp) {
-            const float w0 = wq ? qweight(wq, par, 0, ap, beta, bp) : 1.f;
-            const float w1 = (wq && pam == 2) ? qweight(wq, par, 1, ap, beta, bp) : 0.f;
-            M[(bp * K + k) * ncol + col] = fmaf(w0, t0, w1 * t1);
-        }
+        for (int bp = 0; bp < pb; ++bp) M[(bp * K + k) * ncol + col] = acc[bp];
     }
 }
 
@@ -420,34 +403,43 @@ decode_fp32_kernel(DecodeArgs a) {
         }
         if (zero || bad) break;
         // ---- right sweep; carry g (rows x S), T into t. A tall last block
-        // kept as the site leaves an identity carry (pb x 1 of ones).
+        // kept as the site leaves an identity carry (st.gid).
         float* g = cin;
         float* t = cout;
-        if (S[d].tall && !S[d].canon) {
-            if (lane < S[d].pb) g[lane] = 1.f;
-            __syncwarp();
-        }
         for (int i = d; i >= 0; --i) {
             const SiteStep st = S[i];
             const int rows = st.K, Sr = st.S, pb = st.pb, cols = pb * Sr, kq = st.kq;
             // T^b = Q^b [G^b; 0] (canonical column), M^b G^b (tall block kept
-            // as the site), or G^b (wide block, Q = I)
-            if (st.tall && !st.canon) {
+            // as the site) or G^b (wide block, Q = I). st.gid: the incoming
+            // carry is the identity, G[row][s] = [row == s]. A binary-expansion
+            // identity site (K_IDL) is not formed at all.
+            const int gid = st.gid;
+            if (st.nkind == K_IDL) {
+                // nothing to form or store; the carry stays the identity
+            } else if (st.tall && !st.canon) {
                 const float* Mb = qst + st.offQ;
                 const int nc = st.ncol;
                 for (int e = lane; e < rows * cols; e += 32) {
                     const int r = e / cols, cc = e - r * cols, bb = cc / Sr, s = cc - bb * Sr;
                     const float* mrow = Mb + (bb * rows + r) * nc;
-                    const float* gcol = g + (bb * kq) * Sr + s;
                     float acc = 0.f;
-                    for (int j = 0; j < nc; ++j) acc = fmaf(mrow[j], gcol[j * Sr], acc);
+                    if (gid == 2) {                    // G^b = I_kq
+                        acc = mrow[s];
+                    } else if (gid) {                  // G = I: G^b selects columns b*kq ..
+                        const int j = s - bb * kq;
+                        acc = (j >= 0 && j < nc) ? mrow[j] : 0.f;
+                    } else {
+                        const float* gcol = g + (bb * kq) * Sr + s;
+                        for (int j = 0; j < nc; ++j) acc = fmaf(mrow[j], gcol[j * Sr], acc);
+                    }
                     t[e] = acc;
                 }
                 __syncwarp();
             } else if (st.tall) {
                 for (int e = lane; e < rows * cols; e += 32) {
                     const int r = e / cols, cc = e - r * cols, bb = cc / Sr, s = cc - bb * Sr;
-                    t[e] = r < kq ? g[(bb * kq + r) * Sr + s] : 0.f;
+                    const int grow = bb * kq + r;
+                    t[e] = r < kq ? (gid ? (grow == s ? 1.f : 0.f) : g[grow * Sr + s]) : 0.f;
                 }
                 __syncwarp();
                 const float* Mq = qst + st.offQ;
@@ -462,18 +454,18 @@ decode_fp32_kernel(DecodeArgs a) {
             } else {
                 for (int e = lane; e < rows * cols; e += 32) {
                     const int r = e / cols, cc = e - r * cols, bb = cc / Sr, s = cc - bb * Sr;
-                    t[e] = g[(bb * rows + r) * Sr + s];
+                    const int grow = bb * rows + r;
+                    t[e] = gid ? (grow == s ? 1.f : 0.f) : g[grow * Sr + s];
                 }
                 __syncwarp();
             }
             float* site = mps + st.offN;
             const int Sl = st.Sl;
             if (st.rmode == R_IDENT) {
-                for (int e = lane; e < cols * cols; e += 32) site[e] = (e / cols == e % cols) ? 1.f : 0.f;
-                float* tmp = g; g = t; t = tmp;        // carry = T (rows x cols)
+                float* tmp = g; g = t; t = tmp;        // site = identity (K_IDR), carry = T
             } else if (st.rmode == R_DENSE) {
-                for (int e = lane; e < rows * cols; e += 32) site[e] = t[e];
-                for (int e = lane; e < rows * rows; e += 32) g[e] = (e / rows == e % rows) ? 1.f : 0.f;
+                if (st.nkind == K_DATA)                // site = T, carry = identity (implicit)
+                    for (int e = lane; e < rows * cols; e += 32) site[e] = t[e];
             } else {
                 // truncated SVD of T keeping Sl singular values
                 const int nv = rows < cols ? rows : cols;
@@ -548,8 +540,14 @@ decode_fp32_kernel(DecodeArgs a) {
             const float* site = mps + st.offN;
             for (int s = lane; s < st.S; s += 32) {
                 float acc = 0.f;
-                for (int sl = 0; sl < st.Sl; ++sl)
-                    for (int bb = 0; bb < st.pb; ++bb) acc = fmaf(v[sl], site[(sl * st.pb + bb) * st.S + s], acc);
+                if (st.nkind == K_IDR) {              // A[l][b][s] = [l == b*S + s]
+                    for (int bb = 0; bb < st.pb; ++bb) acc += v[bb * st.S + s];
+                } else if (st.nkind == K_IDL) {       // A[l][b][s] = [s == b*Sl + l]
+                    acc = v[s % st.Sl];
+                } else {
+                    for (int sl = 0; sl < st.Sl; ++sl)
+                        for (int bb = 0; bb < st.pb; ++bb) acc = fmaf(v[sl], site[(sl * st.pb + bb) * st.S + s], acc);
+                }
                 vn[s] = acc;
             }
             __syncwarp();
@@ -613,9 +611,9 @@ const mld_code::PlanDev* get_plan(mld_code* C, int chi, mld_status* st) {
     pd.chi = chi;
     pd.plan = mld::make_plan(C->d, chi);
     pd.d_steps = nullptr;
-    const size_t bytes = pd.plan.steps.size() * sizeof(mld::SiteStep);
+    const size_t bytes = (size_t)pd.plan.nsteps * sizeof(mld::SiteStep);
     if (cudaMalloc(&pd.d_steps, bytes) != cudaSuccess) { *st = MLD_ERR_NOMEM; return nullptr; }
-    if (cudaMemcpy(pd.d_steps, pd.plan.steps.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (cudaMemcpy(pd.d_steps, pd.plan.steps, bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(pd.d_steps);
         *st = MLD_ERR_CUDA;
         return nullptr;
@@ -680,6 +678,14 @@ mld_status mld_code_layout(const mld_code* C, int32_t* type, int32_t* sup, uint8
 
 int mld_decode_launches(void) { return 2; }
 
+mld_status mld_decode_flops(const mld_code* C, int chi, int precision, double* out) {
+    if (!C || chi < 1 || !out) return MLD_ERR_INVALID_ARG;
+    if (precision != MLD_FP32 && precision != MLD_MIXED_BF16 && precision != MLD_MIXED_TF32)
+        return MLD_ERR_INVALID_ARG;
+    *out = 4.0 * mld::make_plan(C->d, chi).flops_per_coset;
+    return MLD_OK;
+}
+
 mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, const uint64_t* syn,
                       int64_t B, int chi, int precision, double* logP, uint8_t* argmax, void* stream) {
     mld_code* C = const_cast<mld_code*>(Cc);
@@ -720,7 +726,10 @@ mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, co
         cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
         return MLD_ERR_CUDA;
-    const size_t pw = (size_t)P.floats_per_warp * sizeof(float);
+    // untruncated chi (every kept dimension is min(rows, cols)): the
+    // compile-time specialised kernel, when one exists for this d
+    const bool exact = P.svd_sites == 0 && precision == MLD_FP32 && mld::exact_floats_per_warp(C->d) > 0;
+    const size_t pw = (size_t)(exact ? mld::exact_floats_per_warp(C->d) : P.floats_per_warp) * sizeof(float);
     if (pw > (size_t)max_optin) return MLD_ERR_UNSUPPORTED;
     // warps per CTA: the most resident warps per SM (32 CTAs and 64 warps
     // per SM at most, 1 KB of shared memory reserved per CTA), fewest warps
@@ -734,10 +743,26 @@ mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, co
         if (warps > best) { best = warps; W = w; }
     }
     const size_t smem = pw * W;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (exact) {
+        mld::ExactArgs ea;
+        ea.dmask = C->d_dmask;
+        ea.noise = noise;
+        ea.syn = syn;
+        ea.logP = logP;
+        ea.status = C->d_status;
+        ea.B = B;
+        ea.noise_mode = noise_mode;
+        if (!mld::launch_exact(C->d, ea, s, W)) return MLD_ERR_CUDA;
+        if (argmax) {
+            mld::argmax_kernel<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(logP, argmax, B);
+            if (cudaGetLastError() != cudaSuccess) return MLD_ERR_CUDA;
+        }
+        return MLD_OK;
+    }
     if (cudaFuncSetAttribute(mld::decode_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return MLD_ERR_CUDA;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int64_t units = 4 * B;
     const int64_t blocks = (units + W - 1) / W;
     if (blocks > 0x7fffffff) return MLD_ERR_UNSUPPORTED;
