@@ -124,6 +124,31 @@ mld_status mld_decode_host(const mld_code* code, const float* noise, int noise_m
                            const uint64_t* syndromes, int64_t B, int chi, int precision,
                            double* logP, uint8_t* argmax);
 
+/* mld_decode without any device allocation, for callers that cannot
+ * allocate device memory (a real-time loop that must not stall on the
+ * device-wide synchronisation of cudaMalloc, or a process whose device memory
+ * is already reserved by another framework's caching allocator). The paper
+ * has no counterpart: this is a deployment variant of the untruncated sweep.
+ *   Scope: precision MLD_FP32, chi at or above the exact bond of every cut
+ *   (no truncation), and the distances with a compile-time specialised kernel
+ *   (3 <= d <= 11); anything else returns MLD_ERR_UNSUPPORTED.
+ *   Scratch: the status word and the code's destabiliser tables live in one
+ *   16 KiB file-scope __device__ array that every GPU loading the library
+ *   holds until the process exits; a code whose tables do not fit returns
+ *   MLD_ERR_UNSUPPORTED. Each call resets the status word and rewrites the
+ *   tables (asynchronous copies on `stream`); the array keeps the last call's
+ *   contents, so calls that overlap on the GPU (other streams, other threads)
+ *   race and must be serialised by the caller.
+ *   Set-up: the first call on a device looks up the array's device address
+ *   (the device must be current); make that first call before any stream
+ *   capture.
+ *   Arguments as mld_decode. check_status != 0 synchronises the stream and
+ *   returns the device status (MLD_OK or MLD_ERR_NUMERIC); 0 returns as soon
+ *   as the work is enqueued. */
+mld_status mld_decode_noalloc(const mld_code* code, const float* noise, int noise_mode,
+                              const uint64_t* syndromes, int64_t B, int chi, int precision,
+                              double* logP, uint8_t* argmax, void* stream, int check_status);
+
 /* Read and clear the device status word written by earlier mld_decode calls
  * on this code (the caller must have synchronised their streams):
  * MLD_OK, MLD_ERR_TIMEOUT or MLD_ERR_NUMERIC. */

@@ -30,7 +30,7 @@ MLD_NOISE_TABLE, MLD_NOISE_DEPOL = 0, 1
 EXPORTED_SYMBOLS = ["mld_code_create_rotated", "mld_code_destroy", "mld_code_info", "mld_code_layout",
                     "mld_code_representatives",
                     "mld_decode", "mld_decode_host", "mld_decode_status", "mld_decode_launches",
-                    "mld_decode_flops", "mld_status_string"]
+                    "mld_decode_flops", "mld_decode_noalloc", "mld_status_string"]
 
 _lib = None
 
@@ -69,6 +69,8 @@ def load(build_if_missing: bool = True):
     lib.mld_code_representatives.restype = I
     lib.mld_decode.argtypes = [P, P, I, P, L, I, I, P, P, P]
     lib.mld_decode.restype = I
+    lib.mld_decode_noalloc.argtypes = [P, P, I, P, L, I, I, P, P, P, I]
+    lib.mld_decode_noalloc.restype = I
     lib.mld_decode_host.argtypes = [P, P, I, P, L, I, I, P, P]
     lib.mld_decode_host.restype = I
     lib.mld_decode_status.argtypes = [P]
@@ -111,6 +113,19 @@ def mld_decode(code, noise, noise_mode, syndromes, B, chi, precision, logP, argm
     st = load().mld_decode(ctypes.c_void_p(code), _ptr(noise), int(noise_mode), _ptr(syndromes), int(B),
                            int(chi), int(precision), _ptr(logP), _ptr(argmax), ctypes.c_void_p(int(stream)))
     _check(st, "mld_decode")
+
+
+def mld_decode_noalloc(code, noise, noise_mode, syndromes, B, chi, precision, logP, argmax=None, stream=None,
+                       check_status=True):
+    """C-ABI mld_decode_noalloc on torch CUDA tensors: no device allocation;
+    scratch in the library's fixed device array (see include/mld.h)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    st = load().mld_decode_noalloc(ctypes.c_void_p(code), _ptr(noise), int(noise_mode), _ptr(syndromes), int(B),
+                                   int(chi), int(precision), _ptr(logP), _ptr(argmax),
+                                   ctypes.c_void_p(int(stream)), int(bool(check_status)))
+    _check(st, "mld_decode_noalloc")
 
 
 def mld_decode_host(code, noise, noise_mode, syndromes, B, chi, precision, logP, argmax=None):
