@@ -50,6 +50,14 @@ def workload(B_local, b0):
     return noise, synth.syndromes_of(D, E)
 
 
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during timing."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -179,40 +187,55 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
-        mld.mld_decode(code.handle, nz, mld.MLD_NOISE_TABLE, sy, Bn, CHI, mld.MLD_FP32, logP, am,
-                       stream.cuda_stream)
+    prec_mixed = mld.MLD_MIXED_TF32
 
-    for _ in range(max(3, args.warmup)):
-        step()
+    def step(prec):
+        mld.mld_decode(code.handle, nz, mld.MLD_NOISE_TABLE, sy, Bn, CHI, prec, logP, am, stream.cuda_stream)
+
+    # accuracy of the mixed-precision path against the FP32 path on this batch
+    step(mld.MLD_FP32)
+    lp32 = logP.clone()
+    step(prec_mixed)
     torch.cuda.synchronize()
+    dlogp = float((logP - lp32).abs().max().item())
     if code.status() != 0:
-        raise RuntimeError("device status after warm-up: " + mld.mld_status_string(code.status()))
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with Clocks(local) as clk:
-        if dist:
-            dist.barrier()
+        raise RuntimeError("device status after the accuracy pass: " + mld.mld_status_string(code.status()))
+
+    def timed(prec, clocks):
+        for _ in range(max(3, args.warmup)):
+            step(prec)
         torch.cuda.synchronize()
-        for k in range(args.steps):
-            flush.fill_(float(k))                      # evict L2 between timed steps (outside the events)
-            ev[k][0].record(stream)
-            step()
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        with Clocks(local) if clocks else _Null() as clk:
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            for k in range(args.steps):
+                flush.fill_(float(k))                  # evict L2 between timed steps (outside the events)
+                ev[k][0].record(stream)
+                step(prec)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        t_local = sum(ms) / 1e3
         if dist:
-            dist.barrier()
-    ms = [a.elapsed_time(b) for a, b in ev]
-    t_local = sum(ms) / 1e3
-    if dist:
-        t = torch.tensor([t_local], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
+            t = torch.tensor([t_local], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_local = float(t.item())
+        st = code.status()
+        if st != 0:
+            raise RuntimeError("device status: " + mld.mld_status_string(st))
+        return t_local, ms, (clk.summary() if clocks else None)
+
+    t32, ms32, _ = timed(mld.MLD_FP32, False)
+    value32 = world * Bn * args.steps / t32
+    t_max, ms, clocks = timed(prec_mixed, True)
     value = world * Bn * args.steps / t_max
-    st = code.status()
-    if st != 0:
-        raise RuntimeError("device status: " + mld.mld_status_string(st))
+    mixed_ok = dlogp <= 1e-3
+    if not mixed_ok:                                   # the metric's bound failed: report the FP32 path
+        value, t_max, ms, prec_mixed = value32, t32, ms32, mld.MLD_FP32
 
     # end-to-end through the host-buffer entry point (pinned host memory)
     h_noise = torch.tensor(noise).pin_memory()
@@ -224,7 +247,7 @@ def main():
     def e2e_step():
         s = mld.load().mld_decode_host(ctypes.c_void_p(code.handle), ctypes.c_void_p(h_noise.data_ptr()),
                                        mld.MLD_NOISE_TABLE, ctypes.c_void_p(h_syn.data_ptr()), Bn, CHI,
-                                       mld.MLD_FP32, ctypes.c_void_p(h_lp.data_ptr()),
+                                       prec_mixed, ctypes.c_void_p(h_lp.data_ptr()),
                                        ctypes.c_void_p(h_am.data_ptr()))
         if s != 0:
             raise RuntimeError("mld_decode_host: " + mld.mld_status_string(s))
@@ -242,18 +265,22 @@ def main():
     # roofline of the dominant kernel (the fused decode kernel): counted flops
     # of the executed schedule / its CUDA-event time (the argmax kernel is
     # < 1% of the step and is included in the timing)
-    flops_per_syn = code.flops(CHI, mld.MLD_FP32)
+    flops_per_syn = code.flops(CHI, prec_mixed)
     achieved = Bn * flops_per_syn / (statistics.median(ms) / 1e3) / 1e12
-    clocks = clk.summary()
     peak = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": "syndromes/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "tf32x3+f32" if prec_mixed == mld.MLD_MIXED_TF32 else "f32", "data": "synthetic",
         "config": {"workload": f"rotated d={D}, depolarizing p={P}, chi={CHI}, {Bn} syndromes per GPU per step, "
-                               f"4 cosets + argmax, FP32 path",
+                               f"4 cosets + argmax",
                    "global_batch": Bn * world, "l2": "flushed between timed steps (256 MiB write)",
-                   "precision": "fp32"},
+                   "precision": ("mixed: MPO.MPS data-site products on tensor cores from split TF32 operands "
+                                 "(hi.hi + hi.lo + lo.hi), FP32 accumulate; everything else FP32")
+                   if prec_mixed == mld.MLD_MIXED_TF32 else "fp32 (mixed path failed the 1e-3 bound)"},
+        "fp32": {"value": value32, "ms_per_step": 1e3 * t32 / args.steps},
+        "mixed_vs_fp32_max_abs_dlogP": dlogp,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "note": "FP32 FFMA pipe: 152 SMs x 128 lanes x 2 flop x 2070 MHz; achieved = counted "

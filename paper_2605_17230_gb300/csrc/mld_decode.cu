@@ -693,7 +693,6 @@ mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, co
     if (noise_mode != MLD_NOISE_TABLE && noise_mode != MLD_NOISE_DEPOL) return MLD_ERR_INVALID_ARG;
     if (precision != MLD_FP32 && precision != MLD_MIXED_BF16 && precision != MLD_MIXED_TF32)
         return MLD_ERR_INVALID_ARG;
-    if (precision != MLD_FP32) return MLD_ERR_UNSUPPORTED;
     if (B == 0) return MLD_OK;
     if (!noise || !syn || !logP) return MLD_ERR_INVALID_ARG;
     if (noise_mode == MLD_NOISE_TABLE && (reinterpret_cast<uintptr_t>(noise) & 15)) return MLD_ERR_INVALID_ARG;
@@ -728,7 +727,10 @@ mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, co
         return MLD_ERR_CUDA;
     // untruncated chi (every kept dimension is min(rows, cols)): the
     // compile-time specialised kernel, when one exists for this d
-    const bool exact = P.svd_sites == 0 && precision == MLD_FP32 && mld::exact_floats_per_warp(C->d) > 0;
+    const bool exact = P.svd_sites == 0 && mld::exact_floats_per_warp(C->d) > 0;
+    // the mixed-precision path exists for the untruncated specialised kernel
+    // (TF32 tensor-core products); BF16 and truncating chi run FP32 only
+    if (precision == MLD_MIXED_BF16 || (precision == MLD_MIXED_TF32 && !exact)) return MLD_ERR_UNSUPPORTED;
     const size_t pw = (size_t)(exact ? mld::exact_floats_per_warp(C->d) : P.floats_per_warp) * sizeof(float);
     if (pw > (size_t)max_optin) return MLD_ERR_UNSUPPORTED;
     // warps per CTA: the most resident warps per SM (32 CTAs and 64 warps
@@ -753,7 +755,7 @@ mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, co
         ea.status = C->d_status;
         ea.B = B;
         ea.noise_mode = noise_mode;
-        if (!mld::launch_exact(C->d, ea, s, W)) return MLD_ERR_CUDA;
+        if (!mld::launch_exact(C->d, ea, s, W, precision)) return MLD_ERR_CUDA;
         if (argmax) {
             mld::argmax_kernel<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(logP, argmax, B);
             if (cudaGetLastError() != cudaSuccess) return MLD_ERR_CUDA;

@@ -73,13 +73,103 @@ __device__ __forceinline__ void x_ident(const float* C, const float* A, int k, i
     }
 }
 
+__device__ __forceinline__ unsigned to_tf32(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// D += A(16x8) B(8x8) on the tensor cores, TF32 operands, FP32 accumulate.
+// Fragments (g = lane/4, t = lane%4): A rows g, g+8 x cols t, t+4; B rows
+// t, t+4 x col g; D rows g, g+8 x cols 2t, 2t+1.
+__device__ __forceinline__ void mma_tf32(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Split x into TF32 parts hi + lo (hi = x rounded to TF32, lo = the
+// rounded remainder): products of the parts recover ~FP32 accuracy.
+__device__ __forceinline__ void split_tf32(float x, unsigned& hi, unsigned& lo) {
+    hi = to_tf32(x);
+    lo = to_tf32(x - __uint_as_float(hi));
+}
+
+// The data-site product of the mixed-precision path: X_a = C_a A on the
+// tensor cores, TF32 operands and FP32 accumulation, each operand split
+// into TF32 hi + lo and the product taken as hi.hi + hi.lo + lo.hi (the
+// lo.lo term is below FP32 rounding). One 16-row block of k for both a at
+// a time, then the FP32 qubit-factor epilogue
+// M^{b'}[k][col] = sum_a w(a, a', beta, b') X_a[k][col].
+template <int K, int PAM, int DL, int PA, int DR, int PB, int NCOL, int KQP>
+__device__ __forceinline__ float gemm_tf32(const float* __restrict__ C, const float* __restrict__ A,
+                                           float* __restrict__ M, const float4 w, int par, int lane) {
+    constexpr int NCOLA = PA * DR;
+    constexpr int LDC = PAM * DL;
+    static_assert(DL % 8 == 0 && NCOLA % 8 == 0, "tensor-core tile shape");
+    const int g = lane >> 2, t = lane & 3;
+    float mx = 0.f;
+    for (int kb = 0; kb < (K + 15) / 16; ++kb) {
+        const int r0 = kb * 16 + g, r1 = r0 + 8;
+#pragma unroll
+        for (int nt = 0; nt < NCOLA / 8; ++nt) {
+            float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+            for (int ks = 0; ks < DL; ks += 8) {
+                unsigned bh0, bl0, bh1, bl1;
+                split_tf32(A[(ks + t) * NCOLA + nt * 8 + g], bh0, bl0);
+                split_tf32(A[(ks + t + 4) * NCOLA + nt * 8 + g], bh1, bl1);
+#pragma unroll
+                for (int a = 0; a < PAM; ++a) {
+                    const float* c0 = C + r0 * LDC + a * DL + ks;
+                    const float* c1 = C + r1 * LDC + a * DL + ks;
+                    unsigned ah[4], al[4];
+                    split_tf32(r0 < K ? c0[t] : 0.f, ah[0], al[0]);
+                    split_tf32(r1 < K ? c1[t] : 0.f, ah[1], al[1]);
+                    split_tf32(r0 < K ? c0[t + 4] : 0.f, ah[2], al[2]);
+                    split_tf32(r1 < K ? c1[t + 4] : 0.f, ah[3], al[3]);
+                    mma_tf32(acc[a], al[0], al[1], al[2], al[3], bh0, bh1);
+                    mma_tf32(acc[a], ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+                    mma_tf32(acc[a], ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = kb * 16 + g + 8 * h;
+                if (k >= K) continue;
+                const int beta = k / KQP;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int col = nt * 8 + 2 * t + e, ap = col / DR;
+                    const float x0 = acc[0][2 * h + e], x1 = PAM == 2 ? acc[1][2 * h + e] : 0.f;
+#pragma unroll
+                    for (int bp = 0; bp < PB; ++bp) {
+                        const float o = fmaf(wsel(w, par, 0, ap, beta, bp), x0, wsel(w, par, 1, ap, beta, bp) * x1);
+                        M[(bp * K + k) * NCOL + col] = o;
+                        mx = fmaxf(mx, fabsf(o));
+                    }
+                }
+            }
+        }
+    }
+    return mx;
+}
+
 // One left-sweep site: M^{b'}[k][col] = sum_a w(a, a', beta(k), b') X_a[k][col].
 // Returns this lane's max |M|.
-template <int K, int PAM, int DL, int PA, int DR, int PB, int NCOL, int KQP, int CID, int OKIND, int LAST>
+template <int K, int PAM, int DL, int PA, int DR, int PB, int NCOL, int KQP, int CID, int OKIND, int LAST,
+          int PREC>
 __device__ __noinline__ float left_step(const float* __restrict__ C, const float* __restrict__ A,
                                         float* __restrict__ M, const float4 w, int par, int lane) {
     constexpr int NCOLA = PA * DR;
     constexpr int LDC = PAM * DL;
+    if constexpr (PREC == MLD_MIXED_TF32 && !CID && OKIND == K_DATA && !LAST && K >= 8 && DL >= 8 &&
+                  NCOLA >= 8) {
+        return gemm_tf32<K, PAM, DL, PA, DR, PB, NCOL, KQP>(C, A, M, w, par, lane);
+    }
     float mx = 0.f;
     if constexpr (LAST) {
         // alpha_d is summed (DR = 1, NCOL = 1): lanes over rows
@@ -201,7 +291,7 @@ __device__ __noinline__ void right_step(const float* __restrict__ Mq, const floa
     }
 }
 
-template <int D>
+template <int D, int PREC>
 struct Ctx {
     float* wts;
     float* mps;
@@ -213,8 +303,8 @@ struct Ctx {
     bool zero, bad;
 };
 
-template <int D, int C, int I>
-__device__ __forceinline__ void left_site(Ctx<D>& x) {
+template <int D, int PREC, int C, int I>
+__device__ __forceinline__ void left_site(Ctx<D, PREC>& x) {
     constexpr SiteStep st = PlanOf<D>::plan.steps[C * (D + 1) + I];
     if (x.zero || x.bad) return;
     float* cin = (I & 1) ? x.buf1 : x.buf0;
@@ -223,7 +313,7 @@ __device__ __forceinline__ void left_site(Ctx<D>& x) {
     const float4 w = I == 0 ? make_float4(1.f, 1.f, 1.f, 1.f)
                             : *reinterpret_cast<const float4*>(x.wts + 4 * ((I - 1) * D + C));
     float mx = left_step<st.K, st.pam, st.Dl, st.pa, st.Dr, st.pb, st.ncol, st.kq_prev, st.cid, st.okind,
-                         (I == D)>(cin, x.mps + st.offA, M, w, st.parity, x.lane);
+                         (I == D), PREC>(cin, x.mps + st.offA, M, w, st.parity, x.lane);
     mx = wmax(mx);
     if (!(mx < INFINITY)) { x.bad = true; return; }
     if (mx == 0.f) { x.zero = true; return; }
@@ -248,8 +338,8 @@ __host__ __device__ constexpr int carry_buffer() {
     return b;
 }
 
-template <int D, int C, int IDX>
-__device__ __forceinline__ void right_site(Ctx<D>& x) {
+template <int D, int PREC, int C, int IDX>
+__device__ __forceinline__ void right_site(Ctx<D, PREC>& x) {
     constexpr int I = D - IDX;
     constexpr SiteStep st = PlanOf<D>::plan.steps[C * (D + 1) + I];
     if (x.zero || x.bad) return;
@@ -261,20 +351,20 @@ __device__ __forceinline__ void right_site(Ctx<D>& x) {
     __syncwarp();
 }
 
-template <int D, int C, int... Is>
-__device__ __forceinline__ void column(Ctx<D>& x, std::integer_sequence<int, Is...>) {
-    (left_site<D, C, Is>(x), ...);
-    (right_site<D, C, Is>(x), ...);
+template <int D, int PREC, int C, int... Is>
+__device__ __forceinline__ void column(Ctx<D, PREC>& x, std::integer_sequence<int, Is...>) {
+    (left_site<D, PREC, C, Is>(x), ...);
+    (right_site<D, PREC, C, Is>(x), ...);
 }
 
-template <int D, int... Cs>
-__device__ __forceinline__ void all_columns(Ctx<D>& x, std::integer_sequence<int, Cs...>) {
-    (column<D, Cs>(x, std::make_integer_sequence<int, D + 1>{}), ...);
+template <int D, int PREC, int... Cs>
+__device__ __forceinline__ void all_columns(Ctx<D, PREC>& x, std::integer_sequence<int, Cs...>) {
+    (column<D, PREC, Cs>(x, std::make_integer_sequence<int, D + 1>{}), ...);
 }
 
 // contract the final MPS (corner column d) with all-ones vectors
-template <int D, int I>
-__device__ __forceinline__ void final_site(Ctx<D>& x) {
+template <int D, int PREC, int I>
+__device__ __forceinline__ void final_site(Ctx<D, PREC>& x) {
     constexpr SiteStep st = PlanOf<D>::plan.steps[(D - 1) * (D + 1) + I];
     const float* v = (I & 1) ? x.buf1 : x.buf0;
     float* vn = (I & 1) ? x.buf0 : x.buf1;
@@ -296,9 +386,9 @@ __device__ __forceinline__ void final_site(Ctx<D>& x) {
     __syncwarp();
 }
 
-template <int D, int... Is>
-__device__ __forceinline__ void final_all(Ctx<D>& x, std::integer_sequence<int, Is...>) {
-    (final_site<D, Is>(x), ...);
+template <int D, int PREC, int... Is>
+__device__ __forceinline__ void final_all(Ctx<D, PREC>& x, std::integer_sequence<int, Is...>) {
+    (final_site<D, PREC, Is>(x), ...);
 }
 
 // initial boundary MPS: all-ones product state over corner column 0
@@ -312,12 +402,12 @@ __host__ __device__ constexpr int init_offset() {
 template <int D, int I>
 __host__ __device__ constexpr int init_size() { return PlanOf<D>::plan.init_sizes[I]; }
 
-template <int D, int... Is>
-__device__ __forceinline__ void init_all(Ctx<D>& x, std::integer_sequence<int, Is...>) {
+template <int D, int PREC, int... Is>
+__device__ __forceinline__ void init_all(Ctx<D, PREC>& x, std::integer_sequence<int, Is...>) {
     ((x.lane < init_size<D, Is>() ? (void)(x.mps[init_offset<D, Is>() + x.lane] = 1.f) : (void)0), ...);
 }
 
-template <int D>
+template <int D, int PREC>
 __global__ void __launch_bounds__(256) decode_exact_kernel(ExactArgs a) {
     constexpr int FPW = PlanOf<D>::plan.floats_per_warp;
     constexpr int OFF_W = PlanOf<D>::plan.off_w, OFF_MPS = PlanOf<D>::plan.off_mps;
@@ -331,7 +421,7 @@ __global__ void __launch_bounds__(256) decode_exact_kernel(ExactArgs a) {
     const int64_t b = unit >> 2;
     const int cls = (int)(unit & 3);
     float* ws = reinterpret_cast<float*>(smem4) + (size_t)warp * FPW;
-    Ctx<D> x;
+    Ctx<D, PREC> x;
     x.wts = ws + OFF_W;
     x.mps = ws + OFF_MPS;
     x.buf0 = ws + OFF_B0;
@@ -374,14 +464,14 @@ __global__ void __launch_bounds__(256) decode_exact_kernel(ExactArgs a) {
             x.wts[4 * q + uv] = row[pidx];
         }
     }
-    init_all<D>(x, std::make_integer_sequence<int, D + 1>{});
+    init_all<D, PREC>(x, std::make_integer_sequence<int, D + 1>{});
     __syncwarp();
-    all_columns<D>(x, std::make_integer_sequence<int, D>{});
+    all_columns<D, PREC>(x, std::make_integer_sequence<int, D>{});
     double logz = -INFINITY;
     if (!x.zero && !x.bad) {
         if (lane == 0) x.buf0[0] = 1.f;
         __syncwarp();
-        final_all<D>(x, std::make_integer_sequence<int, D + 1>{});
+        final_all<D, PREC>(x, std::make_integer_sequence<int, D + 1>{});
         const float z = ((D + 1) & 1) ? x.buf1[0] : x.buf0[0];
         if (!(z == z)) x.bad = true;
         else if (z > 0.f) logz = log((double)z) + (double)x.e2 * 0.69314718055994530942;
@@ -392,17 +482,24 @@ __global__ void __launch_bounds__(256) decode_exact_kernel(ExactArgs a) {
     }
 }
 
-template <int D>
-bool launch_d(const ExactArgs& a, cudaStream_t s, int warps_per_block) {
+template <int D, int PREC>
+bool launch_dp(const ExactArgs& a, cudaStream_t s, int warps_per_block) {
     constexpr int FPW = PlanOf<D>::plan.floats_per_warp;
     const size_t smem = (size_t)FPW * sizeof(float) * warps_per_block;
-    if (cudaFuncSetAttribute(decode_exact_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(decode_exact_kernel<D, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
         return false;
     const int64_t units = 4 * a.B;
     const int64_t blocks = (units + warps_per_block - 1) / warps_per_block;
-    decode_exact_kernel<D><<<(unsigned)blocks, 32 * warps_per_block, smem, s>>>(a);
+    decode_exact_kernel<D, PREC><<<(unsigned)blocks, 32 * warps_per_block, smem, s>>>(a);
     return cudaGetLastError() == cudaSuccess;
+}
+
+template <int D>
+bool launch_d(const ExactArgs& a, cudaStream_t s, int warps_per_block, int precision) {
+    if (precision == MLD_MIXED_TF32) return launch_dp<D, MLD_MIXED_TF32>(a, s, warps_per_block);
+    if (precision == MLD_FP32) return launch_dp<D, MLD_FP32>(a, s, warps_per_block);
+    return false;
 }
 
 }  // namespace exact
@@ -418,13 +515,13 @@ int exact_floats_per_warp(int d) {
     return 0;
 }
 
-bool launch_exact(int d, const ExactArgs& a, cudaStream_t s, int warps_per_block) {
+bool launch_exact(int d, const ExactArgs& a, cudaStream_t s, int warps_per_block, int precision) {
     switch (d) {
-        case 3: return exact::launch_d<3>(a, s, warps_per_block);
-        case 5: return exact::launch_d<5>(a, s, warps_per_block);
-        case 7: return exact::launch_d<7>(a, s, warps_per_block);
-        case 9: return exact::launch_d<9>(a, s, warps_per_block);
-        case 11: return exact::launch_d<11>(a, s, warps_per_block);
+        case 3: return exact::launch_d<3>(a, s, warps_per_block, precision);
+        case 5: return exact::launch_d<5>(a, s, warps_per_block, precision);
+        case 7: return exact::launch_d<7>(a, s, warps_per_block, precision);
+        case 9: return exact::launch_d<9>(a, s, warps_per_block, precision);
+        case 11: return exact::launch_d<11>(a, s, warps_per_block, precision);
     }
     return false;
 }

@@ -17,9 +17,9 @@ struct ExactArgs {
 };
 
 // Distances with a specialised kernel (0 if none), its shared memory per warp
-// (floats), and the launch; false if d has no specialised kernel or the
-// launch failed.
+// (floats), and the launch (precision MLD_FP32 or MLD_MIXED_TF32); false if d
+// has no specialised kernel or the launch failed.
 int exact_floats_per_warp(int d);
-bool launch_exact(int d, const ExactArgs& a, cudaStream_t s, int warps_per_block);
+bool launch_exact(int d, const ExactArgs& a, cudaStream_t s, int warps_per_block, int precision);
 
 }  // namespace mld

@@ -106,7 +106,7 @@ extern "C" mld_status mld_decode_noalloc(const mld_code* C, const float* noise, 
     ea.status = reinterpret_cast<int*>(scratch);
     ea.B = B;
     ea.noise_mode = noise_mode;
-    if (!mld::launch_exact(C->d, ea, s, W)) return MLD_ERR_CUDA;
+    if (!mld::launch_exact(C->d, ea, s, W, MLD_FP32)) return MLD_ERR_CUDA;
     if (argmax) {
         noalloc_argmax<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(logP, argmax, B);
         if (cudaGetLastError() != cudaSuccess) return MLD_ERR_CUDA;

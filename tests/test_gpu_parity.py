@@ -209,3 +209,30 @@ def test_full_size_bench_config_sampled(mld):
     ref, _ = oracle.decode(d, noise, syn[idx])
     np.testing.assert_allclose(lp[idx], ref, rtol=0, atol=TOL)
     check_argmax(am[idx], ref)
+
+
+@pytest.mark.parametrize("d,chi", [(5, 4), (7, 8), (9, 32), (11, 32)])
+def test_mixed_tf32_vs_oracle_and_fp32(mld, d, chi):
+    """Mixed precision (split-TF32 tensor-core products, FP32 accumulate):
+    within 1e-5 of the oracle and of the FP32 path on every coset."""
+    n = d * d
+    noise = synth.depolarizing(n, 0.12).astype(np.float32)
+    E = synth.sample_errors(d, noise, 200, seed=31)
+    syn = synth.syndromes_of(d, E)
+    ref, _ = oracle.decode(d, noise, syn)
+    lp32, _ = gpu_decode(mld, d, noise, syn, chi)
+    lpm, am = gpu_decode(mld, d, noise, syn, chi, precision=mld.MLD_MIXED_TF32)
+    np.testing.assert_allclose(lpm, ref, rtol=0, atol=TOL)
+    np.testing.assert_allclose(lpm, lp32, rtol=0, atol=TOL)
+    check_argmax(am, ref)
+
+
+def test_mixed_unsupported_cases(mld):
+    d, n = 9, 81
+    C = code(mld, d)
+    nz = torch.tensor(synth.depolarizing(n, 0.1).astype(np.float32), device="cuda")
+    sy = torch.zeros((4, C.words), dtype=torch.int64, device="cuda")
+    for chi, prec in [(32, mld.MLD_MIXED_BF16), (8, mld.MLD_MIXED_TF32)]:
+        with pytest.raises(mld.MldError) as e:
+            C.decode(nz, sy, chi, prec)
+        assert e.value.status == 2
