@@ -34,6 +34,7 @@ constexpr float kJacobiTol = 1.0e-5f;   // above the ~L*eps noise floor of FP32 
 
 struct DecodeArgs {
     const SiteStep* steps;
+    float* gws;                // global workspace (nullptr: shared memory)
     const uint64_t* dmask;     // [n][2][words]
     const float* noise;
     const uint64_t* syn;
@@ -311,16 +312,12 @@ __device__ bool jacobi(float* X, int L, int ldx, int nv, float* acc, int lane) {
 }
 
 // ------------------------------------------------------------------ kernel
-__global__ void __launch_bounds__(32 * kMaxWarpsPerBlock)
-decode_fp32_kernel(DecodeArgs a) {
-    extern __shared__ float4 smem4[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t unit = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (unit >= 4 * a.B) return;
+// One (syndrome, class) unit on one warp, with its state at ws (shared
+// memory, or this warp's slice of the global workspace).
+__device__ __forceinline__ void decode_unit(const DecodeArgs& a, float* ws, int64_t unit, int lane) {
     const int64_t b = unit >> 2;
     const int cls = (int)(unit & 3);
     const int d = a.d, n = a.n;
-    float* ws = reinterpret_cast<float*>(smem4) + (size_t)warp * a.per_warp;
     float* wts = ws + a.off_w;
     float* mps = ws + a.off_mps;
     float* qst = ws + a.off_q;
@@ -564,6 +561,28 @@ decode_fp32_kernel(DecodeArgs a) {
     }
 }
 
+// Shared-memory mode: one unit per warp. Global-workspace mode (a.gws set,
+// for states larger than a block's shared memory): a fixed set of resident
+// warps, each with its own slice of the workspace, strides over the units.
+template <bool GLOBAL>
+__global__ void __launch_bounds__(32 * kMaxWarpsPerBlock)
+decode_fp32_kernel(DecodeArgs a) {
+    extern __shared__ float4 smem4[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    if constexpr (GLOBAL) {
+        const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+        float* ws = a.gws + (size_t)gw * a.per_warp;
+        for (int64_t unit = gw; unit < 4 * a.B; unit += nw) {
+            decode_unit(a, ws, unit, lane);
+            __syncwarp();
+        }
+    } else {
+        if (gw >= 4 * a.B) return;
+        decode_unit(a, reinterpret_cast<float*>(smem4) + (size_t)warp * a.per_warp, gw, lane);
+    }
+}
+
 __global__ void argmax_kernel(const double* __restrict__ logP, uint8_t* __restrict__ am, int64_t B) {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
@@ -650,6 +669,7 @@ void mld_code_destroy(mld_code* C) {
         cudaFree(C->d_dmask);
         cudaFree(C->d_status);
         cudaFree(C->h_stage_dev);
+        cudaFree(C->d_gws);
     }
     delete C;
 }
@@ -732,19 +752,45 @@ mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, co
     // (TF32 tensor-core products); BF16 and truncating chi run FP32 only
     if (precision == MLD_MIXED_BF16 || (precision == MLD_MIXED_TF32 && !exact)) return MLD_ERR_UNSUPPORTED;
     const size_t pw = (size_t)(exact ? mld::exact_floats_per_warp(C->d) : P.floats_per_warp) * sizeof(float);
-    if (pw > (size_t)max_optin) return MLD_ERR_UNSUPPORTED;
-    // warps per CTA: the most resident warps per SM (32 CTAs and 64 warps
-    // per SM at most, 1 KB of shared memory reserved per CTA), fewest warps
-    // per CTA on ties
-    int W = 1, best = 0;
-    for (int w = 1; w <= mld::kMaxWarpsPerBlock; ++w) {
-        if (pw * w > (size_t)max_optin) break;
-        int ctas = (int)((size_t)per_sm / (pw * w + 1024));
-        ctas = ctas < 32 ? ctas : 32;
-        int warps = ctas * w < 64 ? ctas * w : 64;
-        if (warps > best) { best = warps; W = w; }
+    const int64_t units = 4 * B;
+    int W = 1;
+    float* gws = nullptr;
+    int64_t gws_warps = 0;
+    if (pw > (size_t)max_optin) {
+        // state larger than a block's shared memory: persistent warps with
+        // global-memory workspaces (16 resident warps per SM, halved until
+        // the workspace is at most 8 GiB)
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MLD_ERR_CUDA;
+        W = 4;
+        int64_t nw = (int64_t)sms * 16;
+        while (nw > (int64_t)sms * W && (size_t)nw * pw > ((size_t)8 << 30)) nw /= 2;
+        const int64_t need = ((units + W - 1) / W) * W;
+        if (nw > need) nw = need;
+        const size_t bytes = (size_t)nw * pw;
+        if (bytes > C->gws_bytes) {
+            cudaFree(C->d_gws);
+            C->d_gws = nullptr;
+            C->gws_bytes = 0;
+            if (cudaMalloc(&C->d_gws, bytes) != cudaSuccess) return MLD_ERR_NOMEM;
+            C->gws_bytes = bytes;
+        }
+        gws = C->d_gws;
+        gws_warps = nw;
+    } else {
+        // warps per CTA: the most resident warps per SM (32 CTAs and 64 warps
+        // per SM at most, 1 KB of shared memory reserved per CTA), fewest
+        // warps per CTA on ties
+        int best = 0;
+        for (int w = 1; w <= mld::kMaxWarpsPerBlock; ++w) {
+            if (pw * w > (size_t)max_optin) break;
+            int ctas = (int)((size_t)per_sm / (pw * w + 1024));
+            ctas = ctas < 32 ? ctas : 32;
+            int warps = ctas * w < 64 ? ctas * w : 64;
+            if (warps > best) { best = warps; W = w; }
+        }
     }
-    const size_t smem = pw * W;
+    const size_t smem = gws ? 0 : pw * W;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (exact) {
         mld::ExactArgs ea;
@@ -755,6 +801,8 @@ mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, co
         ea.status = C->d_status;
         ea.B = B;
         ea.noise_mode = noise_mode;
+        ea.gws = gws;
+        ea.gws_warps = gws_warps;
         if (!mld::launch_exact(C->d, ea, s, W, precision)) return MLD_ERR_CUDA;
         if (argmax) {
             mld::argmax_kernel<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(logP, argmax, B);
@@ -762,13 +810,14 @@ mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, co
         }
         return MLD_OK;
     }
-    if (cudaFuncSetAttribute(mld::decode_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+    auto kern = gws ? mld::decode_fp32_kernel<true> : mld::decode_fp32_kernel<false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return MLD_ERR_CUDA;
-    const int64_t units = 4 * B;
-    const int64_t blocks = (units + W - 1) / W;
+    a.gws = gws;
+    int64_t blocks = (units + W - 1) / W;
+    if (gws && blocks > gws_warps / W) blocks = gws_warps / W;
     if (blocks > 0x7fffffff) return MLD_ERR_UNSUPPORTED;
-    mld::decode_fp32_kernel<<<(unsigned)blocks, 32 * W, smem, s>>>(a);
+    kern<<<(unsigned)blocks, 32 * W, smem, s>>>(a);
     if (cudaGetLastError() != cudaSuccess) return MLD_ERR_CUDA;
     if (argmax) {
         mld::argmax_kernel<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(logP, argmax, B);

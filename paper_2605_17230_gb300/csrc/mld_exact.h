@@ -14,6 +14,8 @@ struct ExactArgs {
     int* status;
     int64_t B;
     int noise_mode;
+    float* gws = nullptr;      // global workspace of gws_warps slices (nullptr: shared memory)
+    int64_t gws_warps = 0;
 };
 
 // Distances with a specialised kernel (0 if none), its shared memory per warp

@@ -1,0 +1,533 @@
+#pragma once
+// Kernel templates of the boundary-MPS sweep at untruncated bond dimension, specialised at compile
+// time on the shape plan of distance d (sm_103a, FP32).
+//
+// When chi is at least the exact bond of every cut (2^floor(d/2) in this
+// layout) no singular value is ever discarded (Sec. 3.2.1: the truncation
+// keeps min(chi, #values)), every column is kept in the non-negative gauge
+// (no QR, no SVD) and the shape of every step is a function of d alone. This
+// kernel instantiates each site step of that plan as a template on its
+// shapes (bond dimensions, block counts, site kinds), so index arithmetic is
+// folded at compile time and identity sites cost no multiplications. The
+// arithmetic is the same as the runtime-plan kernel's: MPO.MPS products per
+// beta block, power-of-two renormalisation per site, bond-matrix products in
+// the right sweep, contraction with all-ones vectors at the end.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <utility>
+
+#include "mld_exact.h"
+#include "mld_internal.h"
+
+namespace mld {
+namespace exact {
+
+constexpr int kExactChi = 1 << 20;
+
+template <int D>
+struct PlanOf {
+    static constexpr Plan plan = make_plan(D, kExactChi);
+};
+
+__device__ __forceinline__ float wmax(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// w(a, a', b, b') of the qubit factor, from its four weights p[E xor X^u Z^v]
+// indexed u + 2v; parity selects which plaquette pair carries u.
+__device__ __forceinline__ float wsel(const float4 w, int par, int a, int ap, int b, int bp) {
+    const int x1 = a ^ bp, x2 = ap ^ b;
+    const int u = par ? x2 : x1, v = par ? x1 : x2;
+    const int idx = u | (v << 1);
+    return idx == 0 ? w.x : idx == 1 ? w.y : idx == 2 ? w.z : w.w;
+}
+
+// X_a[k][col] = sum_r C[k][a*DL + r] A[r][col] for the identity cases
+// (identity carry and/or identity old site), where the sum has one term.
+template <int DL, int DR, int PAM, int NCOLA, int KQP, int CID, int OKIND>
+__device__ __forceinline__ void x_ident(const float* C, const float* A, int k, int ap, int rp, float X[2]) {
+    constexpr int LDC = PAM * DL;
+    X[0] = 0.f;
+    X[1] = 0.f;
+    if constexpr (CID) {
+        const int j = k % KQP, ja = j / DL, jr = j % DL;
+        float av;
+        if constexpr (OKIND == K_DATA) av = A[jr * NCOLA + ap * DR + rp];
+        else if constexpr (OKIND == K_IDR) av = (jr == ap * DR + rp) ? 1.f : 0.f;
+        else av = (rp == ap * DL + jr) ? 1.f : 0.f;
+        if (ja == 0) X[0] = av; else X[1] = av;
+    } else {
+#pragma unroll
+        for (int a = 0; a < PAM; ++a) {
+            const float* crow = C + k * LDC + a * DL;
+            if constexpr (OKIND == K_IDR) {
+                X[a] = crow[ap * DR + rp];
+            } else {
+                const int r = rp - ap * DL;
+                X[a] = (r >= 0 && r < DL) ? crow[r] : 0.f;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned to_tf32(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// D += A(16x8) B(8x8) on the tensor cores, TF32 operands, FP32 accumulate.
+// Fragments (g = lane/4, t = lane%4): A rows g, g+8 x cols t, t+4; B rows
+// t, t+4 x col g; D rows g, g+8 x cols 2t, 2t+1.
+__device__ __forceinline__ void mma_tf32(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Split x into TF32 parts hi + lo (hi = x rounded to TF32, lo = the
+// rounded remainder): products of the parts recover ~FP32 accuracy.
+__device__ __forceinline__ void split_tf32(float x, unsigned& hi, unsigned& lo) {
+    hi = to_tf32(x);
+    lo = to_tf32(x - __uint_as_float(hi));
+}
+
+// The data-site product of the mixed-precision path: X_a = C_a A on the
+// tensor cores, TF32 operands and FP32 accumulation, each operand split
+// into TF32 hi + lo and the product taken as hi.hi + hi.lo + lo.hi (the
+// lo.lo term is below FP32 rounding). One 16-row block of k for both a at
+// a time, then the FP32 qubit-factor epilogue
+// M^{b'}[k][col] = sum_a w(a, a', beta, b') X_a[k][col].
+template <int K, int PAM, int DL, int PA, int DR, int PB, int NCOL, int KQP>
+__device__ __forceinline__ float gemm_tf32(const float* __restrict__ C, const float* __restrict__ A,
+                                           float* __restrict__ M, const float4 w, int par, int lane) {
+    constexpr int NCOLA = PA * DR;
+    constexpr int LDC = PAM * DL;
+    static_assert(DL % 8 == 0 && NCOLA % 8 == 0, "tensor-core tile shape");
+    const int g = lane >> 2, t = lane & 3;
+    float mx = 0.f;
+    for (int kb = 0; kb < (K + 15) / 16; ++kb) {
+        const int r0 = kb * 16 + g, r1 = r0 + 8;
+#pragma unroll
+        for (int nt = 0; nt < NCOLA / 8; ++nt) {
+            float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+            for (int ks = 0; ks < DL; ks += 8) {
+                unsigned bh0, bl0, bh1, bl1;
+                split_tf32(A[(ks + t) * NCOLA + nt * 8 + g], bh0, bl0);
+                split_tf32(A[(ks + t + 4) * NCOLA + nt * 8 + g], bh1, bl1);
+#pragma unroll
+                for (int a = 0; a < PAM; ++a) {
+                    const float* c0 = C + r0 * LDC + a * DL + ks;
+                    const float* c1 = C + r1 * LDC + a * DL + ks;
+                    unsigned ah[4], al[4];
+                    split_tf32(r0 < K ? c0[t] : 0.f, ah[0], al[0]);
+                    split_tf32(r1 < K ? c1[t] : 0.f, ah[1], al[1]);
+                    split_tf32(r0 < K ? c0[t + 4] : 0.f, ah[2], al[2]);
+                    split_tf32(r1 < K ? c1[t + 4] : 0.f, ah[3], al[3]);
+                    mma_tf32(acc[a], al[0], al[1], al[2], al[3], bh0, bh1);
+                    mma_tf32(acc[a], ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+                    mma_tf32(acc[a], ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = kb * 16 + g + 8 * h;
+                if (k >= K) continue;
+                const int beta = k / KQP;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int col = nt * 8 + 2 * t + e, ap = col / DR;
+                    const float x0 = acc[0][2 * h + e], x1 = PAM == 2 ? acc[1][2 * h + e] : 0.f;
+#pragma unroll
+                    for (int bp = 0; bp < PB; ++bp) {
+                        const float o = fmaf(wsel(w, par, 0, ap, beta, bp), x0, wsel(w, par, 1, ap, beta, bp) * x1);
+                        M[(bp * K + k) * NCOL + col] = o;
+                        mx = fmaxf(mx, fabsf(o));
+                    }
+                }
+            }
+        }
+    }
+    return mx;
+}
+
+// One left-sweep site: M^{b'}[k][col] = sum_a w(a, a', beta(k), b') X_a[k][col].
+// Returns this lane's max |M|.
+template <int K, int PAM, int DL, int PA, int DR, int PB, int NCOL, int KQP, int CID, int OKIND, int LAST,
+          int PREC>
+__device__ __noinline__ float left_step(const float* __restrict__ C, const float* __restrict__ A,
+                                        float* __restrict__ M, const float4 w, int par, int lane) {
+    constexpr int NCOLA = PA * DR;
+    constexpr int LDC = PAM * DL;
+    if constexpr (PREC == MLD_MIXED_TF32 && !CID && OKIND == K_DATA && !LAST && K >= 8 && DL >= 8 &&
+                  NCOLA >= 8) {
+        return gemm_tf32<K, PAM, DL, PA, DR, PB, NCOL, KQP>(C, A, M, w, par, lane);
+    }
+    float mx = 0.f;
+    if constexpr (LAST) {
+        // alpha_d is summed (DR = 1, NCOL = 1): lanes over rows
+        for (int k = lane; k < K; k += 32) {
+            const int beta = k / KQP;
+            float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+            for (int ap = 0; ap < PA; ++ap) {
+                float X[2];
+                if constexpr (!CID && OKIND == K_DATA) {
+#pragma unroll
+                    for (int a = 0; a < 2; ++a) {
+                        float s = 0.f;
+                        if (a < PAM) {
+                            const float* crow = C + k * LDC + a * DL;
+#pragma unroll
+                            for (int r = 0; r < DL; ++r) s = fmaf(crow[r], A[r * NCOLA + ap], s);
+                        }
+                        X[a] = s;
+                    }
+                } else {
+                    x_ident<DL, DR, PAM, NCOLA, KQP, CID, OKIND>(C, A, k, ap, 0, X);
+                }
+                acc0 = fmaf(wsel(w, par, 0, ap, beta, 0), X[0], fmaf(wsel(w, par, 1, ap, beta, 0), X[1], acc0));
+                if (PB == 2)
+                    acc1 = fmaf(wsel(w, par, 0, ap, beta, 1), X[0], fmaf(wsel(w, par, 1, ap, beta, 1), X[1], acc1));
+            }
+            M[k] = acc0;
+            mx = fmaxf(mx, fabsf(acc0));
+            if (PB == 2) {
+                M[K + k] = acc1;
+                mx = fmaxf(mx, fabsf(acc1));
+            }
+        }
+        return mx;
+    }
+    static_assert((NCOLA & (NCOLA - 1)) == 0, "power-of-two columns");
+    constexpr int RG = NCOLA >= 32 ? 1 : 32 / NCOLA;     // row groups across the warp
+    constexpr int CPL = NCOLA >= 32 ? NCOLA / 32 : 1;    // columns per lane
+    const int rg = lane / (32 / RG);
+    const int cl = lane % (32 / RG);
+#pragma unroll
+    for (int cidx = 0; cidx < CPL; ++cidx) {
+        const int col = cl + 32 * cidx;
+        if (col >= NCOLA) continue;
+        const int ap = col / DR, rp = col % DR;
+        if constexpr (!CID && OKIND == K_DATA) {
+            // a real GEMM: this lane's column of A in registers
+            float acol[DL];
+#pragma unroll
+            for (int r = 0; r < DL; ++r) acol[r] = A[r * NCOLA + col];
+            for (int k = rg; k < K; k += RG) {
+                const float* c0 = C + k * LDC;
+                float x0 = 0.f, x1 = 0.f;
+#pragma unroll
+                for (int r = 0; r < DL; ++r) {
+                    x0 = fmaf(c0[r], acol[r], x0);
+                    if (PAM == 2) x1 = fmaf(c0[DL + r], acol[r], x1);
+                }
+                const int beta = k / KQP;
+#pragma unroll
+                for (int bp = 0; bp < PB; ++bp) {
+                    const float o = fmaf(wsel(w, par, 0, ap, beta, bp), x0, wsel(w, par, 1, ap, beta, bp) * x1);
+                    M[(bp * K + k) * NCOL + col] = o;
+                    mx = fmaxf(mx, fabsf(o));
+                }
+            }
+        } else {
+            for (int k = rg; k < K; k += RG) {
+                float X[2];
+                x_ident<DL, DR, PAM, NCOLA, KQP, CID, OKIND>(C, A, k, ap, rp, X);
+                const int beta = k / KQP;
+#pragma unroll
+                for (int bp = 0; bp < PB; ++bp) {
+                    const float o = fmaf(wsel(w, par, 0, ap, beta, bp), X[0], wsel(w, par, 1, ap, beta, bp) * X[1]);
+                    M[(bp * K + k) * NCOL + col] = o;
+                    mx = fmaxf(mx, fabsf(o));
+                }
+            }
+        }
+    }
+    return mx;
+}
+
+// One right-sweep site: T (ROWS x PB*S) from the kept block M (TALL) or the
+// carry G, then IDENT (carry = T, written to t) or DENSE (site = T, written
+// straight into the MPS buffer; carry = identity).
+template <int ROWS, int S, int PB, int KQ, int NC, int TALL, int GID, int RMODE, int NKIND>
+__device__ __noinline__ void right_step(const float* __restrict__ Mq, const float* __restrict__ g,
+                                        float* __restrict__ t, float* __restrict__ site, int lane) {
+    if constexpr (NKIND == K_IDL) {
+        return;                                   // identity site, identity carry: nothing to form
+    } else {
+        constexpr int COLS = PB * S;
+        float* dst = (RMODE == R_DENSE) ? site : t;
+        for (int e = lane; e < ROWS * COLS; e += 32) {
+            const int r = e / COLS, cc = e % COLS, bb = cc / S, s = cc % S;
+            float v;
+            if constexpr (TALL) {
+                const float* mrow = Mq + (bb * ROWS + r) * NC;
+                if constexpr (GID == 2) {
+                    v = mrow[s];
+                } else if constexpr (GID == 1) {
+                    const int j = s - bb * KQ;
+                    v = (j >= 0 && j < NC) ? mrow[j] : 0.f;
+                } else {
+                    const float* gcol = g + (bb * KQ) * S + s;
+                    v = 0.f;
+#pragma unroll
+                    for (int j = 0; j < NC; ++j) v = fmaf(mrow[j], gcol[j * S], v);
+                }
+            } else {
+                const int grow = bb * ROWS + r;
+                if constexpr (GID) v = (grow == s) ? 1.f : 0.f;
+                else v = g[grow * S + s];
+            }
+            dst[e] = v;
+        }
+    }
+}
+
+template <int D, int PREC>
+struct Ctx {
+    float* wts;
+    float* mps;
+    float* buf0;
+    float* buf1;
+    float* qst;
+    int lane;
+    int e2;
+    bool zero, bad;
+};
+
+template <int D, int PREC, int C, int I>
+__device__ __forceinline__ void left_site(Ctx<D, PREC>& x) {
+    constexpr SiteStep st = PlanOf<D>::plan.steps[C * (D + 1) + I];
+    if (x.zero || x.bad) return;
+    float* cin = (I & 1) ? x.buf1 : x.buf0;
+    float* cout = (I & 1) ? x.buf0 : x.buf1;
+    float* M = st.tall ? x.qst + st.offQ : cout;
+    const float4 w = I == 0 ? make_float4(1.f, 1.f, 1.f, 1.f)
+                            : *reinterpret_cast<const float4*>(x.wts + 4 * ((I - 1) * D + C));
+    float mx = left_step<st.K, st.pam, st.Dl, st.pa, st.Dr, st.pb, st.ncol, st.kq_prev, st.cid, st.okind,
+                         (I == D), PREC>(cin, x.mps + st.offA, M, w, st.parity, x.lane);
+    mx = wmax(mx);
+    if (!(mx < INFINITY)) { x.bad = true; return; }
+    if (mx == 0.f) { x.zero = true; return; }
+    int ex;
+    frexpf(mx, &ex);
+    if (ex > 126 || ex < -125) { x.bad = true; return; }
+    const float sc = __int_as_float((127 - ex) << 23);
+    constexpr int LEN = st.pb * st.K * st.ncol;
+    __syncwarp();
+    for (int e = x.lane; e < LEN; e += 32) M[e] *= sc;
+    x.e2 += ex;
+    __syncwarp();
+}
+
+// buffer that holds the right-sweep carry at site I: the left sweep leaves
+// its last carry in the cout of site D; every IDENT step swaps carry and T
+template <int D, int C, int I>
+__host__ __device__ constexpr int carry_buffer() {
+    int b = (D & 1) ? 0 : 1;
+    for (int i = D; i > I; --i)
+        if (PlanOf<D>::plan.steps[C * (D + 1) + i].rmode == R_IDENT) b ^= 1;
+    return b;
+}
+
+template <int D, int PREC, int C, int IDX>
+__device__ __forceinline__ void right_site(Ctx<D, PREC>& x) {
+    constexpr int I = D - IDX;
+    constexpr SiteStep st = PlanOf<D>::plan.steps[C * (D + 1) + I];
+    if (x.zero || x.bad) return;
+    constexpr int gb = carry_buffer<D, C, I>();
+    float* g = gb ? x.buf1 : x.buf0;
+    float* t = gb ? x.buf0 : x.buf1;
+    right_step<st.K, st.S, st.pb, st.kq, st.ncol, st.tall, st.gid, st.rmode, st.nkind>(
+        x.qst + st.offQ, g, t, x.mps + st.offN, x.lane);
+    __syncwarp();
+}
+
+template <int D, int PREC, int C, int... Is>
+__device__ __forceinline__ void column(Ctx<D, PREC>& x, std::integer_sequence<int, Is...>) {
+    (left_site<D, PREC, C, Is>(x), ...);
+    (right_site<D, PREC, C, Is>(x), ...);
+}
+
+template <int D, int PREC, int... Cs>
+__device__ __forceinline__ void all_columns(Ctx<D, PREC>& x, std::integer_sequence<int, Cs...>) {
+    (column<D, PREC, Cs>(x, std::make_integer_sequence<int, D + 1>{}), ...);
+}
+
+// contract the final MPS (corner column d) with all-ones vectors
+template <int D, int PREC, int I>
+__device__ __forceinline__ void final_site(Ctx<D, PREC>& x) {
+    constexpr SiteStep st = PlanOf<D>::plan.steps[(D - 1) * (D + 1) + I];
+    const float* v = (I & 1) ? x.buf1 : x.buf0;
+    float* vn = (I & 1) ? x.buf0 : x.buf1;
+    const float* site = x.mps + st.offN;
+    for (int s = x.lane; s < st.S; s += 32) {
+        float acc = 0.f;
+        if constexpr (st.nkind == K_IDR) {
+#pragma unroll
+            for (int bb = 0; bb < st.pb; ++bb) acc += v[bb * st.S + s];
+        } else if constexpr (st.nkind == K_IDL) {
+            acc = v[s % st.Sl];
+        } else {
+            for (int sl = 0; sl < st.Sl; ++sl)
+#pragma unroll
+                for (int bb = 0; bb < st.pb; ++bb) acc = fmaf(v[sl], site[(sl * st.pb + bb) * st.S + s], acc);
+        }
+        vn[s] = acc;
+    }
+    __syncwarp();
+}
+
+template <int D, int PREC, int... Is>
+__device__ __forceinline__ void final_all(Ctx<D, PREC>& x, std::integer_sequence<int, Is...>) {
+    (final_site<D, PREC, Is>(x), ...);
+}
+
+// initial boundary MPS: all-ones product state over corner column 0
+template <int D, int I>
+__host__ __device__ constexpr int init_offset() {
+    int o = 0;
+    for (int i = 0; i < I; ++i) o += (PlanOf<D>::plan.init_sizes[i] + 3) & ~3;
+    return o;
+}
+
+template <int D, int I>
+__host__ __device__ constexpr int init_size() { return PlanOf<D>::plan.init_sizes[I]; }
+
+template <int D, int PREC, int... Is>
+__device__ __forceinline__ void init_all(Ctx<D, PREC>& x, std::integer_sequence<int, Is...>) {
+    ((x.lane < init_size<D, Is>() ? (void)(x.mps[init_offset<D, Is>() + x.lane] = 1.f) : (void)0), ...);
+}
+
+template <int D, int PREC>
+__device__ __forceinline__ void decode_unit(const ExactArgs& a, float* ws, int64_t unit, int lane);
+
+// Shared-memory mode: one unit per warp. Global-workspace mode (a.gws set,
+// for states larger than a block's shared memory): a fixed set of resident
+// warps, each with its own slice of the workspace, strides over the units.
+template <int D, int PREC, bool GLOBAL>
+__global__ void __launch_bounds__(256) decode_exact_kernel(ExactArgs a) {
+    constexpr int FPW = PlanOf<D>::plan.floats_per_warp;
+    extern __shared__ float4 smem4[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    if constexpr (GLOBAL) {
+        const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+        float* ws = a.gws + (size_t)gw * FPW;
+        for (int64_t unit = gw; unit < 4 * a.B; unit += nw) {
+            decode_unit<D, PREC>(a, ws, unit, lane);
+            __syncwarp();
+        }
+    } else {
+        if (gw >= 4 * a.B) return;
+        decode_unit<D, PREC>(a, reinterpret_cast<float*>(smem4) + (size_t)warp * FPW, gw, lane);
+    }
+}
+
+template <int D, int PREC>
+__device__ __forceinline__ void decode_unit(const ExactArgs& a, float* ws, int64_t unit, int lane) {
+    constexpr int OFF_W = PlanOf<D>::plan.off_w, OFF_MPS = PlanOf<D>::plan.off_mps;
+    constexpr int OFF_B0 = PlanOf<D>::plan.off_buf0, OFF_B1 = PlanOf<D>::plan.off_buf1;
+    constexpr int OFF_Q = PlanOf<D>::plan.off_q;
+    constexpr int n = D * D;
+    const int64_t b = unit >> 2;
+    const int cls = (int)(unit & 3);
+    Ctx<D, PREC> x;
+    x.wts = ws + OFF_W;
+    x.mps = ws + OFF_MPS;
+    x.buf0 = ws + OFF_B0;
+    x.buf1 = ws + OFF_B1;
+    x.qst = ws + OFF_Q;
+    x.lane = lane;
+    x.e2 = 0;
+    x.zero = false;
+    x.bad = false;
+
+    // pure error f(s) = prod_{s_k=1} T_k, representative E_{l,s} =
+    // f X_L^{l_X} Z_L^{l_Z}, and the four weights of every qubit factor
+    constexpr int W = (n - 1 + 63) / 64;
+    uint64_t sw[W];
+#pragma unroll
+    for (int u = 0; u < W; ++u) sw[u] = a.syn[b * W + u];
+    for (int q = lane; q < n; q += 32) {
+        int xb = 0, zb = 0;
+        const uint64_t* mk = a.dmask + (size_t)q * 2 * W;
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            xb ^= __popcll(sw[u] & mk[u]) & 1;
+            zb ^= __popcll(sw[u] & mk[W + u]) & 1;
+        }
+        const int r = q / D, c = q % D;
+        if ((cls & 1) && c == 0) xb ^= 1;
+        if ((cls & 2) && r == 0) zb ^= 1;
+        float row[4];
+        if (a.noise_mode == MLD_NOISE_TABLE) {
+            const float4 v = *reinterpret_cast<const float4*>(a.noise + 4 * (size_t)q);
+            row[0] = v.x; row[1] = v.y; row[2] = v.z; row[3] = v.w;
+        } else {
+            const float p = a.noise[b];
+            row[0] = 1.f - p; row[1] = row[2] = row[3] = p * (1.f / 3.f);
+        }
+#pragma unroll
+        for (int uv = 0; uv < 4; ++uv) {
+            const int xx = xb ^ (uv & 1), zz = zb ^ (uv >> 1);
+            const int pidx = (!xx && !zz) ? 0 : (xx && !zz) ? 1 : (xx && zz) ? 2 : 3;
+            x.wts[4 * q + uv] = row[pidx];
+        }
+    }
+    init_all<D, PREC>(x, std::make_integer_sequence<int, D + 1>{});
+    __syncwarp();
+    all_columns<D, PREC>(x, std::make_integer_sequence<int, D>{});
+    double logz = -INFINITY;
+    if (!x.zero && !x.bad) {
+        if (lane == 0) x.buf0[0] = 1.f;
+        __syncwarp();
+        final_all<D, PREC>(x, std::make_integer_sequence<int, D + 1>{});
+        const float z = ((D + 1) & 1) ? x.buf1[0] : x.buf0[0];
+        if (!(z == z)) x.bad = true;
+        else if (z > 0.f) logz = log((double)z) + (double)x.e2 * 0.69314718055994530942;
+    }
+    if (lane == 0) {
+        a.logP[b * 4 + cls] = logz;
+        if (x.bad) atomicOr(a.status, 1 << MLD_ERR_NUMERIC);
+    }
+}
+
+// States up to this many floats per warp run from shared memory; larger
+// ones (d >= 13) from the global workspace.
+constexpr int kSharedFloatsMax = (227 * 1024) / 4;
+
+template <int D, int PREC>
+bool launch_dp(const ExactArgs& a, cudaStream_t s, int warps_per_block) {
+    constexpr int FPW = PlanOf<D>::plan.floats_per_warp;
+    constexpr bool GLOBAL = FPW > kSharedFloatsMax;
+    if (GLOBAL != (a.gws != nullptr)) return false;
+    const size_t smem = GLOBAL ? 0 : (size_t)FPW * sizeof(float) * warps_per_block;
+    if (cudaFuncSetAttribute(decode_exact_kernel<D, PREC, GLOBAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return false;
+    const int64_t units = 4 * a.B;
+    int64_t blocks = (units + warps_per_block - 1) / warps_per_block;
+    if (GLOBAL && blocks > a.gws_warps / warps_per_block) blocks = a.gws_warps / warps_per_block;
+    decode_exact_kernel<D, PREC, GLOBAL><<<(unsigned)blocks, 32 * warps_per_block, smem, s>>>(a);
+    return cudaGetLastError() == cudaSuccess;
+}
+
+template <int D>
+bool launch_d(const ExactArgs& a, cudaStream_t s, int warps_per_block, int precision) {
+    if (precision == MLD_MIXED_TF32) return launch_dp<D, MLD_MIXED_TF32>(a, s, warps_per_block);
+    if (precision == MLD_FP32) return launch_dp<D, MLD_FP32>(a, s, warps_per_block);
+    return false;
+}
+
+}  // namespace exact
+}  // namespace mld

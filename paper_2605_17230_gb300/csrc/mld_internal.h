@@ -26,4 +26,7 @@ struct mld_code {
     // host-API staging
     void* h_stage_dev = nullptr;
     size_t h_stage_bytes = 0;
+    // global workspace for states larger than a block's shared memory
+    float* d_gws = nullptr;
+    size_t gws_bytes = 0;
 };

@@ -236,3 +236,44 @@ def test_mixed_unsupported_cases(mld):
         with pytest.raises(mld.MldError) as e:
             C.decode(nz, sy, chi, prec)
         assert e.value.status == 2
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_d13_exact_global_workspace(mld, prec):
+    """d=13 at chi=64 (untruncated): the state no longer fits a block's shared
+    memory, so the persistent global-workspace mode runs; exact parity."""
+    d, n = 13, 169
+    noise = synth.depolarizing(n, 0.10).astype(np.float32)
+    E = synth.sample_errors(d, noise, 48, seed=13)
+    syn = synth.syndromes_of(d, E)
+    ref, _ = oracle.decode(d, noise, syn)
+    lp, am = gpu_decode(mld, d, noise, syn, 64, precision=prec)
+    np.testing.assert_allclose(lp, ref, rtol=0, atol=TOL)
+    check_argmax(am, ref)
+
+
+def test_d13_truncated_global_workspace_vs_fp64_mps(mld):
+    d, n, chi = 13, 169, 32
+    noise = synth.depolarizing(n, 0.10).astype(np.float32)
+    E = synth.sample_errors(d, noise, 2, seed=17)
+    syn = synth.syndromes_of(d, E)
+    ref = omps.decode_mps(d, noise.astype(np.float64), syn, chi)
+    lp, _ = gpu_decode(mld, d, noise, syn, chi)
+    best = np.argmax(ref, axis=1)
+    np.testing.assert_allclose(lp[np.arange(len(ref)), best], ref[np.arange(len(ref)), best], rtol=0, atol=1e-4)
+
+
+def test_d17_truncated_close_to_exact(mld):
+    """d=17 at chi=16 (truncating, global workspace): the boundary-MPS value
+    is an approximation of the exact contraction (Sec. 3.2.1: small chi
+    suffices well below threshold). Loose sanity bound: the leading coset is
+    within 0.05 of exact at p=0.05 and the decision agrees."""
+    d, n, chi = 17, 289, 16
+    noise = synth.depolarizing(n, 0.05).astype(np.float32)
+    E = synth.sample_errors(d, noise, 4, seed=19)
+    syn = synth.syndromes_of(d, E)
+    ref, _ = oracle.decode(d, noise, syn)
+    lp, am = gpu_decode(mld, d, noise, syn, chi)
+    best = np.argmax(ref, axis=1)
+    assert np.all(np.abs(lp[np.arange(4), best] - ref[np.arange(4), best]) < 5e-2)
+    assert np.array_equal(am, best)
