@@ -149,6 +149,42 @@ mld_status mld_decode_noalloc(const mld_code* code, const float* noise, int nois
                               const uint64_t* syndromes, int64_t B, int chi, int precision,
                               double* logP, uint8_t* argmax, void* stream, int check_status);
 
+/* One decode job of a mixed batch: arguments of mld_decode (device pointers). */
+typedef struct {
+    const mld_code* code;
+    const float* noise;
+    int noise_mode;
+    const uint64_t* syndromes;
+    int64_t B;
+    int chi;
+    int precision;
+    double* logP;
+    uint8_t* argmax;             /* may be NULL */
+} mld_job;
+
+/* Decode a batch of jobs of different d, noise and chi (the batching of
+ * independent syndromes across codes; the paper has no counterpart). Jobs run
+ * concurrently on library-owned streams forked from `stream` and joined back
+ * into it; jobs that share a code object run one after another (they share
+ * its workspace). Asynchronous; statuses as mld_decode. */
+mld_status mld_decode_batch(const mld_job* jobs, int n_jobs, void* stream);
+
+typedef struct mld_graph mld_graph;   /* opaque */
+
+/* Capture mld_decode_batch(jobs) into an executable CUDA graph: one graph
+ * launch then decodes every job again, on whatever the job buffers hold at
+ * that time (the buffer pointers are fixed at capture). The jobs are run
+ * once, uncaptured, before the capture so that every plan and workspace is
+ * allocated (and every autotuned shape chosen) first. */
+mld_status mld_graph_create(const mld_job* jobs, int n_jobs, mld_graph** out);
+mld_status mld_graph_launch(mld_graph* graph, void* stream);
+void mld_graph_destroy(mld_graph* graph);
+
+/* Time the candidate CTA shapes (warps per block) of this code, chi and
+ * precision on a synthetic batch of the given size and keep the fastest for
+ * later decodes of this code object (per chi and precision). Synchronous. */
+mld_status mld_autotune(const mld_code* code, int chi, int precision, int64_t sample_B, int* chosen_warps);
+
 /* Read and clear the device status word written by earlier mld_decode calls
  * on this code (the caller must have synchronised their streams):
  * MLD_OK, MLD_ERR_TIMEOUT or MLD_ERR_NUMERIC. */

@@ -30,9 +30,17 @@ MLD_NOISE_TABLE, MLD_NOISE_DEPOL = 0, 1
 EXPORTED_SYMBOLS = ["mld_code_create_rotated", "mld_code_destroy", "mld_code_info", "mld_code_layout",
                     "mld_code_representatives",
                     "mld_decode", "mld_decode_host", "mld_decode_status", "mld_decode_launches",
-                    "mld_decode_flops", "mld_decode_noalloc", "mld_status_string"]
+                    "mld_decode_flops", "mld_decode_noalloc", "mld_decode_batch", "mld_graph_create",
+                    "mld_graph_launch", "mld_graph_destroy", "mld_autotune", "mld_status_string"]
 
 _lib = None
+
+
+class MldJob(ctypes.Structure):
+    """C struct mld_job (one decode job of a mixed batch)."""
+    _fields_ = [("code", ctypes.c_void_p), ("noise", ctypes.c_void_p), ("noise_mode", ctypes.c_int),
+                ("syndromes", ctypes.c_void_p), ("B", ctypes.c_int64), ("chi", ctypes.c_int),
+                ("precision", ctypes.c_int), ("logP", ctypes.c_void_p), ("argmax", ctypes.c_void_p)]
 
 
 class MldError(RuntimeError):
@@ -77,6 +85,16 @@ def load(build_if_missing: bool = True):
     lib.mld_decode_status.restype = I
     lib.mld_decode_flops.argtypes = [P, I, I, ctypes.POINTER(ctypes.c_double)]
     lib.mld_decode_flops.restype = I
+    lib.mld_decode_batch.argtypes = [P, I, P]
+    lib.mld_decode_batch.restype = I
+    lib.mld_graph_create.argtypes = [P, I, ctypes.POINTER(P)]
+    lib.mld_graph_create.restype = I
+    lib.mld_graph_launch.argtypes = [P, P]
+    lib.mld_graph_launch.restype = I
+    lib.mld_graph_destroy.argtypes = [P]
+    lib.mld_graph_destroy.restype = None
+    lib.mld_autotune.argtypes = [P, I, I, L, ctypes.POINTER(I)]
+    lib.mld_autotune.restype = I
     lib.mld_decode_launches.argtypes = []
     lib.mld_decode_launches.restype = I
     lib.mld_status_string.argtypes = [I]
@@ -218,3 +236,59 @@ class Code:
 
     def status(self) -> int:
         return mld_decode_status(self.handle)
+
+
+def make_jobs(items):
+    """items: list of (Code, noise tensor, syndromes tensor, chi, precision,
+    logP tensor, argmax tensor or None) on the GPU -> ctypes array of MldJob."""
+    arr = (MldJob * len(items))()
+    for k, (code, noise, syn, chi, prec, logP, am) in enumerate(items):
+        arr[k] = MldJob(code.handle, noise.data_ptr(), MLD_NOISE_TABLE if noise.dim() == 2 else MLD_NOISE_DEPOL,
+                        syn.data_ptr(), syn.shape[0], int(chi), int(prec), logP.data_ptr(),
+                        am.data_ptr() if am is not None else 0)
+    return arr
+
+
+def mld_decode_batch(jobs, stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(load().mld_decode_batch(ctypes.cast(jobs, ctypes.c_void_p), len(jobs), ctypes.c_void_p(int(stream))),
+           "mld_decode_batch")
+
+
+class Graph:
+    """A mixed batch captured into one CUDA graph (mld_graph_create); launch()
+    decodes whatever the jobs' buffers hold."""
+
+    def __init__(self, jobs):
+        self._jobs = jobs                        # keep the job array alive
+        h = ctypes.c_void_p()
+        _check(load().mld_graph_create(ctypes.cast(jobs, ctypes.c_void_p), len(jobs), ctypes.byref(h)),
+               "mld_graph_create")
+        self.handle = h.value
+
+    def launch(self, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        _check(load().mld_graph_launch(ctypes.c_void_p(self.handle), ctypes.c_void_p(int(stream))),
+               "mld_graph_launch")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().mld_graph_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mld_autotune(code, chi, precision=MLD_FP32, sample_B=8192) -> int:
+    w = ctypes.c_int()
+    _check(load().mld_autotune(ctypes.c_void_p(code.handle), int(chi), int(precision), int(sample_B),
+                               ctypes.byref(w)), "mld_autotune")
+    return w.value

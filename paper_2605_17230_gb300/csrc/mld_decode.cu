@@ -778,9 +778,9 @@ mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, co
         gws = C->d_gws;
         gws_warps = nw;
     } else {
-        // warps per CTA: the most resident warps per SM (32 CTAs and 64 warps
-        // per SM at most, 1 KB of shared memory reserved per CTA), fewest
-        // warps per CTA on ties
+        // warps per CTA: the autotuned shape if mld_autotune chose one, else
+        // the most resident warps per SM (32 CTAs and 64 warps per SM at most,
+        // 1 KB of shared memory reserved per CTA), fewest warps per CTA on ties
         int best = 0;
         for (int w = 1; w <= mld::kMaxWarpsPerBlock; ++w) {
             if (pw * w > (size_t)max_optin) break;
@@ -789,6 +789,10 @@ mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, co
             int warps = ctas * w < 64 ? ctas * w : 64;
             if (warps > best) { best = warps; W = w; }
         }
+        const int key = chi * 4 + precision;
+        for (const auto& kv : C->tuned)
+            if (kv.first == key && kv.second >= 1 && pw * kv.second <= (size_t)max_optin) W = kv.second;
+        if (C->force_warps > 0 && pw * C->force_warps <= (size_t)max_optin) W = C->force_warps;
     }
     const size_t smem = gws ? 0 : pw * W;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -3,6 +3,7 @@
 
 #include <stdint.h>
 
+#include <utility>
 #include <vector>
 
 #include "../../include/mld.h"
@@ -29,4 +30,7 @@ struct mld_code {
     // global workspace for states larger than a block's shared memory
     float* d_gws = nullptr;
     size_t gws_bytes = 0;
+    // autotuned warps per CTA, keyed by chi * 4 + precision
+    std::vector<std::pair<int, int>> tuned;
+    int force_warps = 0;                 // set only while mld_autotune times a candidate
 };
