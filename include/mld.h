@@ -185,6 +185,22 @@ void mld_graph_destroy(mld_graph* graph);
  * later decodes of this code object (per chi and precision). Synchronous. */
 mld_status mld_autotune(const mld_code* code, int chi, int precision, int64_t sample_B, int* chosen_warps);
 
+/* Adjoint of the sweep: derivatives of ln Z_l(s) with respect to the noise
+ * table (Sec. 3.2.4: the contraction is differentiable in the local error
+ * probabilities; Eq. 10's estimation back-propagates through it).
+ *   noise      device float[n][4] (MLD_NOISE_TABLE only).
+ *   dlogP      device double[B][4] upstream gradient dL/d ln Z_l(s), or NULL
+ *              (then only logP is computed).
+ *   logP       device double[B][4] output (ln Z_l(s)), or NULL.
+ *   dnoise     device double[n][4]: dL/dp_{q,P} (all four entries of a row
+ *              treated as independent) is ADDED to it.
+ * Each qubit factor's environment is contracted exactly from the checkpointed
+ * left states of the forward sweep and the right states of the sweep of the
+ * half-turn image, so chi must not truncate (MLD_ERR_UNSUPPORTED otherwise)
+ * and d <= 11. FP32 contraction, FP64 accumulation. Asynchronous on stream. */
+mld_status mld_decode_grad(const mld_code* code, const float* noise, const uint64_t* syndromes, int64_t B,
+                           int chi, const double* dlogP, double* logP, double* dnoise, void* stream);
+
 /* Read and clear the device status word written by earlier mld_decode calls
  * on this code (the caller must have synchronised their streams):
  * MLD_OK, MLD_ERR_TIMEOUT or MLD_ERR_NUMERIC. */

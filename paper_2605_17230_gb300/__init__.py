@@ -31,7 +31,8 @@ EXPORTED_SYMBOLS = ["mld_code_create_rotated", "mld_code_destroy", "mld_code_inf
                     "mld_code_representatives",
                     "mld_decode", "mld_decode_host", "mld_decode_status", "mld_decode_launches",
                     "mld_decode_flops", "mld_decode_noalloc", "mld_decode_batch", "mld_graph_create",
-                    "mld_graph_launch", "mld_graph_destroy", "mld_autotune", "mld_status_string"]
+                    "mld_graph_launch", "mld_graph_destroy", "mld_autotune", "mld_decode_grad",
+                    "mld_status_string"]
 
 _lib = None
 
@@ -95,6 +96,8 @@ def load(build_if_missing: bool = True):
     lib.mld_graph_destroy.restype = None
     lib.mld_autotune.argtypes = [P, I, I, L, ctypes.POINTER(I)]
     lib.mld_autotune.restype = I
+    lib.mld_decode_grad.argtypes = [P, P, P, L, I, P, P, P, P]
+    lib.mld_decode_grad.restype = I
     lib.mld_decode_launches.argtypes = []
     lib.mld_decode_launches.restype = I
     lib.mld_status_string.argtypes = [I]
@@ -292,3 +295,51 @@ def mld_autotune(code, chi, precision=MLD_FP32, sample_B=8192) -> int:
     _check(load().mld_autotune(ctypes.c_void_p(code.handle), int(chi), int(precision), int(sample_B),
                                ctypes.byref(w)), "mld_autotune")
     return w.value
+
+
+def mld_decode_grad(code, noise, syndromes, B, chi, dlogP, logP, dnoise, stream=None):
+    """C-ABI mld_decode_grad on torch CUDA tensors (dnoise is accumulated)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(load().mld_decode_grad(ctypes.c_void_p(code), _ptr(noise), _ptr(syndromes), int(B), int(chi),
+                                  _ptr(dlogP), _ptr(logP), _ptr(dnoise), ctypes.c_void_p(int(stream))),
+           "mld_decode_grad")
+
+
+def _logz_function():
+    import torch
+
+    class LogZ(torch.autograd.Function):
+        """ln Z_l(s) as a differentiable function of the noise table [n][4]:
+        forward through mld_decode, backward through the adjoint sweep."""
+
+        @staticmethod
+        def forward(ctx, noise, code, syndromes, chi):
+            nz = noise.detach().to(torch.float32).contiguous()
+            logP, _ = code.decode(nz, syndromes, chi, MLD_FP32, with_argmax=False)
+            ctx.code, ctx.chi = code, chi
+            ctx.save_for_backward(nz, syndromes)
+            return logP
+
+        @staticmethod
+        def backward(ctx, dlogP):
+            nz, syn = ctx.saved_tensors
+            dnoise = torch.zeros((ctx.code.n, 4), dtype=torch.float64, device=nz.device)
+            mld_decode_grad(ctx.code.handle, nz, syn, syn.shape[0], ctx.chi,
+                            dlogP.detach().to(torch.float64).contiguous(), None, dnoise)
+            return dnoise, None, None, None
+
+    return LogZ
+
+
+_LogZ = None
+
+
+def log_coset_probabilities(code, noise, syndromes, chi):
+    """Differentiable ln Z_l(s) [B][4] (float64) of a noise table [n][4]
+    (torch CUDA tensor, may require grad). chi must not truncate."""
+    global _LogZ
+    if _LogZ is None:
+        _LogZ = _logz_function()
+    return _LogZ.apply(noise, code, syndromes, chi)

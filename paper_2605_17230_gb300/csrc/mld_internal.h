@@ -33,4 +33,7 @@ struct mld_code {
     // autotuned warps per CTA, keyed by chi * 4 + precision
     std::vector<std::pair<int, int>> tuned;
     int force_warps = 0;                 // set only while mld_autotune times a candidate
+    // workspace of the adjoint kernel
+    float* d_gradws = nullptr;
+    size_t gradws_bytes = 0;
 };

@@ -4,6 +4,12 @@
 
 #include <stdint.h>
 
+#if defined(__CUDACC__)
+#define MLD_HD __host__ __device__
+#else
+#define MLD_HD
+#endif
+
 namespace mld {
 
 constexpr int kMaxD = 25;
@@ -81,7 +87,7 @@ struct Plan {
     int init_sizes[kMaxD + 1] = {};   // initial product-state site sizes
 };
 
-constexpr bool plaquette_is_check(int d, int i, int j) {
+MLD_HD constexpr bool plaquette_is_check(int d, int i, int j) {
     const bool in_rows = i >= 1 && i <= d - 1, in_cols = j >= 1 && j <= d - 1;
     if (in_rows && in_cols) return true;                                // interior
     if ((i == 0 || i == d) && in_cols) return ((i + j) & 1) == 0;       // X-type, top/bottom

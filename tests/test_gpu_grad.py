@@ -1,0 +1,141 @@
+"""Adjoint of the sweep (mld_decode_grad) and its autograd wrapper.
+
+Z is multilinear in the noise rows, so the oracle's exact derivative
+(d ln Z / d p_{q,P} = Z with row q set to e_P, divided by Z) pins the GPU
+gradient; central differences of the FP64 oracle pin the chain rule of the
+conditional log-likelihood; rate recovery checks the gradient is usable for
+maximum-likelihood noise estimation (Sec. 3.2.4, Eq. 10)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mld():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_17230_gb300 as m
+    m.load()
+    return m
+
+
+def _setup(d, B, seed):
+    n = d * d
+    noise = synth.lognormal_biased(n, seed=seed).astype(np.float32)
+    E = synth.sample_errors(d, noise, B, seed=seed + 1)
+    syn = synth.syndromes_of(d, E)
+    return n, noise, E, syn
+
+
+@pytest.mark.parametrize("d,chi", [(3, 8), (5, 4), (7, 8), (9, 16)])
+def test_gradient_matches_oracle(mld, d, chi):
+    n, noise, E, syn = _setup(d, 24, seed=d)
+    code = mld.Code(d)
+    rng = np.random.default_rng(d)
+    up = rng.normal(size=(len(syn), 4))
+    nz = torch.tensor(noise, device="cuda")
+    sy = torch.tensor(syn.view(np.int64), device="cuda")
+    dn = torch.zeros((n, 4), dtype=torch.float64, device="cuda")
+    lp = torch.zeros((len(syn), 4), dtype=torch.float64, device="cuda")
+    mld.mld_decode_grad(code.handle, nz, sy, len(syn), chi, torch.tensor(up, device="cuda"), lp, dn)
+    torch.cuda.synchronize()
+    assert code.status() == 0
+    reps = oracle.representatives(d, syn)
+    lz, g = oracle.coset_dlogz(d, noise.astype(np.float64), reps.reshape(-1, n))
+    np.testing.assert_allclose(lp.cpu().numpy(), lz.reshape(-1, 4), rtol=0, atol=1e-5)
+    ref = np.einsum("bl,blqp->qp", up, g.reshape(len(syn), 4, n, 4))
+    np.testing.assert_allclose(dn.cpu().numpy(), ref, rtol=1e-4, atol=1e-4 * np.abs(ref).max())
+
+
+def test_euler_identity_per_unit(mld):
+    """sum_P p_{q,P} d ln Z / d p_{q,P} = 1 for every qubit (Z is linear in
+    each row), for a single (syndrome, class) unit."""
+    d, chi = 7, 8
+    n, noise, E, syn = _setup(d, 3, seed=5)
+    code = mld.Code(d)
+    nz = torch.tensor(noise, device="cuda")
+    sy = torch.tensor(syn.view(np.int64), device="cuda")
+    for unit in range(4 * len(syn)):
+        up = torch.zeros((len(syn), 4), dtype=torch.float64, device="cuda")
+        up.view(-1)[unit] = 1.0
+        dn = torch.zeros((n, 4), dtype=torch.float64, device="cuda")
+        mld.mld_decode_grad(code.handle, nz, sy, len(syn), chi, up, None, dn)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose((dn.cpu().numpy() * noise).sum(axis=1), 1.0, rtol=0, atol=2e-5)
+
+
+def test_autograd_conditional_loglik_vs_central_differences(mld):
+    """L = sum_b ln Pr(l_true | s_b) with p_I = 1 - p_X - p_Y - p_Z per qubit:
+    autograd through the adjoint vs central differences (h = 1e-4) of the
+    FP64 oracle."""
+    d, chi = 5, 4
+    n, noise, E, syn = _setup(d, 64, seed=11)
+    cls = torch.tensor(synth.true_class(d, E).astype(np.int64), device="cuda")
+    code = mld.Code(d)
+    sy = torch.tensor(syn.view(np.int64), device="cuda")
+    theta = torch.tensor(noise[:, 1:].astype(np.float64), device="cuda", requires_grad=True)
+
+    def table(t):
+        return torch.cat([1.0 - t.sum(dim=1, keepdim=True), t], dim=1)
+
+    lp = mld.log_coset_probabilities(code, table(theta), sy, chi)
+    L = (lp.gather(1, cls[:, None]).squeeze(1) - torch.logsumexp(lp, dim=1)).sum()
+    L.backward()
+    grad = theta.grad.cpu().numpy()
+
+    def L_oracle(th):
+        tab = np.concatenate([1.0 - th.sum(axis=1, keepdims=True), th], axis=1)
+        lpo, _ = oracle.decode(d, tab, syn)
+        m = lpo.max(axis=1, keepdims=True)
+        lse = m[:, 0] + np.log(np.exp(lpo - m).sum(axis=1))
+        return float((lpo[np.arange(len(syn)), synth.true_class(d, E)] - lse).sum())
+
+    th0 = noise[:, 1:].astype(np.float32).astype(np.float64)
+    h = 1e-4
+    rng = np.random.default_rng(0)
+    for q, k in zip(rng.choice(n, 6, replace=False), rng.integers(0, 3, 6)):
+        up = th0.copy(); up[q, k] += h
+        dn = th0.copy(); dn[q, k] -= h
+        fd = (L_oracle(up) - L_oracle(dn)) / (2 * h)
+        assert abs(grad[q, k] - fd) <= 2e-3 * max(1.0, abs(fd)), (q, k, grad[q, k], fd)
+
+
+def test_rate_recovery_by_gradient_ascent(mld):
+    """Maximum-likelihood estimation of per-qubit rates from syndromes alone
+    (the marginal likelihood sum_b ln sum_l Z_l(s_b), Eq. 10): starting from a
+    uniform guess, gradient ascent moves the total per-qubit rates toward
+    the seeded ones."""
+    d, chi = 5, 4
+    n = d * d
+    true = synth.lognormal_biased(n, seed=21)
+    E = synth.sample_errors(d, true, 16384, seed=22)
+    syn = synth.syndromes_of(d, E)
+    code = mld.Code(d)
+    sy = torch.tensor(syn.view(np.int64), device="cuda")
+    # parametrise the three Pauli rates per qubit through logits
+    z0 = np.log(np.full((n, 3), 0.05 / 3) / (1 - 0.05))
+    zt = torch.tensor(z0, device="cuda", requires_grad=True)
+    opt = torch.optim.Adam([zt], lr=0.08)
+
+    def table(z):
+        e = torch.exp(z)
+        den = 1.0 + e.sum(dim=1, keepdim=True)
+        return torch.cat([1.0 / den, e / den], dim=1)
+
+    p_true = true[:, 1:].sum(axis=1)
+    err0 = np.abs(table(zt).detach().cpu().numpy()[:, 1:].sum(axis=1) - p_true).mean()
+    for _ in range(300):
+        opt.zero_grad()
+        lp = mld.log_coset_probabilities(code, table(zt), sy, chi)
+        loss = -torch.logsumexp(lp, dim=1).mean()
+        loss.backward()
+        opt.step()
+    p_fit = table(zt).detach().cpu().numpy()[:, 1:].sum(axis=1)
+    err1 = np.abs(p_fit - p_true).mean()
+    assert err1 < 0.5 * err0, (err0, err1)
+    assert np.corrcoef(p_fit, p_true)[0, 1] > 0.5
