@@ -46,6 +46,13 @@ __device__ __forceinline__ float wsel(const float4 w, int par, int a, int ap, in
     return idx == 0 ? w.x : idx == 1 ? w.y : idx == 2 ? w.z : w.w;
 }
 
+// The eight weights w(a, a', beta, b') of a lane whose column fixes a',
+// indexed a | b' << 1 | beta << 2.
+__device__ __forceinline__ void weights8(const float4 w, int par, int ap, float (&o)[8]) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) o[m] = wsel(w, par, m & 1, ap, (m >> 2) & 1, (m >> 1) & 1);
+}
+
 // X_a[k][col] = sum_r C[k][a*DL + r] A[r][col] for the identity cases
 // (identity carry and/or identity old site), where the sum has one term.
 template <int DL, int DR, int PAM, int NCOLA, int KQP, int CID, int OKIND>
@@ -110,45 +117,57 @@ __device__ __forceinline__ float gemm_tf32(const float* __restrict__ C, const fl
                                            float* __restrict__ M, const float4 w, int par, int lane) {
     constexpr int NCOLA = PA * DR;
     constexpr int LDC = PAM * DL;
+    constexpr int KB = (K + 15) / 16;
     static_assert(DL % 8 == 0 && NCOLA % 8 == 0, "tensor-core tile shape");
     const int g = lane >> 2, t = lane & 3;
     float mx = 0.f;
-    for (int kb = 0; kb < (K + 15) / 16; ++kb) {
-        const int r0 = kb * 16 + g, r1 = r0 + 8;
 #pragma unroll
-        for (int nt = 0; nt < NCOLA / 8; ++nt) {
+    for (int nt = 0; nt < NCOLA / 8; ++nt) {
+        // B fragments (the data site) split once per n-tile, reused by every
+        // row block and both a
+        unsigned bh[DL / 8][2], bl[DL / 8][2];
+#pragma unroll
+        for (int ks = 0; ks < DL / 8; ++ks) {
+            split_tf32(A[(8 * ks + t) * NCOLA + nt * 8 + g], bh[ks][0], bl[ks][0]);
+            split_tf32(A[(8 * ks + t + 4) * NCOLA + nt * 8 + g], bh[ks][1], bl[ks][1]);
+        }
+        // weights of this lane's two columns (e = 0, 1)
+        float wp[2][8];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) weights8(w, par, (nt * 8 + 2 * t + e) / DR, wp[e]);
+        for (int kb = 0; kb < KB; ++kb) {
+            const int r0 = kb * 16 + g, r1 = r0 + 8;
             float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
-            for (int ks = 0; ks < DL; ks += 8) {
-                unsigned bh0, bl0, bh1, bl1;
-                split_tf32(A[(ks + t) * NCOLA + nt * 8 + g], bh0, bl0);
-                split_tf32(A[(ks + t + 4) * NCOLA + nt * 8 + g], bh1, bl1);
+            for (int ks = 0; ks < DL / 8; ++ks) {
 #pragma unroll
                 for (int a = 0; a < PAM; ++a) {
-                    const float* c0 = C + r0 * LDC + a * DL + ks;
-                    const float* c1 = C + r1 * LDC + a * DL + ks;
+                    const float* c0 = C + r0 * LDC + a * DL + 8 * ks;
+                    const float* c1 = C + r1 * LDC + a * DL + 8 * ks;
                     unsigned ah[4], al[4];
                     split_tf32(r0 < K ? c0[t] : 0.f, ah[0], al[0]);
                     split_tf32(r1 < K ? c1[t] : 0.f, ah[1], al[1]);
                     split_tf32(r0 < K ? c0[t + 4] : 0.f, ah[2], al[2]);
                     split_tf32(r1 < K ? c1[t + 4] : 0.f, ah[3], al[3]);
-                    mma_tf32(acc[a], al[0], al[1], al[2], al[3], bh0, bh1);
-                    mma_tf32(acc[a], ah[0], ah[1], ah[2], ah[3], bl0, bl1);
-                    mma_tf32(acc[a], ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+                    mma_tf32(acc[a], al[0], al[1], al[2], al[3], bh[ks][0], bh[ks][1]);
+                    mma_tf32(acc[a], ah[0], ah[1], ah[2], ah[3], bl[ks][0], bl[ks][1]);
+                    mma_tf32(acc[a], ah[0], ah[1], ah[2], ah[3], bh[ks][0], bh[ks][1]);
                 }
             }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int k = kb * 16 + g + 8 * h;
                 if (k >= K) continue;
-                const int beta = k / KQP;
+                const bool beta = (k / KQP) != 0;
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
-                    const int col = nt * 8 + 2 * t + e, ap = col / DR;
+                    const int col = nt * 8 + 2 * t + e;
                     const float x0 = acc[0][2 * h + e], x1 = PAM == 2 ? acc[1][2 * h + e] : 0.f;
 #pragma unroll
                     for (int bp = 0; bp < PB; ++bp) {
-                        const float o = fmaf(wsel(w, par, 0, ap, beta, bp), x0, wsel(w, par, 1, ap, beta, bp) * x1);
+                        const float w0 = beta ? wp[e][(bp << 1) | 4] : wp[e][bp << 1];
+                        const float w1 = beta ? wp[e][1 | (bp << 1) | 4] : wp[e][1 | (bp << 1)];
+                        const float o = fmaf(w0, x0, w1 * x1);
                         M[(bp * K + k) * NCOL + col] = o;
                         mx = fmaxf(mx, fabsf(o));
                     }
@@ -217,6 +236,8 @@ __device__ __noinline__ float left_step(const float* __restrict__ C, const float
         const int col = cl + 32 * cidx;
         if (col >= NCOLA) continue;
         const int ap = col / DR, rp = col % DR;
+        float wp[8];
+        weights8(w, par, ap, wp);
         if constexpr (!CID && OKIND == K_DATA) {
             // a real GEMM: this lane's column of A in registers
             float acol[DL];
@@ -230,10 +251,12 @@ __device__ __noinline__ float left_step(const float* __restrict__ C, const float
                     x0 = fmaf(c0[r], acol[r], x0);
                     if (PAM == 2) x1 = fmaf(c0[DL + r], acol[r], x1);
                 }
-                const int beta = k / KQP;
+                const bool beta = (k / KQP) != 0;
 #pragma unroll
                 for (int bp = 0; bp < PB; ++bp) {
-                    const float o = fmaf(wsel(w, par, 0, ap, beta, bp), x0, wsel(w, par, 1, ap, beta, bp) * x1);
+                    const float w0 = beta ? wp[(bp << 1) | 4] : wp[bp << 1];
+                    const float w1 = beta ? wp[1 | (bp << 1) | 4] : wp[1 | (bp << 1)];
+                    const float o = fmaf(w0, x0, w1 * x1);
                     M[(bp * K + k) * NCOL + col] = o;
                     mx = fmaxf(mx, fabsf(o));
                 }
@@ -242,10 +265,12 @@ __device__ __noinline__ float left_step(const float* __restrict__ C, const float
             for (int k = rg; k < K; k += RG) {
                 float X[2];
                 x_ident<DL, DR, PAM, NCOLA, KQP, CID, OKIND>(C, A, k, ap, rp, X);
-                const int beta = k / KQP;
+                const bool beta = (k / KQP) != 0;
 #pragma unroll
                 for (int bp = 0; bp < PB; ++bp) {
-                    const float o = fmaf(wsel(w, par, 0, ap, beta, bp), X[0], wsel(w, par, 1, ap, beta, bp) * X[1]);
+                    const float w0 = beta ? wp[(bp << 1) | 4] : wp[bp << 1];
+                    const float w1 = beta ? wp[1 | (bp << 1) | 4] : wp[1 | (bp << 1)];
+                    const float o = fmaf(w0, X[0], w1 * X[1]);
                     M[(bp * K + k) * NCOL + col] = o;
                     mx = fmaxf(mx, fabsf(o));
                 }
@@ -301,6 +326,7 @@ struct Ctx {
     float* qst;
     int lane;
     int e2;
+    int pe;                     // exponent of the last block's max |M|, not yet folded
     bool zero, bad;
 };
 
@@ -311,8 +337,14 @@ __device__ __forceinline__ void left_site(Ctx<D, PREC>& x) {
     float* cin = (I & 1) ? x.buf1 : x.buf0;
     float* cout = (I & 1) ? x.buf0 : x.buf1;
     float* M = st.tall ? x.qst + st.offQ : cout;
-    const float4 w = I == 0 ? make_float4(1.f, 1.f, 1.f, 1.f)
-                            : *reinterpret_cast<const float4*>(x.wts + 4 * ((I - 1) * D + C));
+    // power-of-two renormalisation, folded: the exponent of the previous
+    // block's max |M| scales this site's factor (Z is linear in it), so no
+    // block is rewritten and every block stays within one site's growth of 1
+    const float sc = __int_as_float((127 - x.pe) << 23);
+    x.e2 += x.pe;
+    float4 w = I == 0 ? make_float4(1.f, 1.f, 1.f, 1.f)
+                      : *reinterpret_cast<const float4*>(x.wts + 4 * ((I - 1) * D + C));
+    w.x *= sc; w.y *= sc; w.z *= sc; w.w *= sc;
     float mx = left_step<st.K, st.pam, st.Dl, st.pa, st.Dr, st.pb, st.ncol, st.kq_prev, st.cid, st.okind,
                          (I == D), PREC>(cin, x.mps + st.offA, M, w, st.parity, x.lane);
     mx = wmax(mx);
@@ -321,11 +353,7 @@ __device__ __forceinline__ void left_site(Ctx<D, PREC>& x) {
     int ex;
     frexpf(mx, &ex);
     if (ex > 126 || ex < -125) { x.bad = true; return; }
-    const float sc = __int_as_float((127 - ex) << 23);
-    constexpr int LEN = st.pb * st.K * st.ncol;
-    __syncwarp();
-    for (int e = x.lane; e < LEN; e += 32) M[e] *= sc;
-    x.e2 += ex;
+    x.pe = ex;
     __syncwarp();
 }
 
@@ -449,6 +477,7 @@ __device__ __forceinline__ void decode_unit(const ExactArgs& a, float* ws, int64
     x.qst = ws + OFF_Q;
     x.lane = lane;
     x.e2 = 0;
+    x.pe = 0;
     x.zero = false;
     x.bad = false;
 
