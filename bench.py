@@ -152,6 +152,106 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+MIXED_CHI = {3: 16, 5: 16, 7: 16, 9: 32, 11: 32, 13: 64}
+
+
+def run_mixed(args):
+    """Mixed batch (1,048,576 syndromes, d uniform over 3..13, p ~ U[0.02, 0.18]
+    per syndrome, chi by d) decoded by one CUDA-graph launch."""
+    import torch
+    import paper_2605_17230_gb300 as mld
+    import oracle
+    total = args.mixed_total
+    ds = sorted(MIXED_CHI)
+    per = total // len(ds)
+    items_by_prec, host = {}, []
+    codes = {d: mld.Code(d) for d in ds}
+    for d in ds:
+        p = synth.per_syndrome_depolarizing(per, seed=synth.config_seed(2, d, 0.0), lo=0.02, hi=0.18)
+        E = synth.sample_errors(d, p, per, seed=synth.config_seed(2, d, 0.1))
+        host.append((d, p, synth.syndromes_of(d, E)))
+    for prec in (mld.MLD_FP32, mld.MLD_MIXED_TF32):
+        items = []
+        for d, p, syn in host:
+            items.append((codes[d], torch.tensor(p.astype(np.float32), device="cuda"),
+                          torch.tensor(syn.view(np.int64), device="cuda"), MIXED_CHI[d], prec,
+                          torch.empty((per, 4), dtype=torch.float64, device="cuda"),
+                          torch.empty((per,), dtype=torch.uint8, device="cuda")))
+        items_by_prec[prec] = items
+    res = {}
+    for prec, items in items_by_prec.items():
+        g = mld.Graph(mld.make_jobs(items))
+        for _ in range(max(1, args.warmup)):
+            g.launch()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            g.launch()
+        e1.record()
+        torch.cuda.synchronize()
+        res[prec] = (e0.elapsed_time(e1) / args.steps, g)
+    rng = np.random.default_rng(0)
+    per_d = {}
+    for k, (d, p, syn) in enumerate(host):
+        a = items_by_prec[mld.MLD_FP32][k][5].cpu().numpy()
+        b = items_by_prec[mld.MLD_MIXED_TF32][k][5].cpu().numpy()
+        idx = rng.choice(per, 64 if d == 13 else 256, replace=False)
+        ref, _ = oracle.decode(d, p[idx].astype(np.float32).astype(np.float64), syn[idx])
+        per_d[str(d)] = {"chi": MIXED_CHI[d], "max_abs_dlogP_mixed_vs_fp32": float(np.abs(a - b).max()),
+                         "max_abs_dlogP_mixed_vs_oracle_sample": float(np.abs(b[idx] - ref).max()),
+                         "oracle_sample": len(idx)}
+    ms32, msm = res[mld.MLD_FP32][0], res[mld.MLD_MIXED_TF32][0]
+    line = {"metric": "syndromes/s, mixed d=3..13 batch in one graph launch", "workload": "mixed",
+            "value": per * len(ds) / (msm / 1e3), "unit": "syndromes/s", "fp32_value": per * len(ds) / (ms32 / 1e3),
+            "ms_per_launch": msm, "fp32_ms_per_launch": ms32, "syndromes": per * len(ds), "steps": args.steps,
+            "per_d": per_d, "data": "synthetic",
+            "config": {"d": ds, "chi_by_d": MIXED_CHI, "p": "U[0.02, 0.18] per syndrome, depolarizing"}}
+    print(json.dumps(line), flush=True)
+
+
+def run_grad(args):
+    """Adjoint of the sweep on the d=7 workload with per-qubit biased noise:
+    gradient of sum_b ln Pr(l_true | s_b) over 65,536 syndromes."""
+    import torch
+    import paper_2605_17230_gb300 as mld
+    d, n, chi, Bg = 7, 49, 32, 65536
+    noise = synth.lognormal_biased(n, seed=3).astype(np.float32)
+    E = synth.sample_errors(d, noise, Bg, seed=4)
+    syn = synth.syndromes_of(d, E)
+    code = mld.Code(d)
+    nz = torch.tensor(noise, device="cuda")
+    sy = torch.tensor(syn.view(np.int64), device="cuda")
+    cls = torch.tensor(synth.true_class(d, E).astype(np.int64), device="cuda")
+    lp, _ = code.decode(nz, sy, chi)
+    up = torch.zeros_like(lp)
+    up.scatter_(1, cls[:, None], 1.0)
+    up -= torch.softmax(lp, dim=1)                # d/d lnZ of ln Pr(l_true|s)
+    dn = torch.zeros((n, 4), dtype=torch.float64, device="cuda")
+    for _ in range(max(1, args.warmup)):
+        mld.mld_decode_grad(code.handle, nz, sy, Bg, chi, up, None, dn)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        mld.mld_decode_grad(code.handle, nz, sy, Bg, chi, up, None, dn)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    line = {"metric": "syndromes/s of the adjoint (d=7, chi=32, per-qubit biased noise)", "workload": "grad",
+            "value": Bg / (ms / 1e3), "unit": "syndromes/s", "ms_per_step": ms, "syndromes": Bg,
+            "steps": args.steps, "data": "synthetic", "dtype": "f32 contraction, f64 accumulation",
+            "forward_only_value": None}
+    t0 = torch.cuda.Event(enable_timing=True); t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        code.decode(nz, sy, chi)
+    t1.record()
+    torch.cuda.synchronize()
+    line["forward_only_value"] = Bg / (t0.elapsed_time(t1) / args.steps / 1e3)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -162,11 +262,19 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=B, help="syndromes per GPU per step (default: the "
                     "65536 of the workload; smaller values only for profiling captures)")
+    ap.add_argument("--workload", default="metric", choices=["metric", "mixed", "grad"],
+                    help="metric: the headline d=9 line (default); mixed: the 1,048,576-syndrome mixed-d "
+                         "graph batch; grad: the adjoint on the d=7 workload")
+    ap.add_argument("--mixed-total", type=int, default=1 << 20)
     args = ap.parse_args()
     rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)
     local = _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "mixed":
+        return run_mixed(args) if rank == 0 else None
+    if args.workload == "grad":
+        return run_grad(args) if rank == 0 else None
 
     import torch
     import paper_2605_17230_gb300 as mld
