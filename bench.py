@@ -278,6 +278,7 @@ def main():
 
     import torch
     import paper_2605_17230_gb300 as mld
+    from paper_2605_17230_gb300 import shard
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -327,11 +328,7 @@ def main():
             if dist:
                 dist.barrier()
         ms = [a.elapsed_time(b) for a, b in ev]
-        t_local = sum(ms) / 1e3
-        if dist:
-            t = torch.tensor([t_local], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_local = float(t.item())
+        t_local = shard.max_over_ranks(sum(ms) / 1e3, device=dev)
         st = code.status()
         if st != 0:
             raise RuntimeError("device status: " + mld.mld_status_string(st))
