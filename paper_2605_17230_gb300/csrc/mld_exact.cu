@@ -11,10 +11,10 @@ int exact_fpw_13();
 
 int exact_floats_per_warp(int d) {
     switch (d) {
-        case 3: return exact::PlanOf<3>::plan.floats_per_warp;
-        case 5: return exact::PlanOf<5>::plan.floats_per_warp;
-        case 7: return exact::PlanOf<7>::plan.floats_per_warp;
-        case 9: return exact::PlanOf<9>::plan.floats_per_warp;
+        case 3: return exact::LayoutOf<3>::lay.floats_per_warp;
+        case 5: return exact::LayoutOf<5>::lay.floats_per_warp;
+        case 7: return exact::LayoutOf<7>::lay.floats_per_warp;
+        case 9: return exact::LayoutOf<9>::lay.floats_per_warp;
         case 11: return exact_fpw_11();
         case 13: return exact_fpw_13();
     }

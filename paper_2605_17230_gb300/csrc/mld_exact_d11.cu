@@ -4,7 +4,7 @@
 
 namespace mld {
 
-int exact_fpw_11() { return exact::PlanOf<11>::plan.floats_per_warp; }
+int exact_fpw_11() { return exact::LayoutOf<11>::lay.floats_per_warp; }
 
 bool launch_exact_11(const ExactArgs& a, cudaStream_t s, int warps_per_block, int precision) {
     return exact::launch_d<11>(a, s, warps_per_block, precision);

@@ -31,6 +31,12 @@ struct PlanOf {
     static constexpr Plan plan = make_plan(D, kExactChi);
 };
 
+template <int D>
+struct LayoutOf {
+    static constexpr ExactLayout lay = make_exact_layout(PlanOf<D>::plan);
+    static_assert(exact_layout_valid(PlanOf<D>::plan, lay), "overlapping live intermediates");
+};
+
 __device__ __forceinline__ float wmax(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -109,67 +115,86 @@ __device__ __forceinline__ void split_tf32(float x, unsigned& hi, unsigned& lo) 
 // The data-site product of the mixed-precision path: X_a = C_a A on the
 // tensor cores, TF32 operands and FP32 accumulation, each operand split
 // into TF32 hi + lo and the product taken as hi.hi + hi.lo + lo.hi (the
-// lo.lo term is below FP32 rounding). One 16-row block of k for both a at
-// a time, then the FP32 qubit-factor epilogue
+// lo.lo term is below FP32 rounding), then the FP32 qubit-factor epilogue
 // M^{b'}[k][col] = sum_a w(a, a', beta, b') X_a[k][col].
+// Per 16-row block kb and group of up to four 8-column tiles, the k-steps
+// of 8 split one A fragment (both a) and the group's B fragments once and
+// issue three MMAs per (tile, a).
 template <int K, int PAM, int DL, int PA, int DR, int PB, int NCOL, int KQP>
 __device__ __forceinline__ float gemm_tf32(const float* __restrict__ C, const float* __restrict__ A,
                                            float* __restrict__ M, const float4 w, int par, int lane) {
     constexpr int NCOLA = PA * DR;
     constexpr int LDC = PAM * DL;
     constexpr int KB = (K + 15) / 16;
-    static_assert(DL % 8 == 0 && NCOLA % 8 == 0, "tensor-core tile shape");
+    constexpr int NT = NCOLA / 8, KS = DL / 8;
+    constexpr int NTG = NT < 4 ? NT : 4;
+    static_assert(DL % 8 == 0 && NCOLA % 8 == 0 && NT % NTG == 0, "tensor-core tile shape");
     const int g = lane >> 2, t = lane & 3;
+    // the lane's weights for a' = 0 and a' = 1
+    float wa[2][8];
+    weights8(w, par, 0, wa[0]);
+    weights8(w, par, 1, wa[1]);
     float mx = 0.f;
+#pragma unroll 1
+    for (int kb = 0; kb < KB; ++kb) {
+        const int r0 = kb * 16 + g, r1 = r0 + 8;
 #pragma unroll
-    for (int nt = 0; nt < NCOLA / 8; ++nt) {
-        // B fragments (the data site) split once per n-tile, reused by every
-        // row block and both a
-        unsigned bh[DL / 8][2], bl[DL / 8][2];
+        for (int n0 = 0; n0 < NT; n0 += NTG) {
+            float acc[NTG][2][4];
 #pragma unroll
-        for (int ks = 0; ks < DL / 8; ++ks) {
-            split_tf32(A[(8 * ks + t) * NCOLA + nt * 8 + g], bh[ks][0], bl[ks][0]);
-            split_tf32(A[(8 * ks + t + 4) * NCOLA + nt * 8 + g], bh[ks][1], bl[ks][1]);
-        }
-        // weights of this lane's two columns (e = 0, 1)
-        float wp[2][8];
+            for (int j = 0; j < NTG; ++j)
 #pragma unroll
-        for (int e = 0; e < 2; ++e) weights8(w, par, (nt * 8 + 2 * t + e) / DR, wp[e]);
-        for (int kb = 0; kb < KB; ++kb) {
-            const int r0 = kb * 16 + g, r1 = r0 + 8;
-            float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+                for (int a = 0; a < 2; ++a)
 #pragma unroll
-            for (int ks = 0; ks < DL / 8; ++ks) {
+                    for (int q = 0; q < 4; ++q) acc[j][a][q] = 0.f;
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks) {
+                unsigned ah[2][4], al[2][4];
 #pragma unroll
                 for (int a = 0; a < PAM; ++a) {
                     const float* c0 = C + r0 * LDC + a * DL + 8 * ks;
                     const float* c1 = C + r1 * LDC + a * DL + 8 * ks;
-                    unsigned ah[4], al[4];
-                    split_tf32(r0 < K ? c0[t] : 0.f, ah[0], al[0]);
-                    split_tf32(r1 < K ? c1[t] : 0.f, ah[1], al[1]);
-                    split_tf32(r0 < K ? c0[t + 4] : 0.f, ah[2], al[2]);
-                    split_tf32(r1 < K ? c1[t + 4] : 0.f, ah[3], al[3]);
-                    mma_tf32(acc[a], al[0], al[1], al[2], al[3], bh[ks][0], bh[ks][1]);
-                    mma_tf32(acc[a], ah[0], ah[1], ah[2], ah[3], bl[ks][0], bl[ks][1]);
-                    mma_tf32(acc[a], ah[0], ah[1], ah[2], ah[3], bh[ks][0], bh[ks][1]);
+                    split_tf32(r0 < K ? c0[t] : 0.f, ah[a][0], al[a][0]);
+                    split_tf32(r1 < K ? c1[t] : 0.f, ah[a][1], al[a][1]);
+                    split_tf32(r0 < K ? c0[t + 4] : 0.f, ah[a][2], al[a][2]);
+                    split_tf32(r1 < K ? c1[t + 4] : 0.f, ah[a][3], al[a][3]);
+                }
+#pragma unroll
+                for (int j = 0; j < NTG; ++j) {
+                    const int nt = n0 + j;
+                    unsigned bh0, bl0, bh1, bl1;
+                    split_tf32(A[(8 * ks + t) * NCOLA + nt * 8 + g], bh0, bl0);
+                    split_tf32(A[(8 * ks + t + 4) * NCOLA + nt * 8 + g], bh1, bl1);
+#pragma unroll
+                    for (int a = 0; a < PAM; ++a) {
+                        mma_tf32(acc[j][a], al[a][0], al[a][1], al[a][2], al[a][3], bh0, bh1);
+                        mma_tf32(acc[j][a], ah[a][0], ah[a][1], ah[a][2], ah[a][3], bl0, bl1);
+                        mma_tf32(acc[j][a], ah[a][0], ah[a][1], ah[a][2], ah[a][3], bh0, bh1);
+                    }
                 }
             }
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int k = kb * 16 + g + 8 * h;
-                if (k >= K) continue;
-                const bool beta = (k / KQP) != 0;
+            for (int j = 0; j < NTG; ++j) {
+                const int nt = n0 + j;
 #pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int col = nt * 8 + 2 * t + e;
-                    const float x0 = acc[0][2 * h + e], x1 = PAM == 2 ? acc[1][2 * h + e] : 0.f;
+                for (int h = 0; h < 2; ++h) {
+                    const int k = kb * 16 + g + 8 * h;
+                    if (k >= K) continue;
+                    const bool beta = (k / KQP) != 0;
 #pragma unroll
-                    for (int bp = 0; bp < PB; ++bp) {
-                        const float w0 = beta ? wp[e][(bp << 1) | 4] : wp[e][bp << 1];
-                        const float w1 = beta ? wp[e][1 | (bp << 1) | 4] : wp[e][1 | (bp << 1)];
-                        const float o = fmaf(w0, x0, w1 * x1);
-                        M[(bp * K + k) * NCOL + col] = o;
-                        mx = fmaxf(mx, fabsf(o));
+                    for (int e = 0; e < 2; ++e) {
+                        const int col = nt * 8 + 2 * t + e;
+                        const int ap = col / DR;
+                        const float x0 = acc[j][0][2 * h + e], x1 = PAM == 2 ? acc[j][1][2 * h + e] : 0.f;
+#pragma unroll
+                        for (int bp = 0; bp < PB; ++bp) {
+                            const int m0 = (bp << 1) | (beta ? 4 : 0);
+                            const float w0 = ap ? wa[1][m0] : wa[0][m0];
+                            const float w1 = ap ? wa[1][m0 | 1] : wa[0][m0 | 1];
+                            const float o = fmaf(w0, x0, w1 * x1);
+                            M[(bp * K + k) * NCOL + col] = o;
+                            mx = fmaxf(mx, fabsf(o));
+                        }
                     }
                 }
             }
@@ -243,25 +268,67 @@ __device__ __noinline__ float left_step(const float* __restrict__ C, const float
             float acol[DL];
 #pragma unroll
             for (int r = 0; r < DL; ++r) acol[r] = A[r * NCOLA + col];
-            for (int k = rg; k < K; k += RG) {
-                const float* c0 = C + k * LDC;
-                float x0 = 0.f, x1 = 0.f;
+            // KU rows of this lane per pass: 2*KU independent FMA chains
+            // (rows k = rg + j*RG, j < NK; when K < RG the lanes past K idle)
+            constexpr int NK = (K + RG - 1) / RG;
+            constexpr int KUMAX = DL <= 16 ? 4 : DL <= 32 ? 2 : 1;
+            constexpr int KU = NK < KUMAX ? NK : KUMAX;
+            if (K % RG != 0 && rg >= K) continue;
+#pragma unroll 1
+            for (int j0 = 0; j0 < NK; j0 += KU) {
+                float x0[KU], x1[KU];
 #pragma unroll
-                for (int r = 0; r < DL; ++r) {
-                    x0 = fmaf(c0[r], acol[r], x0);
-                    if (PAM == 2) x1 = fmaf(c0[DL + r], acol[r], x1);
+                for (int u = 0; u < KU; ++u) {
+                    x0[u] = 0.f;
+                    x1[u] = 0.f;
                 }
-                const bool beta = (k / KQP) != 0;
+                if constexpr (DL % 4 == 0) {
 #pragma unroll
-                for (int bp = 0; bp < PB; ++bp) {
-                    const float w0 = beta ? wp[(bp << 1) | 4] : wp[bp << 1];
-                    const float w1 = beta ? wp[1 | (bp << 1) | 4] : wp[1 | (bp << 1)];
-                    const float o = fmaf(w0, x0, w1 * x1);
-                    M[(bp * K + k) * NCOL + col] = o;
-                    mx = fmaxf(mx, fabsf(o));
+                    for (int r = 0; r < DL; r += 4) {
+#pragma unroll
+                        for (int u = 0; u < KU; ++u) {
+                            const float* c0 = C + (rg + (j0 + u) * RG) * LDC;
+                            const float4 v0 = *reinterpret_cast<const float4*>(c0 + r);
+                            x0[u] = fmaf(v0.x, acol[r], x0[u]);
+                            x0[u] = fmaf(v0.y, acol[r + 1], x0[u]);
+                            x0[u] = fmaf(v0.z, acol[r + 2], x0[u]);
+                            x0[u] = fmaf(v0.w, acol[r + 3], x0[u]);
+                            if (PAM == 2) {
+                                const float4 v1 = *reinterpret_cast<const float4*>(c0 + DL + r);
+                                x1[u] = fmaf(v1.x, acol[r], x1[u]);
+                                x1[u] = fmaf(v1.y, acol[r + 1], x1[u]);
+                                x1[u] = fmaf(v1.z, acol[r + 2], x1[u]);
+                                x1[u] = fmaf(v1.w, acol[r + 3], x1[u]);
+                            }
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < DL; ++r) {
+#pragma unroll
+                        for (int u = 0; u < KU; ++u) {
+                            const float* c0 = C + (rg + (j0 + u) * RG) * LDC;
+                            x0[u] = fmaf(c0[r], acol[r], x0[u]);
+                            if (PAM == 2) x1[u] = fmaf(c0[DL + r], acol[r], x1[u]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < KU; ++u) {
+                    const int k = rg + (j0 + u) * RG;
+                    const bool beta = (k / KQP) != 0;
+#pragma unroll
+                    for (int bp = 0; bp < PB; ++bp) {
+                        const float w0 = beta ? wp[(bp << 1) | 4] : wp[bp << 1];
+                        const float w1 = beta ? wp[1 | (bp << 1) | 4] : wp[1 | (bp << 1)];
+                        const float o = fmaf(w0, x0[u], w1 * x1[u]);
+                        M[(bp * K + k) * NCOL + col] = o;
+                        mx = fmaxf(mx, fabsf(o));
+                    }
                 }
             }
         } else {
+#pragma unroll 4
             for (int k = rg; k < K; k += RG) {
                 float X[2];
                 x_ident<DL, DR, PAM, NCOLA, KQP, CID, OKIND>(C, A, k, ap, rp, X);
@@ -321,9 +388,7 @@ template <int D, int PREC>
 struct Ctx {
     float* wts;
     float* mps;
-    float* buf0;
-    float* buf1;
-    float* qst;
+    float* arena;               // per-column intermediates at their layout offsets
     int lane;
     int e2;
     int pe;                     // exponent of the last block's max |M|, not yet folded
@@ -333,10 +398,11 @@ struct Ctx {
 template <int D, int PREC, int C, int I>
 __device__ __forceinline__ void left_site(Ctx<D, PREC>& x) {
     constexpr SiteStep st = PlanOf<D>::plan.steps[C * (D + 1) + I];
+    constexpr int ocin = LayoutOf<D>::lay.cin[C * (D + 1) + I];
+    constexpr int omout = LayoutOf<D>::lay.mout[C * (D + 1) + I];
     if (x.zero || x.bad) return;
-    float* cin = (I & 1) ? x.buf1 : x.buf0;
-    float* cout = (I & 1) ? x.buf0 : x.buf1;
-    float* M = st.tall ? x.qst + st.offQ : cout;
+    const float* cin = x.arena + ocin;
+    float* M = x.arena + omout;
     // power-of-two renormalisation, folded: the exponent of the previous
     // block's max |M| scales this site's factor (Z is linear in it), so no
     // block is rewritten and every block stays within one site's growth of 1
@@ -357,26 +423,16 @@ __device__ __forceinline__ void left_site(Ctx<D, PREC>& x) {
     __syncwarp();
 }
 
-// buffer that holds the right-sweep carry at site I: the left sweep leaves
-// its last carry in the cout of site D; every IDENT step swaps carry and T
-template <int D, int C, int I>
-__host__ __device__ constexpr int carry_buffer() {
-    int b = (D & 1) ? 0 : 1;
-    for (int i = D; i > I; --i)
-        if (PlanOf<D>::plan.steps[C * (D + 1) + i].rmode == R_IDENT) b ^= 1;
-    return b;
-}
-
 template <int D, int PREC, int C, int IDX>
 __device__ __forceinline__ void right_site(Ctx<D, PREC>& x) {
     constexpr int I = D - IDX;
     constexpr SiteStep st = PlanOf<D>::plan.steps[C * (D + 1) + I];
+    constexpr int ogin = LayoutOf<D>::lay.gin[C * (D + 1) + I];
+    constexpr int otout = LayoutOf<D>::lay.tout[C * (D + 1) + I];
+    constexpr int omout = LayoutOf<D>::lay.mout[C * (D + 1) + I];
     if (x.zero || x.bad) return;
-    constexpr int gb = carry_buffer<D, C, I>();
-    float* g = gb ? x.buf1 : x.buf0;
-    float* t = gb ? x.buf0 : x.buf1;
     right_step<st.K, st.S, st.pb, st.kq, st.ncol, st.tall, st.gid, st.rmode, st.nkind>(
-        x.qst + st.offQ, g, t, x.mps + st.offN, x.lane);
+        x.arena + omout, x.arena + ogin, x.arena + otout, x.mps + st.offN, x.lane);
     __syncwarp();
 }
 
@@ -395,8 +451,8 @@ __device__ __forceinline__ void all_columns(Ctx<D, PREC>& x, std::integer_sequen
 template <int D, int PREC, int I>
 __device__ __forceinline__ void final_site(Ctx<D, PREC>& x) {
     constexpr SiteStep st = PlanOf<D>::plan.steps[(D - 1) * (D + 1) + I];
-    const float* v = (I & 1) ? x.buf1 : x.buf0;
-    float* vn = (I & 1) ? x.buf0 : x.buf1;
+    const float* v = x.arena + ((I & 1) ? 64 : 0);
+    float* vn = x.arena + ((I & 1) ? 0 : 64);
     const float* site = x.mps + st.offN;
     for (int s = x.lane; s < st.S; s += 32) {
         float acc = 0.f;
@@ -444,7 +500,7 @@ __device__ __forceinline__ void decode_unit(const ExactArgs& a, float* ws, int64
 // warps, each with its own slice of the workspace, strides over the units.
 template <int D, int PREC, bool GLOBAL>
 __global__ void __launch_bounds__(256) decode_exact_kernel(ExactArgs a) {
-    constexpr int FPW = PlanOf<D>::plan.floats_per_warp;
+    constexpr int FPW = LayoutOf<D>::lay.floats_per_warp;
     extern __shared__ float4 smem4[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -463,18 +519,15 @@ __global__ void __launch_bounds__(256) decode_exact_kernel(ExactArgs a) {
 
 template <int D, int PREC>
 __device__ __forceinline__ void decode_unit(const ExactArgs& a, float* ws, int64_t unit, int lane) {
-    constexpr int OFF_W = PlanOf<D>::plan.off_w, OFF_MPS = PlanOf<D>::plan.off_mps;
-    constexpr int OFF_B0 = PlanOf<D>::plan.off_buf0, OFF_B1 = PlanOf<D>::plan.off_buf1;
-    constexpr int OFF_Q = PlanOf<D>::plan.off_q;
+    constexpr int OFF_W = LayoutOf<D>::lay.off_w, OFF_MPS = LayoutOf<D>::lay.off_mps;
+    constexpr int OFF_ARENA = LayoutOf<D>::lay.off_arena;
     constexpr int n = D * D;
     const int64_t b = unit >> 2;
     const int cls = (int)(unit & 3);
     Ctx<D, PREC> x;
     x.wts = ws + OFF_W;
     x.mps = ws + OFF_MPS;
-    x.buf0 = ws + OFF_B0;
-    x.buf1 = ws + OFF_B1;
-    x.qst = ws + OFF_Q;
+    x.arena = ws + OFF_ARENA;
     x.lane = lane;
     x.e2 = 0;
     x.pe = 0;
@@ -518,10 +571,10 @@ __device__ __forceinline__ void decode_unit(const ExactArgs& a, float* ws, int64
     all_columns<D, PREC>(x, std::make_integer_sequence<int, D>{});
     double logz = -INFINITY;
     if (!x.zero && !x.bad) {
-        if (lane == 0) x.buf0[0] = 1.f;
+        if (lane == 0) x.arena[0] = 1.f;
         __syncwarp();
         final_all<D, PREC>(x, std::make_integer_sequence<int, D + 1>{});
-        const float z = ((D + 1) & 1) ? x.buf1[0] : x.buf0[0];
+        const float z = x.arena[((D + 1) & 1) ? 64 : 0];
         if (!(z == z)) x.bad = true;
         else if (z > 0.f) logz = log((double)z) + (double)x.e2 * 0.69314718055994530942;
     }
@@ -537,7 +590,7 @@ constexpr int kSharedFloatsMax = (227 * 1024) / 4;
 
 template <int D, int PREC>
 bool launch_dp(const ExactArgs& a, cudaStream_t s, int warps_per_block) {
-    constexpr int FPW = PlanOf<D>::plan.floats_per_warp;
+    constexpr int FPW = LayoutOf<D>::lay.floats_per_warp;
     constexpr bool GLOBAL = FPW > kSharedFloatsMax;
     if (GLOBAL != (a.gws != nullptr)) return false;
     const size_t smem = GLOBAL ? 0 : (size_t)FPW * sizeof(float) * warps_per_block;

@@ -298,4 +298,160 @@ constexpr Plan make_plan(int d, int chi) {
     return P;
 }
 
+// Shared-memory layout of the untruncated sweep (a plan without truncating
+// columns). Every intermediate of a column -- the carry a left step passes to
+// the next, a tall block kept until the right sweep reaches its site, the
+// bond matrix T a right step passes to the one above -- lives in one per-warp
+// arena only between the step that writes it and the last step that reads it
+// (left step i at time i, right step i at time 2d+1-i). Offsets are assigned
+// from both ends of an arena sized to the largest total of simultaneously
+// live objects: each object goes to the end opposite the most recently
+// written object it overlaps in time, so a growing carry chain alternates
+// ends instead of fragmenting.
+struct ExactLayout {
+    int cin[kMaxSteps] = {};    // left step: incoming carry (when cid == 0)
+    int mout[kMaxSteps] = {};   // left step: its M blocks (the next carry, or the kept tall block)
+    int gin[kMaxSteps] = {};    // right step: incoming carry G (when gid == 0)
+    int tout[kMaxSteps] = {};   // right step: T (R_IDENT)
+    int arena = 0;              // floats of the arena
+    int off_w = 0, off_mps = 0, off_arena = 0, floats_per_warp = 0;
+    int ok = 0;                 // the plan truncates nowhere, so the layout applies
+};
+
+constexpr int kMaxColObj = 2 * (kMaxD + 1);
+
+// The intermediates of column c: [start, end] step times and sizes; idm[i] /
+// idt[i] index the output of left step i / the T of right step i (-1: none).
+struct ColumnObjects {
+    int n = 0;
+    int st[kMaxColObj] = {}, en[kMaxColObj] = {}, sz[kMaxColObj] = {};
+    int idm[kMaxD + 1] = {}, idt[kMaxD + 1] = {};
+};
+
+constexpr ColumnObjects column_objects(const Plan& P, int c) {
+    ColumnObjects O{};
+    const int d = P.d;
+    const SiteStep* S = &P.steps[c * (d + 1)];
+    for (int i = 0; i <= d; ++i) {
+        O.st[O.n] = i;
+        O.en[O.n] = S[i].tall ? 2 * d + 1 - i : i + 1;
+        O.sz[O.n] = align4(S[i].pb * S[i].K * S[i].ncol);
+        O.idm[i] = O.n++;
+    }
+    for (int i = d; i >= 0; --i) {
+        O.idt[i] = -1;
+        if (S[i].rmode == R_IDENT) {
+            O.st[O.n] = 2 * d + 1 - i;
+            O.en[O.n] = O.st[O.n] + 1;
+            O.sz[O.n] = align4(S[i].K * S[i].pb * S[i].S);
+            O.idt[i] = O.n++;
+        }
+    }
+    return O;
+}
+
+constexpr ExactLayout make_exact_layout(const Plan& P) {
+    ExactLayout L{};
+    if (P.svd_sites != 0) return L;
+    L.ok = 1;
+    const int d = P.d;
+    // the arena's lower bound: the largest total of live objects at one time
+    int cap = 128;                                  // the final contraction's two vectors: [0, 64), [64, 128)
+    for (int c = 0; c < d; ++c) {
+        const ColumnObjects O = column_objects(P, c);
+        for (int t = 0; t <= 2 * d + 2; ++t) {
+            int live = 0;
+            for (int a = 0; a < O.n; ++a)
+                if (O.st[a] <= t && t <= O.en[a]) live += O.sz[a];
+            cap = cmax(cap, live);
+        }
+    }
+    int hw = cap;
+    for (int c = 0; c < d; ++c) {
+        const ColumnObjects O = column_objects(P, c);
+        int off[kMaxColObj] = {}, top[kMaxColObj] = {};
+        for (int a = 0; a < O.n; ++a) {
+            // the end opposite the most recently written live object
+            int recent = -1;
+            for (int b = 0; b < a; ++b)
+                if (O.st[a] <= O.en[b] && O.st[b] <= O.en[a] && (recent < 0 || O.st[b] >= O.st[recent]))
+                    recent = b;
+            const bool want_top = recent >= 0 && !top[recent];
+            int o = 0;
+            bool placed = false;
+            if (want_top) {                         // highest free offset below the cap
+                o = cap - O.sz[a];
+                bool moved = true;
+                while (moved && o >= 0) {
+                    moved = false;
+                    for (int b = 0; b < a; ++b) {
+                        const bool live = O.st[a] <= O.en[b] && O.st[b] <= O.en[a];
+                        if (live && o < off[b] + O.sz[b] && off[b] < o + O.sz[a]) {
+                            o = off[b] - O.sz[a];
+                            moved = true;
+                        }
+                    }
+                }
+                placed = o >= 0;
+            }
+            if (!placed) {                          // lowest free offset
+                o = 0;
+                bool moved = true;
+                while (moved) {
+                    moved = false;
+                    for (int b = 0; b < a; ++b) {
+                        const bool live = O.st[a] <= O.en[b] && O.st[b] <= O.en[a];
+                        if (live && o < off[b] + O.sz[b] && off[b] < o + O.sz[a]) {
+                            o = off[b] + O.sz[b];
+                            moved = true;
+                        }
+                    }
+                }
+            }
+            off[a] = o;
+            top[a] = placed ? 1 : 0;
+            hw = cmax(hw, o + O.sz[a]);
+        }
+        for (int i = 0; i <= d; ++i) {
+            const int k = c * (d + 1) + i;
+            L.mout[k] = off[O.idm[i]];
+            L.cin[k] = i > 0 ? off[O.idm[i - 1]] : 0;
+            L.tout[k] = O.idt[i] >= 0 ? off[O.idt[i]] : 0;
+            L.gin[k] = i == d ? off[O.idm[d]] : (O.idt[i + 1] >= 0 ? off[O.idt[i + 1]] : 0);
+        }
+    }
+    L.arena = hw;
+    L.off_w = 0;
+    L.off_mps = align4(4 * d * d);
+    L.off_arena = L.off_mps + align4(P.max_mps);
+    L.floats_per_warp = L.off_arena + align4(hw);
+    return L;
+}
+
+// Compile-time check of a layout: objects live at the same time never share
+// a float, and every object lies inside the arena.
+constexpr bool exact_layout_valid(const Plan& P, const ExactLayout& L) {
+    if (!L.ok) return false;
+    const int d = P.d;
+    for (int c = 0; c < d; ++c) {
+        const ColumnObjects O = column_objects(P, c);
+        int off[kMaxColObj] = {};
+        for (int i = 0; i <= d; ++i) {
+            off[O.idm[i]] = L.mout[c * (d + 1) + i];
+            if (O.idt[i] >= 0) off[O.idt[i]] = L.tout[c * (d + 1) + i];
+        }
+        for (int a = 0; a < O.n; ++a) {
+            if (off[a] < 0 || off[a] + O.sz[a] > L.arena || (off[a] & 3)) return false;
+            for (int b = 0; b < a; ++b) {
+                const bool live = O.st[a] <= O.en[b] && O.st[b] <= O.en[a];
+                const bool mem = off[a] < off[b] + O.sz[b] && off[b] < off[a] + O.sz[a];
+                if (live && mem) return false;
+            }
+        }
+        for (int i = 1; i <= d; ++i)               // a left step reads what the one before it wrote
+            if (L.cin[c * (d + 1) + i] != L.mout[c * (d + 1) + i - 1]) return false;
+    }
+    return L.arena >= 128;
+}
+
 }  // namespace mld
