@@ -16,6 +16,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
 #include <utility>
 
 #include "mld_exact.h"
@@ -37,26 +38,22 @@ struct LayoutOf {
     static_assert(exact_layout_valid(PlanOf<D>::plan, lay), "overlapping live intermediates");
 };
 
-__device__ __forceinline__ float wmax(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
 // w(a, a', b, b') of the qubit factor, from its four weights p[E xor X^u Z^v]
-// indexed u + 2v; parity selects which plaquette pair carries u.
-__device__ __forceinline__ float wsel(const float4 w, int par, int a, int ap, int b, int bp) {
+// indexed u + 2v; the parity PAR selects which plaquette pair carries u.
+template <int PAR>
+__device__ __forceinline__ float wsel(const float4 w, int a, int ap, int b, int bp) {
     const int x1 = a ^ bp, x2 = ap ^ b;
-    const int u = par ? x2 : x1, v = par ? x1 : x2;
+    const int u = PAR ? x2 : x1, v = PAR ? x1 : x2;
     const int idx = u | (v << 1);
     return idx == 0 ? w.x : idx == 1 ? w.y : idx == 2 ? w.z : w.w;
 }
 
 // The eight weights w(a, a', beta, b') of a lane whose column fixes a',
 // indexed a | b' << 1 | beta << 2.
-__device__ __forceinline__ void weights8(const float4 w, int par, int ap, float (&o)[8]) {
+template <int PAR>
+__device__ __forceinline__ void weights8(const float4 w, int ap, float (&o)[8]) {
 #pragma unroll
-    for (int m = 0; m < 8; ++m) o[m] = wsel(w, par, m & 1, ap, (m >> 2) & 1, (m >> 1) & 1);
+    for (int m = 0; m < 8; ++m) o[m] = wsel<PAR>(w, m & 1, ap, (m >> 2) & 1, (m >> 1) & 1);
 }
 
 // X_a[k][col] = sum_r C[k][a*DL + r] A[r][col] for the identity cases
@@ -120,9 +117,9 @@ __device__ __forceinline__ void split_tf32(float x, unsigned& hi, unsigned& lo) 
 // Per 16-row block kb and group of up to four 8-column tiles, the k-steps
 // of 8 split one A fragment (both a) and the group's B fragments once and
 // issue three MMAs per (tile, a).
-template <int K, int PAM, int DL, int PA, int DR, int PB, int NCOL, int KQP>
+template <int K, int PAM, int DL, int PA, int DR, int PB, int NCOL, int KQP, int PAR>
 __device__ __forceinline__ float gemm_tf32(const float* __restrict__ C, const float* __restrict__ A,
-                                           float* __restrict__ M, const float4 w, int par, int lane) {
+                                           float* __restrict__ M, const float4 w, int lane) {
     constexpr int NCOLA = PA * DR;
     constexpr int LDC = PAM * DL;
     constexpr int KB = (K + 15) / 16;
@@ -132,8 +129,8 @@ __device__ __forceinline__ float gemm_tf32(const float* __restrict__ C, const fl
     const int g = lane >> 2, t = lane & 3;
     // the lane's weights for a' = 0 and a' = 1
     float wa[2][8];
-    weights8(w, par, 0, wa[0]);
-    weights8(w, par, 1, wa[1]);
+    weights8<PAR>(w, 0, wa[0]);
+    weights8<PAR>(w, 1, wa[1]);
     float mx = 0.f;
 #pragma unroll 1
     for (int kb = 0; kb < KB; ++kb) {
@@ -205,15 +202,19 @@ __device__ __forceinline__ float gemm_tf32(const float* __restrict__ C, const fl
 
 // One left-sweep site: M^{b'}[k][col] = sum_a w(a, a', beta(k), b') X_a[k][col].
 // Returns this lane's max |M|.
+//
+// Lanes own columns (col = cl + 32*cidx) and every RG-th row; the rows of a
+// lane split at k = KQP into the beta = 0 and beta = 1 halves, so inside each
+// half the factor weights are fixed registers.
 template <int K, int PAM, int DL, int PA, int DR, int PB, int NCOL, int KQP, int CID, int OKIND, int LAST,
-          int PREC>
+          int PREC, int PAR>
 __device__ __noinline__ float left_step(const float* __restrict__ C, const float* __restrict__ A,
-                                        float* __restrict__ M, const float4 w, int par, int lane) {
+                                        float* __restrict__ M, const float4 w, int lane) {
     constexpr int NCOLA = PA * DR;
     constexpr int LDC = PAM * DL;
     if constexpr (PREC == MLD_MIXED_TF32 && !CID && OKIND == K_DATA && !LAST && K >= 8 && DL >= 8 &&
                   NCOLA >= 8) {
-        return gemm_tf32<K, PAM, DL, PA, DR, PB, NCOL, KQP>(C, A, M, w, par, lane);
+        return gemm_tf32<K, PAM, DL, PA, DR, PB, NCOL, KQP, PAR>(C, A, M, w, lane);
     }
     float mx = 0.f;
     if constexpr (LAST) {
@@ -238,9 +239,9 @@ __device__ __noinline__ float left_step(const float* __restrict__ C, const float
                 } else {
                     x_ident<DL, DR, PAM, NCOLA, KQP, CID, OKIND>(C, A, k, ap, 0, X);
                 }
-                acc0 = fmaf(wsel(w, par, 0, ap, beta, 0), X[0], fmaf(wsel(w, par, 1, ap, beta, 0), X[1], acc0));
+                acc0 = fmaf(wsel<PAR>(w, 0, ap, beta, 0), X[0], fmaf(wsel<PAR>(w, 1, ap, beta, 0), X[1], acc0));
                 if (PB == 2)
-                    acc1 = fmaf(wsel(w, par, 0, ap, beta, 1), X[0], fmaf(wsel(w, par, 1, ap, beta, 1), X[1], acc1));
+                    acc1 = fmaf(wsel<PAR>(w, 0, ap, beta, 1), X[0], fmaf(wsel<PAR>(w, 1, ap, beta, 1), X[1], acc1));
             }
             M[k] = acc0;
             mx = fmaxf(mx, fabsf(acc0));
@@ -254,97 +255,135 @@ __device__ __noinline__ float left_step(const float* __restrict__ C, const float
     static_assert((NCOLA & (NCOLA - 1)) == 0, "power-of-two columns");
     constexpr int RG = NCOLA >= 32 ? 1 : 32 / NCOLA;     // row groups across the warp
     constexpr int CPL = NCOLA >= 32 ? NCOLA / 32 : 1;    // columns per lane
+    constexpr int NK = (K + RG - 1) / RG;                 // rows per lane
+    constexpr bool GEMM = !CID && OKIND == K_DATA;
     const int rg = lane / (32 / RG);
     const int cl = lane % (32 / RG);
+    if (K % RG != 0 && rg >= K) return 0.f;              // K < RG: lanes past the last row idle
 #pragma unroll
     for (int cidx = 0; cidx < CPL; ++cidx) {
         const int col = cl + 32 * cidx;
-        if (col >= NCOLA) continue;
         const int ap = col / DR, rp = col % DR;
         float wp[8];
-        weights8(w, par, ap, wp);
-        if constexpr (!CID && OKIND == K_DATA) {
-            // a real GEMM: this lane's column of A in registers
-            float acol[DL];
+        weights8<PAR>(w, ap, wp);
+        float acol[GEMM ? DL : 1];
+        if constexpr (GEMM) {
 #pragma unroll
             for (int r = 0; r < DL; ++r) acol[r] = A[r * NCOLA + col];
-            // KU rows of this lane per pass: 2*KU independent FMA chains
-            // (rows k = rg + j*RG, j < NK; when K < RG the lanes past K idle)
-            constexpr int NK = (K + RG - 1) / RG;
-            constexpr int KUMAX = DL <= 16 ? 4 : DL <= 32 ? 2 : 1;
-            constexpr int KU = NK < KUMAX ? NK : KUMAX;
-            if (K % RG != 0 && rg >= K) continue;
+        }
+        // rows j0 <= j < j1 of this lane (k = rg + j*RG), all with beta = BT
+        // (BT < 0: beta of the lane's single row, taken at run time)
+        auto rows = [&](auto bt_tag, int j0, int j1) {
+            constexpr int BT = decltype(bt_tag)::value;
+            float wb[PB][2];
+            const int beta_rt = BT >= 0 ? BT : (rg >= KQP ? 1 : 0);
+#pragma unroll
+            for (int bp = 0; bp < PB; ++bp) {
+                wb[bp][0] = beta_rt ? wp[(bp << 1) | 4] : wp[bp << 1];
+                wb[bp][1] = beta_rt ? wp[1 | (bp << 1) | 4] : wp[1 | (bp << 1)];
+            }
+            if constexpr (GEMM) {
+                // KU rows per pass: 2*KU independent FMA chains
+                constexpr int KUMAX = DL <= 16 ? 4 : DL <= 32 ? 2 : 1;
+                constexpr int NH = (BT >= 0 && K != KQP) ? NK / 2 : NK;
+                constexpr int KU = NH < KUMAX ? (NH < 1 ? 1 : NH) : KUMAX;
 #pragma unroll 1
-            for (int j0 = 0; j0 < NK; j0 += KU) {
-                float x0[KU], x1[KU];
+                for (int jj = j0; jj < j1; jj += KU) {
+                    float x0[KU], x1[KU];
 #pragma unroll
-                for (int u = 0; u < KU; ++u) {
-                    x0[u] = 0.f;
-                    x1[u] = 0.f;
-                }
-                if constexpr (DL % 4 == 0) {
+                    for (int u = 0; u < KU; ++u) {
+                        x0[u] = 0.f;
+                        x1[u] = 0.f;
+                    }
+                    if constexpr (DL % 4 == 0) {
 #pragma unroll
-                    for (int r = 0; r < DL; r += 4) {
+                        for (int r = 0; r < DL; r += 4) {
 #pragma unroll
-                        for (int u = 0; u < KU; ++u) {
-                            const float* c0 = C + (rg + (j0 + u) * RG) * LDC;
-                            const float4 v0 = *reinterpret_cast<const float4*>(c0 + r);
-                            x0[u] = fmaf(v0.x, acol[r], x0[u]);
-                            x0[u] = fmaf(v0.y, acol[r + 1], x0[u]);
-                            x0[u] = fmaf(v0.z, acol[r + 2], x0[u]);
-                            x0[u] = fmaf(v0.w, acol[r + 3], x0[u]);
-                            if (PAM == 2) {
-                                const float4 v1 = *reinterpret_cast<const float4*>(c0 + DL + r);
-                                x1[u] = fmaf(v1.x, acol[r], x1[u]);
-                                x1[u] = fmaf(v1.y, acol[r + 1], x1[u]);
-                                x1[u] = fmaf(v1.z, acol[r + 2], x1[u]);
-                                x1[u] = fmaf(v1.w, acol[r + 3], x1[u]);
+                            for (int u = 0; u < KU; ++u) {
+                                const float* c0 = C + (rg + (jj + u) * RG) * LDC;
+                                const float4 v0 = *reinterpret_cast<const float4*>(c0 + r);
+                                x0[u] = fmaf(v0.x, acol[r], x0[u]);
+                                x0[u] = fmaf(v0.y, acol[r + 1], x0[u]);
+                                x0[u] = fmaf(v0.z, acol[r + 2], x0[u]);
+                                x0[u] = fmaf(v0.w, acol[r + 3], x0[u]);
+                                if (PAM == 2) {
+                                    const float4 v1 = *reinterpret_cast<const float4*>(c0 + DL + r);
+                                    x1[u] = fmaf(v1.x, acol[r], x1[u]);
+                                    x1[u] = fmaf(v1.y, acol[r + 1], x1[u]);
+                                    x1[u] = fmaf(v1.z, acol[r + 2], x1[u]);
+                                    x1[u] = fmaf(v1.w, acol[r + 3], x1[u]);
+                                }
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < DL; ++r) {
+#pragma unroll
+                            for (int u = 0; u < KU; ++u) {
+                                const float* c0 = C + (rg + (jj + u) * RG) * LDC;
+                                x0[u] = fmaf(c0[r], acol[r], x0[u]);
+                                if (PAM == 2) x1[u] = fmaf(c0[DL + r], acol[r], x1[u]);
                             }
                         }
                     }
-                } else {
 #pragma unroll
-                    for (int r = 0; r < DL; ++r) {
+                    for (int u = 0; u < KU; ++u) {
+                        const int k = rg + (jj + u) * RG;
 #pragma unroll
-                        for (int u = 0; u < KU; ++u) {
-                            const float* c0 = C + (rg + (j0 + u) * RG) * LDC;
-                            x0[u] = fmaf(c0[r], acol[r], x0[u]);
-                            if (PAM == 2) x1[u] = fmaf(c0[DL + r], acol[r], x1[u]);
+                        for (int bp = 0; bp < PB; ++bp) {
+                            const float o = fmaf(wb[bp][0], x0[u], wb[bp][1] * x1[u]);
+                            M[(bp * K + k) * NCOL + col] = o;
+                            mx = fmaxf(mx, fabsf(o));
                         }
                     }
                 }
-#pragma unroll
-                for (int u = 0; u < KU; ++u) {
-                    const int k = rg + (j0 + u) * RG;
-                    const bool beta = (k / KQP) != 0;
+            } else {
+#pragma unroll 4
+                for (int jj = j0; jj < j1; ++jj) {
+                    const int k = rg + jj * RG;
+                    float X[2];
+                    x_ident<DL, DR, PAM, NCOLA, KQP, CID, OKIND>(C, A, k, ap, rp, X);
 #pragma unroll
                     for (int bp = 0; bp < PB; ++bp) {
-                        const float w0 = beta ? wp[(bp << 1) | 4] : wp[bp << 1];
-                        const float w1 = beta ? wp[1 | (bp << 1) | 4] : wp[1 | (bp << 1)];
-                        const float o = fmaf(w0, x0[u], w1 * x1[u]);
+                        const float o = fmaf(wb[bp][0], X[0], wb[bp][1] * X[1]);
                         M[(bp * K + k) * NCOL + col] = o;
                         mx = fmaxf(mx, fabsf(o));
                     }
                 }
             }
+        };
+        if constexpr (K == KQP) {
+            rows(std::integral_constant<int, 0>{}, 0, NK);
+        } else if constexpr (KQP % RG == 0) {
+            rows(std::integral_constant<int, 0>{}, 0, KQP / RG);
+            rows(std::integral_constant<int, 1>{}, KQP / RG, NK);
         } else {
-#pragma unroll 4
-            for (int k = rg; k < K; k += RG) {
-                float X[2];
-                x_ident<DL, DR, PAM, NCOLA, KQP, CID, OKIND>(C, A, k, ap, rp, X);
-                const bool beta = (k / KQP) != 0;
-#pragma unroll
-                for (int bp = 0; bp < PB; ++bp) {
-                    const float w0 = beta ? wp[(bp << 1) | 4] : wp[bp << 1];
-                    const float w1 = beta ? wp[1 | (bp << 1) | 4] : wp[1 | (bp << 1)];
-                    const float o = fmaf(w0, X[0], w1 * X[1]);
-                    M[(bp * K + k) * NCOL + col] = o;
-                    mx = fmaxf(mx, fabsf(o));
-                }
-            }
+            static_assert(NK == 1, "a lane's rows straddle beta only when it has one row");
+            rows(std::integral_constant<int, -1>{}, 0, NK);
         }
     }
     return mx;
+}
+
+// Element (r, cc) of T, cc = bb*S + s, for the steps without a product: a
+// relabeling of the kept block M (TALL, GID 1 or 2), the identity pattern
+// (GID, not TALL) or a relabeling of the carry G.
+template <int ROWS, int S, int KQ, int NC, int TALL, int GID>
+__device__ __forceinline__ float t_relabel(const float* __restrict__ Mq, const float* __restrict__ g, int r,
+                                           int bb, int s) {
+    if constexpr (TALL) {
+        const float* mrow = Mq + (bb * ROWS + r) * NC;
+        if constexpr (GID == 2) {
+            return mrow[s];
+        } else {
+            const int j = s - bb * KQ;
+            return (j >= 0 && j < NC) ? mrow[j] : 0.f;
+        }
+    } else {
+        const int grow = bb * ROWS + r;
+        if constexpr (GID) return (grow == s) ? 1.f : 0.f;
+        else return g[grow * S + s];
+    }
 }
 
 // One right-sweep site: T (ROWS x PB*S) from the kept block M (TALL) or the
@@ -353,33 +392,77 @@ __device__ __noinline__ float left_step(const float* __restrict__ C, const float
 template <int ROWS, int S, int PB, int KQ, int NC, int TALL, int GID, int RMODE, int NKIND>
 __device__ __noinline__ void right_step(const float* __restrict__ Mq, const float* __restrict__ g,
                                         float* __restrict__ t, float* __restrict__ site, int lane) {
+    constexpr int COLS = PB * S;
+    float* dst = (RMODE == R_DENSE) ? site : t;
     if constexpr (NKIND == K_IDL) {
         return;                                   // identity site, identity carry: nothing to form
+    } else if constexpr (TALL && GID == 0) {
+        // T^{bb}[r][s] = sum_j M^{bb}[r][j] G[bb*KQ + j][s]: lanes own columns
+        // cc (the G column in registers) and every RG-th row
+        constexpr int RG = COLS >= 32 ? 1 : 32 / COLS;
+        constexpr int CPL = COLS >= 32 ? COLS / 32 : 1;
+        constexpr int NR = (ROWS + RG - 1) / RG;
+        constexpr int KU = NR < 4 ? NR : 4;
+        static_assert((COLS & (COLS - 1)) == 0 && NR % KU == 0, "power-of-two shapes");
+        const int rg = lane / (32 / RG), cl = lane % (32 / RG);
+        if (ROWS % RG != 0 && rg >= ROWS) return;
+#pragma unroll
+        for (int cidx = 0; cidx < CPL; ++cidx) {
+            const int cc = cl + 32 * cidx, bb = cc / S, s = cc % S;
+            float gcol[NC];
+#pragma unroll
+            for (int j = 0; j < NC; ++j) gcol[j] = g[(bb * KQ + j) * S + s];
+#pragma unroll 1
+            for (int j0 = 0; j0 < NR; j0 += KU) {
+                float v[KU];
+#pragma unroll
+                for (int u = 0; u < KU; ++u) {
+                    const float* mrow = Mq + (bb * ROWS + rg + (j0 + u) * RG) * NC;
+                    v[u] = 0.f;
+                    if constexpr (NC % 4 == 0) {
+#pragma unroll
+                        for (int j = 0; j < NC; j += 4) {
+                            const float4 m4 = *reinterpret_cast<const float4*>(mrow + j);
+                            v[u] = fmaf(m4.x, gcol[j], v[u]);
+                            v[u] = fmaf(m4.y, gcol[j + 1], v[u]);
+                            v[u] = fmaf(m4.z, gcol[j + 2], v[u]);
+                            v[u] = fmaf(m4.w, gcol[j + 3], v[u]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < NC; ++j) v[u] = fmaf(mrow[j], gcol[j], v[u]);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < KU; ++u) dst[(rg + (j0 + u) * RG) * COLS + cc] = v[u];
+            }
+        }
+    } else if constexpr (S % 4 == 0) {
+        // four consecutive s of one (r, bb) per lane and pass
+        constexpr int C4 = COLS / 4;
+#pragma unroll 4
+        for (int e4 = lane; e4 < ROWS * C4; e4 += 32) {
+            const int r = e4 / C4, cc = 4 * (e4 % C4), bb = cc / S, s = cc % S;
+            float4 v;
+            if constexpr (!TALL && !GID) {
+                v = *reinterpret_cast<const float4*>(g + (bb * ROWS + r) * S + s);
+            } else if constexpr (TALL && GID == 1 && KQ % 4 == 0 && NC % 4 == 0) {
+                const int j = s - bb * KQ;
+                v = (j >= 0 && j < NC) ? *reinterpret_cast<const float4*>(Mq + (bb * ROWS + r) * NC + j)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                v.x = t_relabel<ROWS, S, KQ, NC, TALL, GID>(Mq, g, r, bb, s);
+                v.y = t_relabel<ROWS, S, KQ, NC, TALL, GID>(Mq, g, r, bb, s + 1);
+                v.z = t_relabel<ROWS, S, KQ, NC, TALL, GID>(Mq, g, r, bb, s + 2);
+                v.w = t_relabel<ROWS, S, KQ, NC, TALL, GID>(Mq, g, r, bb, s + 3);
+            }
+            *reinterpret_cast<float4*>(dst + 4 * e4) = v;
+        }
     } else {
-        constexpr int COLS = PB * S;
-        float* dst = (RMODE == R_DENSE) ? site : t;
+#pragma unroll 4
         for (int e = lane; e < ROWS * COLS; e += 32) {
             const int r = e / COLS, cc = e % COLS, bb = cc / S, s = cc % S;
-            float v;
-            if constexpr (TALL) {
-                const float* mrow = Mq + (bb * ROWS + r) * NC;
-                if constexpr (GID == 2) {
-                    v = mrow[s];
-                } else if constexpr (GID == 1) {
-                    const int j = s - bb * KQ;
-                    v = (j >= 0 && j < NC) ? mrow[j] : 0.f;
-                } else {
-                    const float* gcol = g + (bb * KQ) * S + s;
-                    v = 0.f;
-#pragma unroll
-                    for (int j = 0; j < NC; ++j) v = fmaf(mrow[j], gcol[j * S], v);
-                }
-            } else {
-                const int grow = bb * ROWS + r;
-                if constexpr (GID) v = (grow == s) ? 1.f : 0.f;
-                else v = g[grow * S + s];
-            }
-            dst[e] = v;
+            dst[e] = t_relabel<ROWS, S, KQ, NC, TALL, GID>(Mq, g, r, bb, s);
         }
     }
 }
@@ -411,13 +494,14 @@ __device__ __forceinline__ void left_site(Ctx<D, PREC>& x) {
     float4 w = I == 0 ? make_float4(1.f, 1.f, 1.f, 1.f)
                       : *reinterpret_cast<const float4*>(x.wts + 4 * ((I - 1) * D + C));
     w.x *= sc; w.y *= sc; w.z *= sc; w.w *= sc;
-    float mx = left_step<st.K, st.pam, st.Dl, st.pa, st.Dr, st.pb, st.ncol, st.kq_prev, st.cid, st.okind,
-                         (I == D), PREC>(cin, x.mps + st.offA, M, w, st.parity, x.lane);
-    mx = wmax(mx);
-    if (!(mx < INFINITY)) { x.bad = true; return; }
-    if (mx == 0.f) { x.zero = true; return; }
-    int ex;
-    frexpf(mx, &ex);
+    const float mx = left_step<st.K, st.pam, st.Dl, st.pa, st.Dr, st.pb, st.ncol, st.kq_prev, st.cid, st.okind,
+                               (I == D), PREC, st.parity>(cin, x.mps + st.offA, M, w, x.lane);
+    // max |M| over the warp as the integer maximum of the bit patterns (the
+    // order of non-negative floats); its biased exponent gives frexp's
+    const unsigned mbits = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+    if (mbits >= 0x7f800000u) { x.bad = true; return; }
+    if (mbits == 0u) { x.zero = true; return; }
+    const int ex = (int)(mbits >> 23) - 126;           // mx = m 2^ex, m in [0.5, 1)
     if (ex > 126 || ex < -125) { x.bad = true; return; }
     x.pe = ex;
     __syncwarp();
