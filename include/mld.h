@@ -56,9 +56,15 @@ typedef enum {
 typedef enum {
     MLD_FP32 = 0,              /* FP32 storage and arithmetic (FP64 only in the
                                   Jacobi rotation parameters and the log-norm) */
-    MLD_MIXED_BF16 = 1,        /* MPO.MPS products from BF16 operands, FP32
-                                  accumulate, power-of-two column scaling */
-    MLD_MIXED_TF32 = 2         /* the same with TF32 operands */
+    MLD_MIXED_BF16 = 1,        /* reserved: MLD_ERR_UNSUPPORTED (BF16 operands
+                                  miss |d ln Z| <= 1e-3 on the leading coset) */
+    MLD_MIXED_TF32 = 2         /* data-site MPO.MPS products on the tensor
+                                  cores from operands split into two TF32
+                                  parts (hi.hi + hi.lo + lo.hi), FP32
+                                  accumulate; untruncated chi only. The split
+                                  products run at d = 9 and 11, where they are
+                                  faster; at other d the FP32 products run
+                                  (same or better accuracy) */
 } mld_precision;
 
 typedef enum {

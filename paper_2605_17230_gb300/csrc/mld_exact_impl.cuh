@@ -38,6 +38,23 @@ struct LayoutOf {
     static_assert(exact_layout_valid(PlanOf<D>::plan, lay), "overlapping live intermediates");
 };
 
+// Float index within a row of an M block of row length NC (the carry of the
+// next left step, or a tall block kept for the right sweep). In the mixed-
+// precision kernel (SW = 1) the row's float4 slots are XOR-permuted by the row
+// index, so that the same column of eight consecutive rows falls in eight
+// different bank groups (rows are multiples of 32 floats long) for the
+// tensor-core fragment loads; rows shorter than 8 floats, and every row of the
+// FP32 kernel (whose loads are warp broadcasts), are stored as they are.
+template <int NC, int SW>
+__device__ __forceinline__ int swz(int row, int col) {
+    if constexpr (SW && NC >= 8) {
+        constexpr int Q = NC / 4 < 8 ? NC / 4 : 8;
+        return col ^ ((row & (Q - 1)) << 2);
+    } else {
+        return col;
+    }
+}
+
 // w(a, a', b, b') of the qubit factor, from its four weights p[E xor X^u Z^v]
 // indexed u + 2v; the parity PAR selects which plaquette pair carries u.
 template <int PAR>
@@ -58,7 +75,7 @@ __device__ __forceinline__ void weights8(const float4 w, int ap, float (&o)[8]) 
 
 // X_a[k][col] = sum_r C[k][a*DL + r] A[r][col] for the identity cases
 // (identity carry and/or identity old site), where the sum has one term.
-template <int DL, int DR, int PAM, int NCOLA, int KQP, int CID, int OKIND>
+template <int DL, int DR, int PAM, int NCOLA, int KQP, int CID, int OKIND, int SW>
 __device__ __forceinline__ void x_ident(const float* C, const float* A, int k, int ap, int rp, float X[2]) {
     constexpr int LDC = PAM * DL;
     X[0] = 0.f;
@@ -73,12 +90,12 @@ __device__ __forceinline__ void x_ident(const float* C, const float* A, int k, i
     } else {
 #pragma unroll
         for (int a = 0; a < PAM; ++a) {
-            const float* crow = C + k * LDC + a * DL;
+            const float* crow = C + k * LDC;
             if constexpr (OKIND == K_IDR) {
-                X[a] = crow[ap * DR + rp];
+                X[a] = crow[swz<LDC, SW>(k, a * DL + ap * DR + rp)];
             } else {
                 const int r = rp - ap * DL;
-                X[a] = (r >= 0 && r < DL) ? crow[r] : 0.f;
+                X[a] = (r >= 0 && r < DL) ? crow[swz<LDC, SW>(k, a * DL + r)] : 0.f;
             }
         }
     }
@@ -125,6 +142,7 @@ __device__ __forceinline__ float gemm_tf32(const float* __restrict__ C, const fl
     constexpr int KB = (K + 15) / 16;
     constexpr int NT = NCOLA / 8, KS = DL / 8;
     constexpr int NTG = NT < 4 ? NT : 4;
+    constexpr int SW = 1;
     static_assert(DL % 8 == 0 && NCOLA % 8 == 0 && NT % NTG == 0, "tensor-core tile shape");
     const int g = lane >> 2, t = lane & 3;
     // the lane's weights for a' = 0 and a' = 1
@@ -149,12 +167,13 @@ __device__ __forceinline__ float gemm_tf32(const float* __restrict__ C, const fl
                 unsigned ah[2][4], al[2][4];
 #pragma unroll
                 for (int a = 0; a < PAM; ++a) {
-                    const float* c0 = C + r0 * LDC + a * DL + 8 * ks;
-                    const float* c1 = C + r1 * LDC + a * DL + 8 * ks;
-                    split_tf32(r0 < K ? c0[t] : 0.f, ah[a][0], al[a][0]);
-                    split_tf32(r1 < K ? c1[t] : 0.f, ah[a][1], al[a][1]);
-                    split_tf32(r0 < K ? c0[t + 4] : 0.f, ah[a][2], al[a][2]);
-                    split_tf32(r1 < K ? c1[t + 4] : 0.f, ah[a][3], al[a][3]);
+                    const float* c0 = C + r0 * LDC;
+                    const float* c1 = C + r1 * LDC;
+                    const int q0 = a * DL + 8 * ks + t;
+                    split_tf32(r0 < K ? c0[swz<LDC, SW>(r0, q0)] : 0.f, ah[a][0], al[a][0]);
+                    split_tf32(r1 < K ? c1[swz<LDC, SW>(r1, q0)] : 0.f, ah[a][1], al[a][1]);
+                    split_tf32(r0 < K ? c0[swz<LDC, SW>(r0, q0 + 4)] : 0.f, ah[a][2], al[a][2]);
+                    split_tf32(r1 < K ? c1[swz<LDC, SW>(r1, q0 + 4)] : 0.f, ah[a][3], al[a][3]);
                 }
 #pragma unroll
                 for (int j = 0; j < NTG; ++j) {
@@ -189,12 +208,158 @@ __device__ __forceinline__ float gemm_tf32(const float* __restrict__ C, const fl
                             const float w0 = ap ? wa[1][m0] : wa[0][m0];
                             const float w1 = ap ? wa[1][m0 | 1] : wa[0][m0 | 1];
                             const float o = fmaf(w0, x0, w1 * x1);
-                            M[(bp * K + k) * NCOL + col] = o;
+                            M[(bp * K + k) * NCOL + swz<NCOL, SW>(bp * K + k, col)] = o;
                             mx = fmaxf(mx, fabsf(o));
                         }
                     }
                 }
             }
+        }
+    }
+    return mx;
+}
+
+// Four consecutive columns col..col+3 (one a', rp..rp+3) of X_a for the
+// identity cases, as float4 (DR % 4 == 0; DL % 4 == 0 unless the carry is
+// the identity).
+template <int DL, int DR, int PAM, int NCOLA, int KQP, int CID, int OKIND, int SW>
+__device__ __forceinline__ void x_ident4(const float* C, const float* A, int k, int ap, int rp, float4 X[2]) {
+    constexpr int LDC = PAM * DL;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    X[0] = z;
+    X[1] = z;
+    if constexpr (CID) {
+        const int j = k % KQP, ja = j / DL, jr = j % DL;
+        float4 av;
+        if constexpr (OKIND == K_DATA) {
+            av = *reinterpret_cast<const float4*>(A + jr * NCOLA + ap * DR + rp);
+        } else {
+            const int hit = OKIND == K_IDR ? jr - (ap * DR + rp) : ap * DL + jr - rp;   // which of the four is 1
+            av.x = hit == 0 ? 1.f : 0.f;
+            av.y = hit == 1 ? 1.f : 0.f;
+            av.z = hit == 2 ? 1.f : 0.f;
+            av.w = hit == 3 ? 1.f : 0.f;
+        }
+        if (ja == 0) X[0] = av; else X[1] = av;
+    } else {
+#pragma unroll
+        for (int a = 0; a < PAM; ++a) {
+            const float* crow = C + k * LDC;
+            if constexpr (OKIND == K_IDR) {
+                X[a] = *reinterpret_cast<const float4*>(crow + swz<LDC, SW>(k, a * DL + ap * DR + rp));
+            } else {
+                const int r = rp - ap * DL;
+                if (r >= 0 && r < DL) X[a] = *reinterpret_cast<const float4*>(crow + swz<LDC, SW>(k, a * DL + r));
+            }
+        }
+    }
+}
+
+// Left-sweep site with four columns per lane (float4 loads and stores; the
+// data-site product keeps four A columns in registers, so each broadcast C
+// element feeds four FMAs). Lanes own column groups and every RG-th row; as
+// in left_step the rows split at KQP into the two beta halves.
+template <int K, int PAM, int DL, int PA, int DR, int PB, int NCOL, int KQP, int CID, int OKIND, int PAR, int SW>
+__device__ __forceinline__ float left_cols4(const float* __restrict__ C, const float* __restrict__ A,
+                                            float* __restrict__ M, const float4 w, int lane) {
+    constexpr int NCOLA = PA * DR;
+    constexpr int LDC = PAM * DL;
+    constexpr int NCW = NCOLA / 4;                       // column groups
+    constexpr int RG = NCW >= 32 ? 1 : 32 / NCW;
+    constexpr int CPL = NCW >= 32 ? NCW / 32 : 1;
+    constexpr int NK = (K + RG - 1) / RG;
+    constexpr bool GEMM = !CID && OKIND == K_DATA;
+    static_assert(NCOLA % 4 == 0 && DR % 4 == 0 && NCOL == NCOLA, "four-column groups");
+    const int rg = lane / (32 / RG);
+    const int cl = lane % (32 / RG);
+    float mx = 0.f;
+    if (K % RG != 0 && rg >= K) return mx;
+#pragma unroll
+    for (int cidx = 0; cidx < CPL; ++cidx) {
+        const int col = 4 * (cl + 32 * cidx);
+        const int ap = col / DR, rp = col % DR;
+        float wp[8];
+        weights8<PAR>(w, ap, wp);
+        float4 acol[GEMM ? DL : 1];
+        if constexpr (GEMM) {
+#pragma unroll
+            for (int r = 0; r < DL; ++r) acol[r] = *reinterpret_cast<const float4*>(A + r * NCOLA + col);
+        }
+        auto rows = [&](auto bt_tag, int j0, int j1) {
+            constexpr int BT = decltype(bt_tag)::value;
+            float wb[PB][2];
+            const int beta_rt = BT >= 0 ? BT : (rg >= KQP ? 1 : 0);
+#pragma unroll
+            for (int bp = 0; bp < PB; ++bp) {
+                wb[bp][0] = beta_rt ? wp[(bp << 1) | 4] : wp[bp << 1];
+                wb[bp][1] = beta_rt ? wp[1 | (bp << 1) | 4] : wp[1 | (bp << 1)];
+            }
+            auto emit = [&](int k, const float4& x0, const float4& x1) {
+#pragma unroll
+                for (int bp = 0; bp < PB; ++bp) {
+                    float4 o;
+                    o.x = fmaf(wb[bp][0], x0.x, wb[bp][1] * x1.x);
+                    o.y = fmaf(wb[bp][0], x0.y, wb[bp][1] * x1.y);
+                    o.z = fmaf(wb[bp][0], x0.z, wb[bp][1] * x1.z);
+                    o.w = fmaf(wb[bp][0], x0.w, wb[bp][1] * x1.w);
+                    *reinterpret_cast<float4*>(M + (bp * K + k) * NCOL + swz<NCOL, SW>(bp * K + k, col)) = o;
+                    mx = fmaxf(mx, fmaxf(fmaxf(fabsf(o.x), fabsf(o.y)), fmaxf(fabsf(o.z), fabsf(o.w))));
+                }
+            };
+            if constexpr (GEMM) {
+                constexpr int KUMAX = DL <= 8 ? 4 : DL <= 16 ? 2 : 1;
+                constexpr int NH = (BT >= 0 && K != KQP) ? NK / 2 : NK;
+                constexpr int KU = NH < KUMAX ? (NH < 1 ? 1 : NH) : KUMAX;
+#pragma unroll 1
+                for (int jj = j0; jj < j1; jj += KU) {
+                    float4 x0[KU], x1[KU];
+#pragma unroll
+                    for (int u = 0; u < KU; ++u) {
+                        x0[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        x1[u] = x0[u];
+                    }
+#pragma unroll
+                    for (int r = 0; r < DL; r += 4) {
+#pragma unroll
+                        for (int u = 0; u < KU; ++u) {
+                            const int row = rg + (jj + u) * RG;
+                            const float* c0 = C + row * LDC;
+#pragma unroll
+                            for (int a = 0; a < PAM; ++a) {
+                                const float4 v = *reinterpret_cast<const float4*>(c0 + swz<LDC, SW>(row, a * DL + r));
+                                float4& x = a ? x1[u] : x0[u];
+                                const float cv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) {
+                                    x.x = fmaf(cv[q], acol[r + q].x, x.x);
+                                    x.y = fmaf(cv[q], acol[r + q].y, x.y);
+                                    x.z = fmaf(cv[q], acol[r + q].z, x.z);
+                                    x.w = fmaf(cv[q], acol[r + q].w, x.w);
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < KU; ++u) emit(rg + (jj + u) * RG, x0[u], x1[u]);
+                }
+            } else {
+#pragma unroll 2
+                for (int jj = j0; jj < j1; ++jj) {
+                    const int k = rg + jj * RG;
+                    float4 X[2];
+                    x_ident4<DL, DR, PAM, NCOLA, KQP, CID, OKIND, SW>(C, A, k, ap, rp, X);
+                    emit(k, X[0], X[1]);
+                }
+            }
+        };
+        if constexpr (K == KQP) {
+            rows(std::integral_constant<int, 0>{}, 0, NK);
+        } else if constexpr (KQP % RG == 0) {
+            rows(std::integral_constant<int, 0>{}, 0, KQP / RG);
+            rows(std::integral_constant<int, 1>{}, KQP / RG, NK);
+        } else {
+            static_assert(NK == 1, "a lane's rows straddle beta only when it has one row");
+            rows(std::integral_constant<int, -1>{}, 0, NK);
         }
     }
     return mx;
@@ -212,9 +377,18 @@ __device__ __noinline__ float left_step(const float* __restrict__ C, const float
                                         float* __restrict__ M, const float4 w, int lane) {
     constexpr int NCOLA = PA * DR;
     constexpr int LDC = PAM * DL;
+    constexpr int SW = PREC == MLD_MIXED_TF32 ? 1 : 0;
     if constexpr (PREC == MLD_MIXED_TF32 && !CID && OKIND == K_DATA && !LAST && K >= 8 && DL >= 8 &&
                   NCOLA >= 8) {
         return gemm_tf32<K, PAM, DL, PA, DR, PB, NCOL, KQP, PAR>(C, A, M, w, lane);
+    }
+    // four columns per lane where a step has at least 64 float4 outputs per
+    // beta' block; for a data-site product only with the swizzled layout
+    // (its four row groups read the same column of four rows)
+    constexpr bool DATA_PRODUCT = !CID && OKIND == K_DATA;
+    if constexpr (!LAST && DR % 4 == 0 && (CID || DL % 4 == 0) && K * NCOLA / 4 >= 64 &&
+                  (!DATA_PRODUCT || (SW && DL <= 32))) {
+        return left_cols4<K, PAM, DL, PA, DR, PB, NCOL, KQP, CID, OKIND, PAR, SW>(C, A, M, w, lane);
     }
     float mx = 0.f;
     if constexpr (LAST) {
@@ -230,14 +404,14 @@ __device__ __noinline__ float left_step(const float* __restrict__ C, const float
                     for (int a = 0; a < 2; ++a) {
                         float s = 0.f;
                         if (a < PAM) {
-                            const float* crow = C + k * LDC + a * DL;
+                            const float* crow = C + k * LDC;
 #pragma unroll
-                            for (int r = 0; r < DL; ++r) s = fmaf(crow[r], A[r * NCOLA + ap], s);
+                            for (int r = 0; r < DL; ++r) s = fmaf(crow[swz<LDC, SW>(k, a * DL + r)], A[r * NCOLA + ap], s);
                         }
                         X[a] = s;
                     }
                 } else {
-                    x_ident<DL, DR, PAM, NCOLA, KQP, CID, OKIND>(C, A, k, ap, 0, X);
+                    x_ident<DL, DR, PAM, NCOLA, KQP, CID, OKIND, SW>(C, A, k, ap, 0, X);
                 }
                 acc0 = fmaf(wsel<PAR>(w, 0, ap, beta, 0), X[0], fmaf(wsel<PAR>(w, 1, ap, beta, 0), X[1], acc0));
                 if (PB == 2)
@@ -300,14 +474,15 @@ __device__ __noinline__ float left_step(const float* __restrict__ C, const float
                         for (int r = 0; r < DL; r += 4) {
 #pragma unroll
                             for (int u = 0; u < KU; ++u) {
-                                const float* c0 = C + (rg + (jj + u) * RG) * LDC;
-                                const float4 v0 = *reinterpret_cast<const float4*>(c0 + r);
+                                const int row = rg + (jj + u) * RG;
+                                const float* c0 = C + row * LDC;
+                                const float4 v0 = *reinterpret_cast<const float4*>(c0 + swz<LDC, SW>(row, r));
                                 x0[u] = fmaf(v0.x, acol[r], x0[u]);
                                 x0[u] = fmaf(v0.y, acol[r + 1], x0[u]);
                                 x0[u] = fmaf(v0.z, acol[r + 2], x0[u]);
                                 x0[u] = fmaf(v0.w, acol[r + 3], x0[u]);
                                 if (PAM == 2) {
-                                    const float4 v1 = *reinterpret_cast<const float4*>(c0 + DL + r);
+                                    const float4 v1 = *reinterpret_cast<const float4*>(c0 + swz<LDC, SW>(row, DL + r));
                                     x1[u] = fmaf(v1.x, acol[r], x1[u]);
                                     x1[u] = fmaf(v1.y, acol[r + 1], x1[u]);
                                     x1[u] = fmaf(v1.z, acol[r + 2], x1[u]);
@@ -320,9 +495,10 @@ __device__ __noinline__ float left_step(const float* __restrict__ C, const float
                         for (int r = 0; r < DL; ++r) {
 #pragma unroll
                             for (int u = 0; u < KU; ++u) {
-                                const float* c0 = C + (rg + (jj + u) * RG) * LDC;
-                                x0[u] = fmaf(c0[r], acol[r], x0[u]);
-                                if (PAM == 2) x1[u] = fmaf(c0[DL + r], acol[r], x1[u]);
+                                const int row = rg + (jj + u) * RG;
+                                const float* c0 = C + row * LDC;
+                                x0[u] = fmaf(c0[swz<LDC, SW>(row, r)], acol[r], x0[u]);
+                                if (PAM == 2) x1[u] = fmaf(c0[swz<LDC, SW>(row, DL + r)], acol[r], x1[u]);
                             }
                         }
                     }
@@ -332,7 +508,7 @@ __device__ __noinline__ float left_step(const float* __restrict__ C, const float
 #pragma unroll
                         for (int bp = 0; bp < PB; ++bp) {
                             const float o = fmaf(wb[bp][0], x0[u], wb[bp][1] * x1[u]);
-                            M[(bp * K + k) * NCOL + col] = o;
+                            M[(bp * K + k) * NCOL + swz<NCOL, SW>(bp * K + k, col)] = o;
                             mx = fmaxf(mx, fabsf(o));
                         }
                     }
@@ -342,11 +518,11 @@ __device__ __noinline__ float left_step(const float* __restrict__ C, const float
                 for (int jj = j0; jj < j1; ++jj) {
                     const int k = rg + jj * RG;
                     float X[2];
-                    x_ident<DL, DR, PAM, NCOLA, KQP, CID, OKIND>(C, A, k, ap, rp, X);
+                    x_ident<DL, DR, PAM, NCOLA, KQP, CID, OKIND, SW>(C, A, k, ap, rp, X);
 #pragma unroll
                     for (int bp = 0; bp < PB; ++bp) {
                         const float o = fmaf(wb[bp][0], X[0], wb[bp][1] * X[1]);
-                        M[(bp * K + k) * NCOL + col] = o;
+                        M[(bp * K + k) * NCOL + swz<NCOL, SW>(bp * K + k, col)] = o;
                         mx = fmaxf(mx, fabsf(o));
                     }
                 }
@@ -368,16 +544,17 @@ __device__ __noinline__ float left_step(const float* __restrict__ C, const float
 // Element (r, cc) of T, cc = bb*S + s, for the steps without a product: a
 // relabeling of the kept block M (TALL, GID 1 or 2), the identity pattern
 // (GID, not TALL) or a relabeling of the carry G.
-template <int ROWS, int S, int KQ, int NC, int TALL, int GID>
+template <int ROWS, int S, int KQ, int NC, int TALL, int GID, int SW>
 __device__ __forceinline__ float t_relabel(const float* __restrict__ Mq, const float* __restrict__ g, int r,
                                            int bb, int s) {
     if constexpr (TALL) {
-        const float* mrow = Mq + (bb * ROWS + r) * NC;
+        const int row = bb * ROWS + r;
+        const float* mrow = Mq + row * NC;
         if constexpr (GID == 2) {
-            return mrow[s];
+            return mrow[swz<NC, SW>(row, s)];
         } else {
             const int j = s - bb * KQ;
-            return (j >= 0 && j < NC) ? mrow[j] : 0.f;
+            return (j >= 0 && j < NC) ? mrow[swz<NC, SW>(row, j)] : 0.f;
         }
     } else {
         const int grow = bb * ROWS + r;
@@ -389,7 +566,7 @@ __device__ __forceinline__ float t_relabel(const float* __restrict__ Mq, const f
 // One right-sweep site: T (ROWS x PB*S) from the kept block M (TALL) or the
 // carry G, then IDENT (carry = T, written to t) or DENSE (site = T, written
 // straight into the MPS buffer; carry = identity).
-template <int ROWS, int S, int PB, int KQ, int NC, int TALL, int GID, int RMODE, int NKIND>
+template <int ROWS, int S, int PB, int KQ, int NC, int TALL, int GID, int RMODE, int NKIND, int SW>
 __device__ __noinline__ void right_step(const float* __restrict__ Mq, const float* __restrict__ g,
                                         float* __restrict__ t, float* __restrict__ site, int lane) {
     constexpr int COLS = PB * S;
@@ -417,12 +594,13 @@ __device__ __noinline__ void right_step(const float* __restrict__ Mq, const floa
                 float v[KU];
 #pragma unroll
                 for (int u = 0; u < KU; ++u) {
-                    const float* mrow = Mq + (bb * ROWS + rg + (j0 + u) * RG) * NC;
+                    const int row = bb * ROWS + rg + (j0 + u) * RG;
+                    const float* mrow = Mq + row * NC;
                     v[u] = 0.f;
                     if constexpr (NC % 4 == 0) {
 #pragma unroll
                         for (int j = 0; j < NC; j += 4) {
-                            const float4 m4 = *reinterpret_cast<const float4*>(mrow + j);
+                            const float4 m4 = *reinterpret_cast<const float4*>(mrow + swz<NC, SW>(row, j));
                             v[u] = fmaf(m4.x, gcol[j], v[u]);
                             v[u] = fmaf(m4.y, gcol[j + 1], v[u]);
                             v[u] = fmaf(m4.z, gcol[j + 2], v[u]);
@@ -430,7 +608,7 @@ __device__ __noinline__ void right_step(const float* __restrict__ Mq, const floa
                         }
                     } else {
 #pragma unroll
-                        for (int j = 0; j < NC; ++j) v[u] = fmaf(mrow[j], gcol[j], v[u]);
+                        for (int j = 0; j < NC; ++j) v[u] = fmaf(mrow[swz<NC, SW>(row, j)], gcol[j], v[u]);
                     }
                 }
 #pragma unroll
@@ -448,13 +626,14 @@ __device__ __noinline__ void right_step(const float* __restrict__ Mq, const floa
                 v = *reinterpret_cast<const float4*>(g + (bb * ROWS + r) * S + s);
             } else if constexpr (TALL && GID == 1 && KQ % 4 == 0 && NC % 4 == 0) {
                 const int j = s - bb * KQ;
-                v = (j >= 0 && j < NC) ? *reinterpret_cast<const float4*>(Mq + (bb * ROWS + r) * NC + j)
+                v = (j >= 0 && j < NC) ? *reinterpret_cast<const float4*>(Mq + (bb * ROWS + r) * NC +
+                                                                          swz<NC, SW>(bb * ROWS + r, j))
                                        : make_float4(0.f, 0.f, 0.f, 0.f);
             } else {
-                v.x = t_relabel<ROWS, S, KQ, NC, TALL, GID>(Mq, g, r, bb, s);
-                v.y = t_relabel<ROWS, S, KQ, NC, TALL, GID>(Mq, g, r, bb, s + 1);
-                v.z = t_relabel<ROWS, S, KQ, NC, TALL, GID>(Mq, g, r, bb, s + 2);
-                v.w = t_relabel<ROWS, S, KQ, NC, TALL, GID>(Mq, g, r, bb, s + 3);
+                v.x = t_relabel<ROWS, S, KQ, NC, TALL, GID, SW>(Mq, g, r, bb, s);
+                v.y = t_relabel<ROWS, S, KQ, NC, TALL, GID, SW>(Mq, g, r, bb, s + 1);
+                v.z = t_relabel<ROWS, S, KQ, NC, TALL, GID, SW>(Mq, g, r, bb, s + 2);
+                v.w = t_relabel<ROWS, S, KQ, NC, TALL, GID, SW>(Mq, g, r, bb, s + 3);
             }
             *reinterpret_cast<float4*>(dst + 4 * e4) = v;
         }
@@ -462,7 +641,7 @@ __device__ __noinline__ void right_step(const float* __restrict__ Mq, const floa
 #pragma unroll 4
         for (int e = lane; e < ROWS * COLS; e += 32) {
             const int r = e / COLS, cc = e % COLS, bb = cc / S, s = cc % S;
-            dst[e] = t_relabel<ROWS, S, KQ, NC, TALL, GID>(Mq, g, r, bb, s);
+            dst[e] = t_relabel<ROWS, S, KQ, NC, TALL, GID, SW>(Mq, g, r, bb, s);
         }
     }
 }
@@ -515,7 +694,8 @@ __device__ __forceinline__ void right_site(Ctx<D, PREC>& x) {
     constexpr int otout = LayoutOf<D>::lay.tout[C * (D + 1) + I];
     constexpr int omout = LayoutOf<D>::lay.mout[C * (D + 1) + I];
     if (x.zero || x.bad) return;
-    right_step<st.K, st.S, st.pb, st.kq, st.ncol, st.tall, st.gid, st.rmode, st.nkind>(
+    right_step<st.K, st.S, st.pb, st.kq, st.ncol, st.tall, st.gid, st.rmode, st.nkind,
+               PREC == MLD_MIXED_TF32 ? 1 : 0>(
         x.arena + omout, x.arena + ogin, x.arena + otout, x.mps + st.offN, x.lane);
     __syncwarp();
 }
@@ -688,9 +868,20 @@ bool launch_dp(const ExactArgs& a, cudaStream_t s, int warps_per_block) {
     return cudaGetLastError() == cudaSuccess;
 }
 
+// Distances whose mixed-precision kernel (split-TF32 tensor-core products,
+// swizzled blocks) is faster than the FP32 one; at the others the products
+// are too small for the split and the fragment traffic to pay, and a
+// mixed-precision request runs the FP32 kernel.
+template <int D>
+constexpr bool kTensorPays = D == 9 || D == 11;
+
 template <int D>
 bool launch_d(const ExactArgs& a, cudaStream_t s, int warps_per_block, int precision) {
-    if (precision == MLD_MIXED_TF32) return launch_dp<D, MLD_MIXED_TF32>(a, s, warps_per_block);
+    if constexpr (kTensorPays<D>) {
+        if (precision == MLD_MIXED_TF32) return launch_dp<D, MLD_MIXED_TF32>(a, s, warps_per_block);
+    } else {
+        if (precision == MLD_MIXED_TF32) return launch_dp<D, MLD_FP32>(a, s, warps_per_block);
+    }
     if (precision == MLD_FP32) return launch_dp<D, MLD_FP32>(a, s, warps_per_block);
     return false;
 }

@@ -225,6 +225,8 @@ def test_mixed_tf32_vs_oracle_and_fp32(mld, d, chi):
     np.testing.assert_allclose(lpm, ref, rtol=0, atol=TOL)
     np.testing.assert_allclose(lpm, lp32, rtol=0, atol=TOL)
     check_argmax(am, ref)
+    if d not in (9, 11):                 # tensor-core products only where they pay: FP32 kernel
+        assert np.array_equal(lpm, lp32)
 
 
 def test_mixed_unsupported_cases(mld):
