@@ -35,6 +35,25 @@ SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 METRIC = "syndromes/s at d=9 χ=32 (4 cosets), mixed-precision vs FP32, |ΔlogP|≤1e-3"
 
+# DRAM bytes per syndrome of the decode kernel (dram__bytes_read.sum + write.sum of one ncu
+# capture of 8,192 syndromes, profiles/decode_exact_d9_chi32_full.md), valid only for the kernel
+# sources they were taken on: any change to them makes the traffic unknown (null).
+TRAFFIC_SOURCES_SHA = "9007817cabbabbb0"
+TRAFFIC_BYTES_PER_SYNDROME = {0: 373.76e3 / 8192, 2: 387.072e3 / 8192}
+
+
+def kernel_sources_sha():
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2605_17230_gb300", "csrc", "*")))
+    for f in files + [os.path.join(ROOT, "include", "mld.h")]:
+        if os.path.isfile(f) and f.rsplit(".", 1)[-1] in ("cu", "cuh", "h", "cpp"):
+            h.update(os.path.basename(f).encode())
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
 
 def _env_int(k, dflt):
     try:
@@ -373,6 +392,9 @@ def main():
     flops_per_syn = code.flops(CHI, prec_mixed)
     achieved = Bn * flops_per_syn / (statistics.median(ms) / 1e3) / 1e12
     peak = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    traffic = (TRAFFIC_BYTES_PER_SYNDROME[prec_mixed] * Bn
+               if kernel_sources_sha() == TRAFFIC_SOURCES_SHA and prec_mixed in TRAFFIC_BYTES_PER_SYNDROME
+               else None)
     line = {
         "metric": METRIC, "value": value, "unit": "syndromes/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
@@ -387,9 +409,11 @@ def main():
         "fp32": {"value": value32, "ms_per_step": 1e3 * t32 / args.steps},
         "mixed_vs_fp32_max_abs_dlogP": dlogp,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic,
                      "note": "FP32 FFMA pipe: 152 SMs x 128 lanes x 2 flop x 2070 MHz; achieved = counted "
-                             "flops of the executed sweep schedule / kernel time"},
+                             "flops of the executed sweep schedule / kernel time; traffic = DRAM bytes per "
+                             "launch (ncu capture of 8,192 syndromes scaled by the syndrome count; null "
+                             "when the kernel sources differ from the captured ones)"},
         "e2e": {"value": e2e_val, "unit": "syndromes/s", "h2d_bytes_per_step": int(h_noise.numel() * 4 +
                                                                                      h_syn.numel() * 8),
                 "d2h_bytes_per_step": int(h_lp.numel() * 8 + h_am.numel())},
