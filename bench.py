@@ -217,9 +217,22 @@ def run_mixed(args):
         b = items_by_prec[mld.MLD_MIXED_TF32][k][5].cpu().numpy()
         idx = rng.choice(per, 64 if d == 13 else 256, replace=False)
         ref, _ = oracle.decode(d, p[idx].astype(np.float32).astype(np.float64), syn[idx])
+        # this distance alone: one mld_decode per precision on the same batch
+        rate = {}
+        for prec in (mld.MLD_FP32, mld.MLD_MIXED_TF32):
+            it = items_by_prec[prec][k]
+            codes[d].decode(it[1], it[2], MIXED_CHI[d], prec)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            codes[d].decode(it[1], it[2], MIXED_CHI[d], prec)
+            e1.record()
+            torch.cuda.synchronize()
+            rate[prec] = per / (e0.elapsed_time(e1) / 1e3)
         per_d[str(d)] = {"chi": MIXED_CHI[d], "max_abs_dlogP_mixed_vs_fp32": float(np.abs(a - b).max()),
                          "max_abs_dlogP_mixed_vs_oracle_sample": float(np.abs(b[idx] - ref).max()),
-                         "oracle_sample": len(idx)}
+                         "oracle_sample": len(idx), "fp32_syndromes_per_s_alone": rate[mld.MLD_FP32],
+                         "mixed_syndromes_per_s_alone": rate[mld.MLD_MIXED_TF32]}
     ms32, msm = res[mld.MLD_FP32][0], res[mld.MLD_MIXED_TF32][0]
     line = {"metric": "syndromes/s, mixed d=3..13 batch in one graph launch", "workload": "mixed",
             "value": per * len(ds) / (msm / 1e3), "unit": "syndromes/s", "fp32_value": per * len(ds) / (ms32 / 1e3),
@@ -227,6 +240,64 @@ def run_mixed(args):
             "per_d": per_d, "data": "synthetic",
             "config": {"d": ds, "chi_by_d": MIXED_CHI, "p": "U[0.02, 0.18] per syndrome, depolarizing"}}
     print(json.dumps(line), flush=True)
+
+
+# Truncating points (chi below the exact bond 2^floor(d/2)): (d, chi, syndromes per point).
+# The large-d points decode one wave of resident warps each (the kernel keeps one
+# (syndrome, class) per warp in a global-memory workspace), a bounded sample of the
+# 16,384-syndrome workload.
+LARGE_POINTS = [(9, 8, 65536), (11, 16, 16384), (17, 32, 608), (17, 64, 608), (25, 32, 608)]
+LARGE_POINTS_ALL = LARGE_POINTS + [(17, 128, 476), (25, 64, 524), (25, 128, 154)]
+
+
+def run_large(args):
+    """Truncated chi: d=9 chi=8 and d=11 chi=16 (the truncating points of the d/p grid), and
+    d=17, 25 at chi 32..128 under depolarizing p=0.12 and biased noise (eta=100, p=0.12).
+    Reports syndromes/s per point and, where the exact oracle runs (d <= 17), the error of the
+    leading coset's ln Z and of the posterior Pr(l|s) on a sample."""
+    import torch
+    import paper_2605_17230_gb300 as mld
+    import oracle
+    pts = LARGE_POINTS_ALL if args.large_all else LARGE_POINTS
+    out = []
+    for d, chi, B in pts:
+        code = mld.Code(d)
+        n = d * d
+        for name, noise in (("depolarizing p=0.12", synth.depolarizing(n, 0.12)),
+                            ("biased eta=100 p=0.12", synth.biased(n, 0.12, 100.0))):
+            noise = noise.astype(np.float32)
+            E = synth.sample_errors(d, noise, B, seed=synth.config_seed(5, d, 0.12))
+            syn = synth.syndromes_of(d, E)
+            nz = torch.tensor(noise, device="cuda")
+            sy = torch.tensor(syn.view(np.int64), device="cuda")
+            code.decode(nz, sy, chi, mld.MLD_FP32)          # warm-up: plan upload, workspace
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            lp, am = code.decode(nz, sy, chi, mld.MLD_FP32)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            if code.status() != 0:
+                raise RuntimeError("device status: " + mld.mld_status_string(code.status()))
+            lp, am = lp.cpu().numpy(), am.cpu().numpy()
+            rec = {"d": d, "chi": chi, "noise": name, "syndromes": B, "ms": ms,
+                   "syndromes_per_s": B / (ms / 1e3),
+                   "argmax_equals_true_class": float(np.mean(am == synth.true_class(d, E)))}
+            if d <= 17:
+                k = 16 if d == 17 else 64
+                ref, _ = oracle.decode(d, noise.astype(np.float64), syn[:k])
+                lead = np.argmax(ref, axis=1)
+                post = lambda x: np.exp(x - np.logaddexp.reduce(x, axis=1, keepdims=True))
+                rec.update({"oracle_sample": k,
+                            "max_abs_dlogP_leading_coset": float(np.abs(lp[np.arange(k), lead] -
+                                                                       ref[np.arange(k), lead]).max()),
+                            "max_abs_dposterior": float(np.abs(post(lp[:k]) - post(ref)).max()),
+                            "argmax_equals_oracle": float(np.mean(am[:k] == lead))})
+            out.append(rec)
+            print(json.dumps(rec), flush=True)
+    print(json.dumps({"metric": "syndromes/s at truncating chi", "workload": "large", "points": out,
+                      "data": "synthetic", "dtype": "f32"}), flush=True)
 
 
 def run_grad(args):
@@ -281,9 +352,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=B, help="syndromes per GPU per step (default: the "
                     "65536 of the workload; smaller values only for profiling captures)")
-    ap.add_argument("--workload", default="metric", choices=["metric", "mixed", "grad"],
+    ap.add_argument("--workload", default="metric", choices=["metric", "mixed", "grad", "large"],
                     help="metric: the headline d=9 line (default); mixed: the 1,048,576-syndrome mixed-d "
-                         "graph batch; grad: the adjoint on the d=7 workload")
+                         "graph batch; grad: the adjoint on the d=7 workload; large: truncating chi "
+                         "(d=9 chi=8, d=11 chi=16, and samples of d=17, 25 at chi 32..128)")
+    ap.add_argument("--large-all", action="store_true", help="with --workload large: also the slow "
+                    "points (d=17 chi=128, d=25 chi=64 and 128)")
     ap.add_argument("--mixed-total", type=int, default=1 << 20)
     args = ap.parse_args()
     rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)
@@ -294,6 +368,8 @@ def main():
         return run_mixed(args) if rank == 0 else None
     if args.workload == "grad":
         return run_grad(args) if rank == 0 else None
+    if args.workload == "large":
+        return run_large(args) if rank == 0 else None
 
     import torch
     import paper_2605_17230_gb300 as mld
