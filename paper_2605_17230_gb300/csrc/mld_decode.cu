@@ -31,6 +31,7 @@ namespace mld {
 constexpr int kMaxWarpsPerBlock = 8;
 constexpr int kMaxJacobiSweeps = 40;
 constexpr float kJacobiTol = 1.0e-5f;   // above the ~L*eps noise floor of FP32 dot products
+constexpr float kJacobiNoise = 1.0e-8f; // rotations that move less than this (relative to the block) are skipped
 
 struct DecodeArgs {
     const SiteStep* steps;
@@ -64,6 +65,11 @@ __device__ __forceinline__ float group_sum(float v, int G) {
 
 __device__ __forceinline__ float pow2f(int e) {   // exact 2^e for -126 <= e <= 127
     return __int_as_float((e + 127) << 23);
+}
+
+__device__ __forceinline__ float group_max(float v, int G) {
+    for (int o = G >> 1; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
 }
 
 // weight of qubit factor at this step: w(a, a', b, b') = p_q[E_q xor X^u Z^v]
@@ -196,20 +202,32 @@ __device__ int renormalise(float* M, int len, int lane, bool* zero, bool* bad) {
 // a group of G lanes (g = lane index in the group). LAPACK sign convention.
 __device__ void qr_block(float* M, float* tau, int K, int n, int g, int G) {
     for (int j = 0; j < n; ++j) {
-        float ss = 0.f;
-        for (int r = j + 1 + g; r < K; r += G) { const float x = M[r * n + j]; ss = fmaf(x, x, ss); }
-        ss = group_sum(ss, G);
+        // the reflector from the column scaled by a power of two near its
+        // maximum: a column far below the block's largest entries (common under
+        // strongly biased noise) would otherwise lose its squares to underflow,
+        // and the reciprocal of a tiny norm would overflow
+        float mx = 0.f;
+        for (int r = j + 1 + g; r < K; r += G) mx = fmaxf(mx, fabsf(M[r * n + j]));
+        mx = group_max(mx, G);
         const float x0 = M[j * n + j];
+        int ex = 0;
+        frexpf(fmaxf(mx, fabsf(x0)), &ex);
+        ex = ex < -125 ? -125 : (ex > 126 ? 126 : ex);
+        const float sc = pow2f(-ex), isc = pow2f(ex);
+        float ss = 0.f;
+        for (int r = j + 1 + g; r < K; r += G) { const float x = M[r * n + j] * sc; ss = fmaf(x, x, ss); }
+        ss = group_sum(ss, G);
         float tj = 0.f, beta = x0, scal = 0.f;
-        if (ss > 0.f) {
-            const float nrm = sqrtf(fmaf(x0, x0, ss));
-            beta = -copysignf(nrm, x0);
-            tj = (beta - x0) / beta;
-            scal = 1.f / (x0 - beta);
+        if (mx > 0.f) {
+            const float x0s = x0 * sc;
+            const float betas = -copysignf(sqrtf(fmaf(x0s, x0s, ss)), x0s);
+            tj = (betas - x0s) / betas;
+            scal = 1.f / (x0s - betas);                // v_r = x_r / (x0 - beta) = (x_r sc) * scal
+            beta = betas * isc;
         }
         __syncwarp();
         if (tj != 0.f)
-            for (int r = j + 1 + g; r < K; r += G) M[r * n + j] *= scal;
+            for (int r = j + 1 + g; r < K; r += G) M[r * n + j] = (M[r * n + j] * sc) * scal;
         if (g == 0) { M[j * n + j] = beta; tau[j] = tj; }
         __syncwarp();
         if (tj != 0.f) {
@@ -248,9 +266,13 @@ __device__ void apply_q(const float* Mq, const float* tau, int K, int n, float* 
 // One-sided Jacobi on the nv columns (length L, ld = ldx) of X, accumulating
 // the rotations into acc (nv x nv, starts at I). Rotation parameters in
 // FP64 from FP32 dot products; cyclic round-robin order; bounded sweeps.
-// A pair is rotated only if both columns lie above the FP32 noise floor of
-// the block (squared norm > 1e-12 of the squared Frobenius norm): below it
-// a column is rounding noise and rotating such columns does not settle.
+// A pair (p, q) is rotated when its columns are not orthogonal to kJacobiTol
+// and the rotation moves a component that matters: the mass that would stay
+// in the smaller column along the larger one, gamma / sqrt(max(alpha, beta)),
+// exceeds kJacobiNoise of the block's Frobenius norm. Below that the pair is
+// FP32 rounding noise, which rotations only regenerate (they would not
+// settle); a fixed floor on the column norms instead left small but real
+// overlaps unrotated, and their truncation cost up to 1e-4 in ln Z.
 // Returns false if the sweep bound was hit.
 __device__ bool jacobi(float* X, int L, int ldx, int nv, float* acc, int lane) {
     float fro2 = 0.f;
@@ -258,7 +280,7 @@ __device__ bool jacobi(float* X, int L, int ldx, int nv, float* acc, int lane) {
         const float x = X[(e / nv) * ldx + (e % nv)];
         fro2 = fmaf(x, x, fro2);
     }
-    const float floor2 = 1e-12f * warp_sum(fro2);
+    const float fro = sqrtf(warp_sum(fro2));
     for (int e = lane; e < nv * nv; e += 32) acc[e] = (e / nv == e % nv) ? 1.f : 0.f;
     __syncwarp();
     const int nvp = nv + (nv & 1);
@@ -285,8 +307,8 @@ __device__ bool jacobi(float* X, int L, int ldx, int nv, float* acc, int lane) {
                         al = fmaf(xp, xp, al); be = fmaf(xq, xq, be); ga = fmaf(xp, xq, ga);
                     }
                 al = group_sum(al, G); be = group_sum(be, G); ga = group_sum(ga, G);
-                if (p >= 0 && ga != 0.f && fminf(al, be) > floor2 &&
-                    fabsf(ga) > kJacobiTol * sqrtf(al) * sqrtf(be)) {
+                if (p >= 0 && ga != 0.f && fabsf(ga) > kJacobiTol * sqrtf(al) * sqrtf(be) &&
+                    fabsf(ga) > kJacobiNoise * sqrtf(fmaxf(al, be)) * fro) {
                     const double zeta = ((double)be - (double)al) / (2.0 * (double)ga);
                     const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
                     const double cd = 1.0 / sqrt(1.0 + t * t);

@@ -124,6 +124,59 @@ def test_truncated_chi_vs_fp64_mps(mld, d, chi):
     np.testing.assert_allclose(post(lp), post(ref), rtol=0, atol=1e-4)
 
 
+@pytest.mark.parametrize("d,chi,B", [(11, 16, 8), (13, 32, 2)])
+def test_truncated_strongly_biased_vs_fp64_mps(mld, d, chi, B):
+    """Strongly biased noise (eta = 100, p = 0.12): the blocks of a truncating
+    column then hold columns many orders of magnitude below their largest
+    entries, and a Householder reflector that squares unscaled entries loses
+    them to underflow (this case was off by 2e-3 in ln Z before the scaled
+    norms). Same bar as the depolarizing case."""
+    n = d * d
+    noise = synth.biased(n, 0.12, 100.0).astype(np.float32)
+    E = synth.sample_errors(d, noise, B, seed=synth.config_seed(5, d, 0.12))
+    syn = synth.syndromes_of(d, E)
+    ref = omps.decode_mps(d, noise.astype(np.float64), syn, chi)
+    lp, _ = gpu_decode(mld, d, noise, syn, chi)
+    best = np.argmax(ref, axis=1)
+    np.testing.assert_allclose(lp[np.arange(B), best], ref[np.arange(B), best], rtol=0, atol=1e-4)
+    post = lambda x: np.exp(x - x.max(axis=1, keepdims=True)) / np.exp(x - x.max(axis=1, keepdims=True)).sum(1, keepdims=True)
+    np.testing.assert_allclose(post(lp), post(ref), rtol=0, atol=1e-4)
+
+
+def test_truncated_depolarizing_d11_vs_fp64_mps(mld):
+    """Depolarizing p = 0.12 at d=11, chi=16 on 16 syndromes: small but real
+    overlaps between a large and a small column must be rotated before the
+    truncation (a fixed norm floor in the Jacobi sweep left them and cost
+    1.4e-4 in ln Z of the leading coset)."""
+    d, chi, B = 11, 16, 16
+    n = d * d
+    noise = synth.depolarizing(n, 0.12).astype(np.float32)
+    E = synth.sample_errors(d, noise, B, seed=synth.config_seed(5, d, 0.12))
+    syn = synth.syndromes_of(d, E)
+    ref = omps.decode_mps(d, noise.astype(np.float64), syn, chi)
+    lp, _ = gpu_decode(mld, d, noise, syn, chi)
+    best = np.argmax(ref, axis=1)
+    np.testing.assert_allclose(lp[np.arange(B), best], ref[np.arange(B), best], rtol=0, atol=1e-4)
+
+
+@pytest.mark.parametrize("d,chi", [(9, 32), (13, 64)])
+@pytest.mark.parametrize("prec", [0, 2])
+def test_exact_strongly_biased(mld, d, chi, prec):
+    """Untruncated sweep under eta = 100: entries of a block span many orders
+    of magnitude, and the non-negative gauge keeps every coset to FP32
+    relative accuracy."""
+    n = d * d
+    noise = synth.biased(n, 0.12, 100.0).astype(np.float32)
+    E = synth.sample_errors(d, noise, 32, seed=synth.config_seed(9, d, 0.12))
+    syn = synth.syndromes_of(d, E)
+    ref, _ = oracle.decode(d, noise, syn)
+    lp, am = gpu_decode(mld, d, noise, syn, chi, precision=prec)
+    fin = np.isfinite(ref)
+    assert np.array_equal(np.isfinite(lp), fin)
+    np.testing.assert_allclose(lp[fin], ref[fin], rtol=0, atol=TOL)
+    check_argmax(am, ref)
+
+
 def test_per_syndrome_depolarizing(mld):
     d = 7
     B = 257
