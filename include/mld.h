@@ -215,7 +215,9 @@ mld_status mld_decode_status(const mld_code* code);
 /* Counted floating-point operations per syndrome (all four classes) of the
  * sweep schedule that mld_decode runs for this code, chi and precision: the
  * MPO.MPS products, the QR and Q applications of truncating columns and the
- * bond-matrix products, from the same shape plan the kernel executes. Jacobi
+ * bond-matrix products, from the same shape plan the kernel executes (at
+ * untruncated chi, columns 0..d-2 are swept once per l_Z and shared by
+ * l_X = 0, 1, whose representatives differ only in the last column). Jacobi
  * SVD work, which depends on the data, is not included. Host only. */
 mld_status mld_decode_flops(const mld_code* code, int chi, int precision, double* flops_per_syndrome);
 

@@ -962,7 +962,14 @@ mld_status mld_decode_flops(const mld_code* C, int chi, int precision, double* o
     if (!C || chi < 1 || !out) return MLD_ERR_INVALID_ARG;
     if (precision != MLD_FP32 && precision != MLD_MIXED_BF16 && precision != MLD_MIXED_TF32)
         return MLD_ERR_INVALID_ARG;
-    *out = 4.0 * mld::make_plan(C->d, chi).flops_per_coset;
+    const mld::Plan P = mld::make_plan(C->d, chi);
+    if (P.svd_sites == 0 && mld::exact_floats_per_warp(C->d) > 0) {
+        // the untruncated kernel sweeps columns 0..d-2 once per l_Z and the
+        // last column once per class
+        *out = 2.0 * (P.flops_per_coset - P.flops_last_col) + 4.0 * P.flops_last_col;
+    } else {
+        *out = 4.0 * P.flops_per_coset;
+    }
     return MLD_OK;
 }
 

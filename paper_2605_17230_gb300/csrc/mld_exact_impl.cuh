@@ -759,6 +759,8 @@ __device__ __forceinline__ void init_all(Ctx<D, PREC>& x, std::integer_sequence<
 template <int D, int PREC>
 __device__ __forceinline__ void decode_unit(const ExactArgs& a, float* ws, int64_t unit, int lane);
 
+// A unit is (syndrome, l_Z): one warp sweeps the columns shared by the two
+// classes l_X = 0, 1 once and the last column once per l_X (decode_unit).
 // Shared-memory mode: one unit per warp. Global-workspace mode (a.gws set,
 // for states larger than a block's shared memory): a fixed set of resident
 // warps, each with its own slice of the workspace, strides over the units.
@@ -771,12 +773,12 @@ __global__ void __launch_bounds__(256) decode_exact_kernel(ExactArgs a) {
     if constexpr (GLOBAL) {
         const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
         float* ws = a.gws + (size_t)gw * FPW;
-        for (int64_t unit = gw; unit < 4 * a.B; unit += nw) {
+        for (int64_t unit = gw; unit < 2 * a.B; unit += nw) {
             decode_unit<D, PREC>(a, ws, unit, lane);
             __syncwarp();
         }
     } else {
-        if (gw >= 4 * a.B) return;
+        if (gw >= 2 * a.B) return;
         decode_unit<D, PREC>(a, reinterpret_cast<float*>(smem4) + (size_t)warp * FPW, gw, lane);
     }
 }
@@ -786,8 +788,8 @@ __device__ __forceinline__ void decode_unit(const ExactArgs& a, float* ws, int64
     constexpr int OFF_W = LayoutOf<D>::lay.off_w, OFF_MPS = LayoutOf<D>::lay.off_mps;
     constexpr int OFF_ARENA = LayoutOf<D>::lay.off_arena;
     constexpr int n = D * D;
-    const int64_t b = unit >> 2;
-    const int cls = (int)(unit & 3);
+    const int64_t b = unit >> 1;
+    const int lz = (int)(unit & 1);
     Ctx<D, PREC> x;
     x.wts = ws + OFF_W;
     x.mps = ws + OFF_MPS;
@@ -799,7 +801,11 @@ __device__ __forceinline__ void decode_unit(const ExactArgs& a, float* ws, int64
     x.bad = false;
 
     // pure error f(s) = prod_{s_k=1} T_k, representative E_{l,s} =
-    // f X_L^{l_X} Z_L^{l_Z}, and the four weights of every qubit factor
+    // f X_L^{l_X} Z_L^{l_Z}, and the four weights of every qubit factor.
+    // Z_L is Z on row 0. X_L is taken as X on column d-1 rather than column
+    // 0: the two differ by X-type stabilisers, so each coset (and Z_l) is
+    // the same, and the classes l_X = 0, 1 then differ only in the last
+    // column, which is swept once for each from the state after column d-2.
     constexpr int W = (n - 1 + 63) / 64;
     uint64_t sw[W];
 #pragma unroll
@@ -813,8 +819,8 @@ __device__ __forceinline__ void decode_unit(const ExactArgs& a, float* ws, int64
             zb ^= __popcll(sw[u] & mk[W + u]) & 1;
         }
         const int r = q / D, c = q % D;
-        if ((cls & 1) && c == 0) xb ^= 1;
-        if ((cls & 2) && r == 0) zb ^= 1;
+        (void)c;
+        if (lz && r == 0) zb ^= 1;
         float row[4];
         if (a.noise_mode == MLD_NOISE_TABLE) {
             const float4 v = *reinterpret_cast<const float4*>(a.noise + 4 * (size_t)q);
@@ -832,19 +838,41 @@ __device__ __forceinline__ void decode_unit(const ExactArgs& a, float* ws, int64
     }
     init_all<D, PREC>(x, std::make_integer_sequence<int, D + 1>{});
     __syncwarp();
-    all_columns<D, PREC>(x, std::make_integer_sequence<int, D>{});
-    double logz = -INFINITY;
-    if (!x.zero && !x.bad) {
-        if (lane == 0) x.arena[0] = 1.f;
+    all_columns<D, PREC>(x, std::make_integer_sequence<int, D - 1>{});
+    // the last column once per l_X, each from the state after column d-2
+    // (the last column writes its sites after the old ones, so they survive)
+    const int e2 = x.e2, pe = x.pe;
+    const bool zero = x.zero, bad = x.bad;
+#pragma unroll 1
+    for (int lx = 0; lx < 2; ++lx) {
+        x.e2 = e2;
+        x.pe = pe;
+        x.zero = zero;
+        x.bad = bad;
+        if (lx == 1) {
+            // X on column d-1: w[u + 2v] = p[E xor X^u Z^v] becomes w[(u ^ 1) + 2v]
+            if (lane < D) {
+                float4* w = reinterpret_cast<float4*>(x.wts + 4 * (lane * D + D - 1));
+                const float4 v = *w;
+                *w = make_float4(v.y, v.x, v.w, v.z);
+            }
+            __syncwarp();
+        }
+        column<D, PREC, D - 1>(x, std::make_integer_sequence<int, D + 1>{});
+        double logz = -INFINITY;
+        if (!x.zero && !x.bad) {
+            if (lane == 0) x.arena[0] = 1.f;
+            __syncwarp();
+            final_all<D, PREC>(x, std::make_integer_sequence<int, D + 1>{});
+            const float z = x.arena[((D + 1) & 1) ? 64 : 0];
+            if (!(z == z)) x.bad = true;
+            else if (z > 0.f) logz = log((double)z) + (double)x.e2 * 0.69314718055994530942;
+        }
+        if (lane == 0) {
+            a.logP[b * 4 + lx + 2 * lz] = logz;
+            if (x.bad) atomicOr(a.status, 1 << MLD_ERR_NUMERIC);
+        }
         __syncwarp();
-        final_all<D, PREC>(x, std::make_integer_sequence<int, D + 1>{});
-        const float z = x.arena[((D + 1) & 1) ? 64 : 0];
-        if (!(z == z)) x.bad = true;
-        else if (z > 0.f) logz = log((double)z) + (double)x.e2 * 0.69314718055994530942;
-    }
-    if (lane == 0) {
-        a.logP[b * 4 + cls] = logz;
-        if (x.bad) atomicOr(a.status, 1 << MLD_ERR_NUMERIC);
     }
 }
 
@@ -861,7 +889,7 @@ bool launch_dp(const ExactArgs& a, cudaStream_t s, int warps_per_block) {
     if (cudaFuncSetAttribute(decode_exact_kernel<D, PREC, GLOBAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return false;
-    const int64_t units = 4 * a.B;
+    const int64_t units = 2 * a.B;                      // (syndrome, l_Z)
     int64_t blocks = (units + warps_per_block - 1) / warps_per_block;
     if (GLOBAL && blocks > a.gws_warps / warps_per_block) blocks = a.gws_warps / warps_per_block;
     decode_exact_kernel<D, PREC, GLOBAL><<<(unsigned)blocks, 32 * warps_per_block, smem, s>>>(a);

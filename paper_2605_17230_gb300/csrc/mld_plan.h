@@ -84,6 +84,7 @@ struct Plan {
     int max_buf = 0, max_mps = 0, max_q = 0, max_svd = 0;
     int svd_sites = 0;                // number of sites that truncate
     double flops_per_coset = 0.0;     // counted flops of this schedule
+    double flops_last_col = 0.0;      // of which the last column (d-1)
     int init_sizes[kMaxD + 1] = {};   // initial product-state site sizes
 };
 
@@ -130,7 +131,9 @@ constexpr Plan make_plan(int d, int chi) {
         int o = 0;
         for (int i = 0; i <= d; ++i) { offA[i] = o; o += align4(P.init_sizes[i]); }
     }
+    double flops_prefix = 0.0;
     for (int c = 0; c < d; ++c) {
+        if (c == d - 1) flops_prefix = flops;
         SiteStep* S = &P.steps[c * (d + 1)];
         int pa[kMaxD + 1] = {}, pb[kMaxD + 1] = {};
         for (int i = 0; i <= d; ++i) {
@@ -257,10 +260,14 @@ constexpr Plan make_plan(int d, int chi) {
             flops += 2.0 * st.pb * st.K * ncolA * (st.cid ? 1 : st.pam);
         }
         // new MPS layout: only data sites are stored (overwrites the old
-        // layout once the left sweep is done)
-        int o = 0, old_tot = 0;
+        // layout once the left sweep is done). The last column's sites go
+        // after the old ones, so that its old sites survive the column and
+        // the column can be swept again from them (a kernel may sweep it once
+        // per representative of X_L, which differ only in that column).
+        int old_tot = 0;
         for (int i = 0; i <= d; ++i)
             if (S[i].okind == K_DATA) old_tot += align4(S[i].Dl * S[i].pa * S[i].Dr);
+        int o = c == d - 1 ? old_tot : 0;
         for (int i = 0; i <= d; ++i) {
             S[i].offN = o;
             if (S[i].nkind == K_DATA) o += align4(S[i].Sl * S[i].pb * S[i].S);
@@ -295,6 +302,7 @@ constexpr Plan make_plan(int d, int chi) {
     P.off_svd = P.off_q + align4(max_q);
     P.floats_per_warp = P.off_svd + align4(max_svd);
     P.flops_per_coset = flops;
+    P.flops_last_col = flops - flops_prefix;
     return P;
 }
 
