@@ -107,7 +107,12 @@ mld_status mld_code_layout(const mld_code* code, int32_t* stab_type, int32_t* st
  *   syndromes  device pointer, uint64[B][syn_words].
  *   chi        maximum bond dimension kept after each column (chi >= 1).
  *              chi >= 2^floor(d/2) discards nothing: the result is then the
- *              exact ln Z_l(s) up to rounding.
+ *              exact ln Z_l(s) up to rounding. Below that it is the
+ *              boundary-MPS approximation for the representative
+ *              f(s) * X^{l_X} * Z_L^{l_Z} with X^{l_X} the X string on column
+ *              d-1 (an X_L of the same cosets; the two classes l_X = 0, 1
+ *              then share every column but the last, which the kernels sweep
+ *              once and reuse).
  *   precision  an mld_precision value.
  *   logP       device pointer, double[B][4]: ln Z_l(s) for l = I, X, Z, Y
  *              (the joint log-probability ln Pr(s, l); ln Pr(l|s) is
@@ -215,9 +220,9 @@ mld_status mld_decode_status(const mld_code* code);
 /* Counted floating-point operations per syndrome (all four classes) of the
  * sweep schedule that mld_decode runs for this code, chi and precision: the
  * MPO.MPS products, the QR and Q applications of truncating columns and the
- * bond-matrix products, from the same shape plan the kernel executes (at
- * untruncated chi, columns 0..d-2 are swept once per l_Z and shared by
- * l_X = 0, 1, whose representatives differ only in the last column). Jacobi
+ * bond-matrix products, from the same shape plan the kernel executes
+ * (columns 0..d-2 are swept once per l_Z and shared by l_X = 0, 1, whose
+ * representatives differ only in the last column). Jacobi
  * SVD work, which depends on the data, is not included. Host only. */
 mld_status mld_decode_flops(const mld_code* code, int chi, int precision, double* flops_per_syndrome);
 

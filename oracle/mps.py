@@ -149,11 +149,25 @@ def coset_logz_mps(d, noise, E, chi):
     return math.log(z) + log2 * math.log(2.0) if z > 0 else -math.inf
 
 
-def decode_mps(d, noise, syn, chi):
-    """ln Z_l(s) for l = I, X, Z, Y ([B][4]) by the boundary-MPS sweep."""
+def decode_mps(d, noise, syn, chi, xl_column=0):
+    """ln Z_l(s) for l = I, X, Z, Y ([B][4]) by the boundary-MPS sweep.
+
+    The coset of E_{l,s} = f(s) X_L^{l_X} Z_L^{l_Z} does not depend on which X
+    string is taken as X_L (X on any column: they differ by X-type
+    stabilisers), but at truncated chi the sweep's approximation does (Sec.
+    3.2.1 contracts one fixed representative). xl_column picks the column of
+    the X string used for l_X = 1 (the GPU kernels take column d-1)."""
     n, _, _ = code_info(d)
     noise = np.asarray(noise, dtype=np.float64)
-    reps = representatives(d, syn)
+    reps = representatives(d, syn).copy()
+    if xl_column != 0:
+        # move the X string of the l_X = 1 classes from column 0 to xl_column
+        # (Pauli code x + 2z: X flips bit 0)
+        move = np.zeros(n, np.uint8)
+        move[0::d] ^= 1
+        move[xl_column::d] ^= 1
+        reps[:, 1] ^= move
+        reps[:, 3] ^= move
     B = reps.shape[0]
     out = np.zeros((B, 4))
     for b in range(B):

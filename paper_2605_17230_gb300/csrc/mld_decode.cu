@@ -342,11 +342,20 @@ __device__ bool jacobi(float* X, int L, int ldx, int nv, float* acc, int lane) {
 // each column c < d-1 the boundary MPS is expanded to the dense vector over
 // corner column c+1 (index bit i = plaquette row i, 2^(d+1) floats) and
 // stored at ckpt + c*2^(d+1), with xbuf (2*2^(d+1) floats) as scratch.
+//
+// pair (optional): the unit is (syndrome, l_Z) = unit >> 1, unit & 1 and both
+// classes l_X = 0, 1 are decoded, ln Z into pair[0] and pair[1]. X_L is then
+// taken as X on column d-1 (it differs from X on column 0 by X-type
+// stabilisers, so each coset is the same); the two representatives agree on
+// columns 0..d-2, which are swept once, and the last column is swept once
+// per class from the state they leave (the plan stores the last column's
+// sites after its old ones). At truncated chi the approximation depends on
+// the representative: this one is E_{l,s} with X_L on column d-1.
 __device__ __forceinline__ double decode_unit(const DecodeArgs& a, float* ws, int64_t unit, int lane,
                                               bool rotate = false, float* ckpt = nullptr,
-                                              float* xbuf = nullptr) {
-    const int64_t b = unit >> 2;
-    const int cls = (int)(unit & 3);
+                                              float* xbuf = nullptr, double* pair = nullptr) {
+    const int64_t b = pair ? unit >> 1 : unit >> 2;
+    const int cls = pair ? (int)(unit & 1) << 1 : (int)(unit & 3);
     const int d = a.d, n = a.n;
     float* wts = ws + a.off_w;
     float* mps = ws + a.off_mps;
@@ -384,6 +393,7 @@ __device__ __forceinline__ double decode_unit(const DecodeArgs& a, float* ws, in
             wts[4 * qf + uv] = row[pidx];
         }
     }
+    (void)cls;
     // initial boundary MPS: all-ones product state over corner column 0
     {
         int o = 0;
@@ -397,7 +407,7 @@ __device__ __forceinline__ double decode_unit(const DecodeArgs& a, float* ws, in
 
     int e2 = 0;
     bool zero = false, bad = false, timeout = false;
-    for (int c = 0; c < d && !zero && !bad; ++c) {
+    auto sweep_column = [&](int c) {
         const SiteStep* S = a.steps + (size_t)c * (d + 1);
         float* cin = bufA;
         float* cout = bufB;
@@ -429,7 +439,7 @@ __device__ __forceinline__ double decode_unit(const DecodeArgs& a, float* ws, in
             }
             float* t = cin; cin = cout; cout = t;
         }
-        if (zero || bad) break;
+        if (zero || bad) return;
         // ---- right sweep; carry g (rows x S), T into t. A tall last block
         // kept as the site leaves an identity carry (st.gid).
         float* g = cin;
@@ -552,7 +562,12 @@ __device__ __forceinline__ double decode_unit(const DecodeArgs& a, float* ws, in
             }
             __syncwarp();
         }
-        if (ckpt && c < d - 1) {
+    };
+    const int cend = pair ? d - 1 : d;
+    for (int c = 0; c < cend && !zero && !bad; ++c) {
+        sweep_column(c);
+        if (ckpt && c < d - 1 && !zero && !bad) {
+            const SiteStep* S = a.steps + (size_t)c * (d + 1);
             // dense vector over corner column c+1 from the new MPS
             const int full = 1 << (d + 1);
             float* v = xbuf;
@@ -583,6 +598,7 @@ __device__ __forceinline__ double decode_unit(const DecodeArgs& a, float* ws, in
             __syncwarp();
         }
     }
+    auto contract = [&]() -> double {
     double logz;
     if (zero) {
         logz = -INFINITY;
@@ -615,6 +631,33 @@ __device__ __forceinline__ double decode_unit(const DecodeArgs& a, float* ws, in
         logz = z > 0.f ? log((double)z) + (double)e2 * 0.69314718055994530942 : -INFINITY;
         if (!(z == z)) bad = true;
     }
+    return logz;
+    };
+    double logz = 0.0;
+    if (!pair) {
+        logz = contract();
+    } else {
+        // the last column once per l_X from the state after column d-2
+        const int e2p = e2;
+        const bool zerop = zero, badp = bad;
+        for (int lx = 0; lx < 2; ++lx) {
+            e2 = e2p;
+            zero = zerop;
+            bad = bad || badp;
+            if (lx == 1) {
+                // X on column d-1: w[u + 2v] = p[E xor X^u Z^v] becomes w[(u ^ 1) + 2v]
+                if (lane < d) {
+                    float* w = wts + 4 * (lane * d + d - 1);
+                    const float w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3];
+                    w[0] = w1; w[1] = w0; w[2] = w3; w[3] = w2;
+                }
+                __syncwarp();
+            }
+            if (!zero && !bad) sweep_column(d - 1);
+            pair[lx] = contract();
+            __syncwarp();
+        }
+    }
     if (lane == 0) {
         if (bad) atomicOr(a.status, 1 << MLD_ERR_NUMERIC);
         if (timeout) atomicOr(a.status, 1 << MLD_ERR_TIMEOUT);
@@ -631,18 +674,27 @@ decode_fp32_kernel(DecodeArgs a) {
     extern __shared__ float4 smem4[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    // unit = (syndrome, l_Z); both l_X from one sweep of columns 0..d-2
+    double lz[2];
     if constexpr (GLOBAL) {
         const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
         float* ws = a.gws + (size_t)gw * a.per_warp;
-        for (int64_t unit = gw; unit < 4 * a.B; unit += nw) {
-            const double lz = decode_unit(a, ws, unit, lane);
-            if (lane == 0) a.logP[unit] = lz;
+        for (int64_t unit = gw; unit < 2 * a.B; unit += nw) {
+            decode_unit(a, ws, unit, lane, false, nullptr, nullptr, lz);
+            if (lane == 0) {
+                a.logP[(unit >> 1) * 4 + 2 * (unit & 1)] = lz[0];
+                a.logP[(unit >> 1) * 4 + 2 * (unit & 1) + 1] = lz[1];
+            }
             __syncwarp();
         }
     } else {
-        if (gw >= 4 * a.B) return;
-        const double lz = decode_unit(a, reinterpret_cast<float*>(smem4) + (size_t)warp * a.per_warp, gw, lane);
-        if (lane == 0) a.logP[gw] = lz;
+        if (gw >= 2 * a.B) return;
+        decode_unit(a, reinterpret_cast<float*>(smem4) + (size_t)warp * a.per_warp, gw, lane, false, nullptr, nullptr,
+                    lz);
+        if (lane == 0) {
+            a.logP[(gw >> 1) * 4 + 2 * (gw & 1)] = lz[0];
+            a.logP[(gw >> 1) * 4 + 2 * (gw & 1) + 1] = lz[1];
+        }
     }
 }
 
@@ -962,14 +1014,10 @@ mld_status mld_decode_flops(const mld_code* C, int chi, int precision, double* o
     if (!C || chi < 1 || !out) return MLD_ERR_INVALID_ARG;
     if (precision != MLD_FP32 && precision != MLD_MIXED_BF16 && precision != MLD_MIXED_TF32)
         return MLD_ERR_INVALID_ARG;
+    // both kernels sweep columns 0..d-2 once per l_Z and the last column once
+    // per class
     const mld::Plan P = mld::make_plan(C->d, chi);
-    if (P.svd_sites == 0 && mld::exact_floats_per_warp(C->d) > 0) {
-        // the untruncated kernel sweeps columns 0..d-2 once per l_Z and the
-        // last column once per class
-        *out = 2.0 * (P.flops_per_coset - P.flops_last_col) + 4.0 * P.flops_last_col;
-    } else {
-        *out = 4.0 * P.flops_per_coset;
-    }
+    *out = 2.0 * (P.flops_per_coset - P.flops_last_col) + 4.0 * P.flops_last_col;
     return MLD_OK;
 }
 
@@ -1019,7 +1067,7 @@ mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, co
     // (TF32 tensor-core products); BF16 and truncating chi run FP32 only
     if (precision == MLD_MIXED_BF16 || (precision == MLD_MIXED_TF32 && !exact)) return MLD_ERR_UNSUPPORTED;
     const size_t pw = (size_t)(exact ? mld::exact_floats_per_warp(C->d) : P.floats_per_warp) * sizeof(float);
-    const int64_t units = 4 * B;
+    const int64_t units = 2 * B;                       // (syndrome, l_Z) pairs, both kernels
     int W = 1;
     float* gws = nullptr;
     int64_t gws_warps = 0;

@@ -116,7 +116,7 @@ def test_truncated_chi_vs_fp64_mps(mld, d, chi):
     noise = synth.depolarizing(n, 0.12).astype(np.float32)
     E = synth.sample_errors(d, noise, 6, seed=11)
     syn = synth.syndromes_of(d, E)
-    ref = omps.decode_mps(d, noise.astype(np.float64), syn, chi)
+    ref = omps.decode_mps(d, noise.astype(np.float64), syn, chi, xl_column=d - 1)
     lp, _ = gpu_decode(mld, d, noise, syn, chi)
     best = np.argmax(ref, axis=1)
     np.testing.assert_allclose(lp[np.arange(len(ref)), best], ref[np.arange(len(ref)), best], rtol=0, atol=1e-4)
@@ -135,7 +135,7 @@ def test_truncated_strongly_biased_vs_fp64_mps(mld, d, chi, B):
     noise = synth.biased(n, 0.12, 100.0).astype(np.float32)
     E = synth.sample_errors(d, noise, B, seed=synth.config_seed(5, d, 0.12))
     syn = synth.syndromes_of(d, E)
-    ref = omps.decode_mps(d, noise.astype(np.float64), syn, chi)
+    ref = omps.decode_mps(d, noise.astype(np.float64), syn, chi, xl_column=d - 1)
     lp, _ = gpu_decode(mld, d, noise, syn, chi)
     best = np.argmax(ref, axis=1)
     np.testing.assert_allclose(lp[np.arange(B), best], ref[np.arange(B), best], rtol=0, atol=1e-4)
@@ -153,7 +153,7 @@ def test_truncated_depolarizing_d11_vs_fp64_mps(mld):
     noise = synth.depolarizing(n, 0.12).astype(np.float32)
     E = synth.sample_errors(d, noise, B, seed=synth.config_seed(5, d, 0.12))
     syn = synth.syndromes_of(d, E)
-    ref = omps.decode_mps(d, noise.astype(np.float64), syn, chi)
+    ref = omps.decode_mps(d, noise.astype(np.float64), syn, chi, xl_column=d - 1)
     lp, _ = gpu_decode(mld, d, noise, syn, chi)
     best = np.argmax(ref, axis=1)
     np.testing.assert_allclose(lp[np.arange(B), best], ref[np.arange(B), best], rtol=0, atol=1e-4)
@@ -312,7 +312,7 @@ def test_d13_truncated_global_workspace_vs_fp64_mps(mld):
     noise = synth.depolarizing(n, 0.10).astype(np.float32)
     E = synth.sample_errors(d, noise, 2, seed=17)
     syn = synth.syndromes_of(d, E)
-    ref = omps.decode_mps(d, noise.astype(np.float64), syn, chi)
+    ref = omps.decode_mps(d, noise.astype(np.float64), syn, chi, xl_column=d - 1)
     lp, _ = gpu_decode(mld, d, noise, syn, chi)
     best = np.argmax(ref, axis=1)
     np.testing.assert_allclose(lp[np.arange(len(ref)), best], ref[np.arange(len(ref)), best], rtol=0, atol=1e-4)

@@ -280,6 +280,23 @@ def test_mps_mode_exact_at_full_bond(d, chi):
     np.testing.assert_allclose(omps.decode_mps(d, noise, syn, chi), ref, rtol=0, atol=1e-9)
 
 
+@pytest.mark.parametrize("col", [2, 4])
+def test_mps_mode_x_string_column(col):
+    """X on any column is an X_L (they differ by X-type stabilisers): at the
+    exact bond the sweep gives the same Z_l for the representative with the X
+    string on another column; below it the value depends on the
+    representative (the truncation of a different network)."""
+    d, n = 5, 25
+    noise = synth.biased(n, 0.12, 5.0)
+    syn = synth.syndromes_of(d, synth.sample_errors(d, noise, 3, seed=2))
+    ref, _ = oracle.decode(d, noise, syn)
+    np.testing.assert_allclose(omps.decode_mps(d, noise, syn, 4, xl_column=col), ref, rtol=0, atol=1e-9)
+    a = omps.decode_mps(d, noise, syn, 2, xl_column=0)
+    b = omps.decode_mps(d, noise, syn, 2, xl_column=col)
+    np.testing.assert_array_equal(a[:, [0, 2]], b[:, [0, 2]])   # l_X = 0: the same network
+    assert np.abs(a - b).max() > 0
+
+
 def test_mps_mode_truncation_converges():
     """Below the exact bond the error shrinks as chi grows (Sec. 3.2.1)."""
     d, n = 9, 81
