@@ -45,6 +45,8 @@ struct DecodeArgs {
     int d, n, words, noise_mode;
     int off_w, off_mps, off_buf0, off_buf1, off_q, off_svd, per_warp;
     int init_sizes[kMaxD + 1];
+    float* qgws = nullptr;     // split mode: the kept tall blocks of each resident warp in global memory
+    int64_t q_per_warp = 0;    // floats per warp of qgws
 };
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -356,13 +358,14 @@ __device__ bool jacobi(float* X, int L, int ldx, int nv, float* acc, int lane) {
 // the representative: this one is E_{l,s} with X_L on column d-1.
 __device__ __forceinline__ double decode_unit(const DecodeArgs& a, float* ws, int64_t unit, int lane,
                                               bool rotate = false, float* ckpt = nullptr,
-                                              float* xbuf = nullptr, double* pair = nullptr) {
+                                              float* xbuf = nullptr, double* pair = nullptr,
+                                              float* qext = nullptr) {
     const int64_t b = pair ? unit >> 1 : unit >> 2;
     const int cls = pair ? (int)(unit & 1) << 1 : (int)(unit & 3);
     const int d = a.d, n = a.n;
     float* wts = ws + a.off_w;
     float* mps = ws + a.off_mps;
-    float* qst = ws + a.off_q;
+    float* qst = qext ? qext : ws + a.off_q;
     float* svd = ws + a.off_svd;
     float* bufA = ws + a.off_buf0;
     float* bufB = ws + a.off_buf1;
@@ -671,6 +674,10 @@ __device__ __forceinline__ double decode_unit(const DecodeArgs& a, float* ws, in
 // Shared-memory mode: one unit per warp. Global-workspace mode (a.gws set,
 // for states larger than a block's shared memory): a fixed set of resident
 // warps, each with its own slice of the workspace, strides over the units.
+// Split mode (a.qgws set): the same persistent warps keep everything but the
+// kept tall blocks in shared memory, and those blocks (the largest part of
+// the state, touched only by the QR and the Q application) in their slice
+// of global memory, so that more units share an SM.
 template <bool GLOBAL>
 __global__ void __launch_bounds__(32 * kMaxWarpsPerBlock)
 decode_fp32_kernel(DecodeArgs a) {
@@ -679,6 +686,20 @@ decode_fp32_kernel(DecodeArgs a) {
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     // unit = (syndrome, l_Z); both l_X from one sweep of columns 0..d-2
     double lz[2];
+    if (!GLOBAL && a.qgws) {
+        const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+        float* ws = reinterpret_cast<float*>(smem4) + (size_t)warp * a.per_warp;
+        float* qx = a.qgws + (size_t)gw * a.q_per_warp;
+        for (int64_t unit = gw; unit < 2 * a.B; unit += nw) {
+            decode_unit(a, ws, unit, lane, false, nullptr, nullptr, lz, qx);
+            if (lane == 0) {
+                a.logP[(unit >> 1) * 4 + 2 * (unit & 1)] = lz[0];
+                a.logP[(unit >> 1) * 4 + 2 * (unit & 1) + 1] = lz[1];
+            }
+            __syncwarp();
+        }
+        return;
+    }
     if constexpr (GLOBAL) {
         const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
         float* ws = a.gws + (size_t)gw * a.per_warp;
@@ -1111,8 +1132,44 @@ mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, co
         for (const auto& kv : C->tuned)
             if (kv.first == key && kv.second >= 1 && pw * kv.second <= (size_t)max_optin) W = kv.second;
         if (C->force_warps > 0 && pw * C->force_warps <= (size_t)max_optin) W = C->force_warps;
+        // runtime-plan kernel: move the kept tall blocks to global memory when
+        // that at least doubles the warps per SM (shared memory sets it)
+        if (!exact && P.max_q > 0) {
+            const size_t ps = (size_t)(P.off_q + ((P.max_svd + 3) & ~3)) * sizeof(float);
+            int best_s = 0, Ws = 1;
+            for (int w = 1; w <= mld::kMaxWarpsPerBlock; ++w) {
+                if (ps * w > (size_t)max_optin) break;
+                int ctas = (int)((size_t)per_sm / (ps * w + 1024));
+                ctas = ctas < 32 ? ctas : 32;
+                const int warps = ctas * w < 16 ? ctas * w : 16;   // registers: 16 warps of 8-warp CTAs
+                if (warps > best_s) { best_s = warps; Ws = w; }
+            }
+            if (best_s >= 2 * best && C->force_warps == 0) {
+                int sms = 0;
+                if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                    return MLD_ERR_CUDA;
+                int64_t nw = (int64_t)sms * (best_s / Ws) * Ws;
+                const int64_t need = ((units + Ws - 1) / Ws) * Ws;
+                if (nw > need) nw = need;
+                const size_t qf = (size_t)((P.max_q + 3) & ~3);
+                const size_t bytes = (size_t)nw * qf * sizeof(float);
+                if (bytes > C->gws_bytes) {
+                    cudaFree(C->d_gws);
+                    C->d_gws = nullptr;
+                    C->gws_bytes = 0;
+                    if (cudaMalloc(&C->d_gws, bytes) != cudaSuccess) return MLD_ERR_NOMEM;
+                    C->gws_bytes = bytes;
+                }
+                a.qgws = C->d_gws;
+                a.q_per_warp = (int64_t)qf;
+                a.off_svd = P.off_q;                   // shared-memory layout without the q area
+                a.per_warp = P.off_q + ((P.max_svd + 3) & ~3);
+                W = Ws;
+                gws_warps = nw;
+            }
+        }
     }
-    const size_t smem = gws ? 0 : pw * W;
+    const size_t smem = gws ? 0 : (a.qgws ? (size_t)a.per_warp * sizeof(float) : pw) * W;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (exact) {
         mld::ExactArgs ea;
@@ -1137,7 +1194,7 @@ mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, co
         return MLD_ERR_CUDA;
     a.gws = gws;
     int64_t blocks = (units + W - 1) / W;
-    if (gws && blocks > gws_warps / W) blocks = gws_warps / W;
+    if ((gws || a.qgws) && blocks > gws_warps / W) blocks = gws_warps / W;
     if (blocks > 0x7fffffff) return MLD_ERR_UNSUPPORTED;
     kern<<<(unsigned)blocks, 32 * W, smem, s>>>(a);
     if (cudaGetLastError() != cudaSuccess) return MLD_ERR_CUDA;
