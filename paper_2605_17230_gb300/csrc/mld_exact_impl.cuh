@@ -39,12 +39,12 @@ struct LayoutOf {
 };
 
 // Float index within a row of an M block of row length NC (the carry of the
-// next left step, or a tall block kept for the right sweep). In the mixed-
-// precision kernel (SW = 1) the row's float4 slots are XOR-permuted by the row
-// index, so that the same column of eight consecutive rows falls in eight
-// different bank groups (rows are multiples of 32 floats long) for the
-// tensor-core fragment loads; rows shorter than 8 floats, and every row of the
-// FP32 kernel (whose loads are warp broadcasts), are stored as they are.
+// next left step, or a tall block kept for the right sweep). In the blocks a
+// tensor-core step reads or writes (SW = 1) the row's float4 slots are
+// XOR-permuted by the row index, so that the same column of eight consecutive
+// rows falls in eight different bank groups (rows are multiples of 32 floats
+// long) for the fragment loads; rows shorter than 8 floats, and every other
+// block (whose reads are warp broadcasts), are stored as they are.
 template <int NC, int SW>
 __device__ __forceinline__ int swz(int row, int col) {
     if constexpr (SW && NC >= 8) {
@@ -259,7 +259,7 @@ __device__ __forceinline__ void x_ident4(const float* C, const float* A, int k, 
 // data-site product keeps four A columns in registers, so each broadcast C
 // element feeds four FMAs). Lanes own column groups and every RG-th row; as
 // in left_step the rows split at KQP into the two beta halves.
-template <int K, int PAM, int DL, int PA, int DR, int PB, int NCOL, int KQP, int CID, int OKIND, int PAR, int SW>
+template <int K, int PAM, int DL, int PA, int DR, int PB, int NCOL, int KQP, int CID, int OKIND, int PAR, int SWC, int SWM>
 __device__ __forceinline__ float left_cols4(const float* __restrict__ C, const float* __restrict__ A,
                                             float* __restrict__ M, const float4 w, int lane) {
     constexpr int NCOLA = PA * DR;
@@ -302,7 +302,7 @@ __device__ __forceinline__ float left_cols4(const float* __restrict__ C, const f
                     o.y = fmaf(wb[bp][0], x0.y, wb[bp][1] * x1.y);
                     o.z = fmaf(wb[bp][0], x0.z, wb[bp][1] * x1.z);
                     o.w = fmaf(wb[bp][0], x0.w, wb[bp][1] * x1.w);
-                    *reinterpret_cast<float4*>(M + (bp * K + k) * NCOL + swz<NCOL, SW>(bp * K + k, col)) = o;
+                    *reinterpret_cast<float4*>(M + (bp * K + k) * NCOL + swz<NCOL, SWM>(bp * K + k, col)) = o;
                     mx = fmaxf(mx, fmaxf(fmaxf(fabsf(o.x), fabsf(o.y)), fmaxf(fabsf(o.z), fabsf(o.w))));
                 }
             };
@@ -326,7 +326,7 @@ __device__ __forceinline__ float left_cols4(const float* __restrict__ C, const f
                             const float* c0 = C + row * LDC;
 #pragma unroll
                             for (int a = 0; a < PAM; ++a) {
-                                const float4 v = *reinterpret_cast<const float4*>(c0 + swz<LDC, SW>(row, a * DL + r));
+                                const float4 v = *reinterpret_cast<const float4*>(c0 + swz<LDC, SWC>(row, a * DL + r));
                                 float4& x = a ? x1[u] : x0[u];
                                 const float cv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
@@ -347,7 +347,7 @@ __device__ __forceinline__ float left_cols4(const float* __restrict__ C, const f
                 for (int jj = j0; jj < j1; ++jj) {
                     const int k = rg + jj * RG;
                     float4 X[2];
-                    x_ident4<DL, DR, PAM, NCOLA, KQP, CID, OKIND, SW>(C, A, k, ap, rp, X);
+                    x_ident4<DL, DR, PAM, NCOLA, KQP, CID, OKIND, SWC>(C, A, k, ap, rp, X);
                     emit(k, X[0], X[1]);
                 }
             }
@@ -372,14 +372,13 @@ __device__ __forceinline__ float left_cols4(const float* __restrict__ C, const f
 // lane split at k = KQP into the beta = 0 and beta = 1 halves, so inside each
 // half the factor weights are fixed registers.
 template <int K, int PAM, int DL, int PA, int DR, int PB, int NCOL, int KQP, int CID, int OKIND, int LAST,
-          int PREC, int PAR>
+          int TEN, int PAR, int SWC, int SWM>
 __device__ __noinline__ float left_step(const float* __restrict__ C, const float* __restrict__ A,
                                         float* __restrict__ M, const float4 w, int lane) {
     constexpr int NCOLA = PA * DR;
     constexpr int LDC = PAM * DL;
-    constexpr int SW = PREC == MLD_MIXED_TF32 ? 1 : 0;
-    if constexpr (PREC == MLD_MIXED_TF32 && !CID && OKIND == K_DATA && !LAST && K >= 8 && DL >= 8 &&
-                  NCOLA >= 8) {
+    if constexpr (TEN) {
+        static_assert(SWC && SWM, "a tensor-core step reads and writes swizzled blocks");
         return gemm_tf32<K, PAM, DL, PA, DR, PB, NCOL, KQP, PAR>(C, A, M, w, lane);
     }
     // four columns per lane where a step has at least 64 float4 outputs per
@@ -387,8 +386,8 @@ __device__ __noinline__ float left_step(const float* __restrict__ C, const float
     // (its four row groups read the same column of four rows)
     constexpr bool DATA_PRODUCT = !CID && OKIND == K_DATA;
     if constexpr (!LAST && DR % 4 == 0 && (CID || DL % 4 == 0) && K * NCOLA / 4 >= 64 &&
-                  (!DATA_PRODUCT || (SW && DL <= 32))) {
-        return left_cols4<K, PAM, DL, PA, DR, PB, NCOL, KQP, CID, OKIND, PAR, SW>(C, A, M, w, lane);
+                  (!DATA_PRODUCT || (SWC && DL <= 32))) {
+        return left_cols4<K, PAM, DL, PA, DR, PB, NCOL, KQP, CID, OKIND, PAR, SWC, SWM>(C, A, M, w, lane);
     }
     float mx = 0.f;
     if constexpr (LAST) {
@@ -406,12 +405,12 @@ __device__ __noinline__ float left_step(const float* __restrict__ C, const float
                         if (a < PAM) {
                             const float* crow = C + k * LDC;
 #pragma unroll
-                            for (int r = 0; r < DL; ++r) s = fmaf(crow[swz<LDC, SW>(k, a * DL + r)], A[r * NCOLA + ap], s);
+                            for (int r = 0; r < DL; ++r) s = fmaf(crow[swz<LDC, SWC>(k, a * DL + r)], A[r * NCOLA + ap], s);
                         }
                         X[a] = s;
                     }
                 } else {
-                    x_ident<DL, DR, PAM, NCOLA, KQP, CID, OKIND, SW>(C, A, k, ap, 0, X);
+                    x_ident<DL, DR, PAM, NCOLA, KQP, CID, OKIND, SWC>(C, A, k, ap, 0, X);
                 }
                 acc0 = fmaf(wsel<PAR>(w, 0, ap, beta, 0), X[0], fmaf(wsel<PAR>(w, 1, ap, beta, 0), X[1], acc0));
                 if (PB == 2)
@@ -476,13 +475,13 @@ __device__ __noinline__ float left_step(const float* __restrict__ C, const float
                             for (int u = 0; u < KU; ++u) {
                                 const int row = rg + (jj + u) * RG;
                                 const float* c0 = C + row * LDC;
-                                const float4 v0 = *reinterpret_cast<const float4*>(c0 + swz<LDC, SW>(row, r));
+                                const float4 v0 = *reinterpret_cast<const float4*>(c0 + swz<LDC, SWC>(row, r));
                                 x0[u] = fmaf(v0.x, acol[r], x0[u]);
                                 x0[u] = fmaf(v0.y, acol[r + 1], x0[u]);
                                 x0[u] = fmaf(v0.z, acol[r + 2], x0[u]);
                                 x0[u] = fmaf(v0.w, acol[r + 3], x0[u]);
                                 if (PAM == 2) {
-                                    const float4 v1 = *reinterpret_cast<const float4*>(c0 + swz<LDC, SW>(row, DL + r));
+                                    const float4 v1 = *reinterpret_cast<const float4*>(c0 + swz<LDC, SWC>(row, DL + r));
                                     x1[u] = fmaf(v1.x, acol[r], x1[u]);
                                     x1[u] = fmaf(v1.y, acol[r + 1], x1[u]);
                                     x1[u] = fmaf(v1.z, acol[r + 2], x1[u]);
@@ -497,8 +496,8 @@ __device__ __noinline__ float left_step(const float* __restrict__ C, const float
                             for (int u = 0; u < KU; ++u) {
                                 const int row = rg + (jj + u) * RG;
                                 const float* c0 = C + row * LDC;
-                                x0[u] = fmaf(c0[swz<LDC, SW>(row, r)], acol[r], x0[u]);
-                                if (PAM == 2) x1[u] = fmaf(c0[swz<LDC, SW>(row, DL + r)], acol[r], x1[u]);
+                                x0[u] = fmaf(c0[swz<LDC, SWC>(row, r)], acol[r], x0[u]);
+                                if (PAM == 2) x1[u] = fmaf(c0[swz<LDC, SWC>(row, DL + r)], acol[r], x1[u]);
                             }
                         }
                     }
@@ -508,7 +507,7 @@ __device__ __noinline__ float left_step(const float* __restrict__ C, const float
 #pragma unroll
                         for (int bp = 0; bp < PB; ++bp) {
                             const float o = fmaf(wb[bp][0], x0[u], wb[bp][1] * x1[u]);
-                            M[(bp * K + k) * NCOL + swz<NCOL, SW>(bp * K + k, col)] = o;
+                            M[(bp * K + k) * NCOL + swz<NCOL, SWM>(bp * K + k, col)] = o;
                             mx = fmaxf(mx, fabsf(o));
                         }
                     }
@@ -518,11 +517,11 @@ __device__ __noinline__ float left_step(const float* __restrict__ C, const float
                 for (int jj = j0; jj < j1; ++jj) {
                     const int k = rg + jj * RG;
                     float X[2];
-                    x_ident<DL, DR, PAM, NCOLA, KQP, CID, OKIND, SW>(C, A, k, ap, rp, X);
+                    x_ident<DL, DR, PAM, NCOLA, KQP, CID, OKIND, SWC>(C, A, k, ap, rp, X);
 #pragma unroll
                     for (int bp = 0; bp < PB; ++bp) {
                         const float o = fmaf(wb[bp][0], X[0], wb[bp][1] * X[1]);
-                        M[(bp * K + k) * NCOL + swz<NCOL, SW>(bp * K + k, col)] = o;
+                        M[(bp * K + k) * NCOL + swz<NCOL, SWM>(bp * K + k, col)] = o;
                         mx = fmaxf(mx, fabsf(o));
                     }
                 }
@@ -657,6 +656,29 @@ struct Ctx {
     bool zero, bad;
 };
 
+// Size of the data-site products that run on the tensor cores in the mixed
+// kernel (smaller ones run in FP32: the split and the fragment traffic cost
+// more than the tensor pipe saves there).
+constexpr int kTensorMinK = 32, kTensorMinDL = 16, kTensorMinN = 32;
+
+// Left step I of column C runs on the tensor cores.
+template <int D, int PREC, int C, int I>
+struct TensorStep {
+    static constexpr SiteStep st = PlanOf<D>::plan.steps[C * (D + 1) + I];
+    static constexpr bool value = PREC == MLD_MIXED_TF32 && I < D && !st.cid && st.okind == K_DATA &&
+                                  st.K >= kTensorMinK && st.Dl >= kTensorMinDL && st.pa * st.Dr >= kTensorMinN;
+};
+
+// The M blocks of left step I are stored swizzled: it is a tensor-core step,
+// or they are the carry of one (conflict-free fragment loads); every other
+// block keeps the plain layout (its reads are warp broadcasts).
+template <int D, int PREC, int C, int I>
+struct SwizzledBlocks {
+    static constexpr bool value = TensorStep<D, PREC, C, I>::value ||
+                                  (I < D && !PlanOf<D>::plan.steps[C * (D + 1) + I].tall &&
+                                   TensorStep<D, PREC, C, (I < D ? I + 1 : I)>::value);
+};
+
 template <int D, int PREC, int C, int I>
 __device__ __forceinline__ void left_site(Ctx<D, PREC>& x) {
     constexpr SiteStep st = PlanOf<D>::plan.steps[C * (D + 1) + I];
@@ -673,8 +695,11 @@ __device__ __forceinline__ void left_site(Ctx<D, PREC>& x) {
     float4 w = I == 0 ? make_float4(1.f, 1.f, 1.f, 1.f)
                       : *reinterpret_cast<const float4*>(x.wts + 4 * ((I - 1) * D + C));
     w.x *= sc; w.y *= sc; w.z *= sc; w.w *= sc;
+    constexpr int TEN = TensorStep<D, PREC, C, I>::value ? 1 : 0;
+    constexpr int SWC = (I > 0 && SwizzledBlocks<D, PREC, C, (I > 0 ? I - 1 : 0)>::value) ? 1 : 0;
+    constexpr int SWM = SwizzledBlocks<D, PREC, C, I>::value ? 1 : 0;
     const float mx = left_step<st.K, st.pam, st.Dl, st.pa, st.Dr, st.pb, st.ncol, st.kq_prev, st.cid, st.okind,
-                               (I == D), PREC, st.parity>(cin, x.mps + st.offA, M, w, x.lane);
+                               (I == D), TEN, st.parity, SWC, SWM>(cin, x.mps + st.offA, M, w, x.lane);
     // max |M| over the warp as the integer maximum of the bit patterns (the
     // order of non-negative floats); its biased exponent gives frexp's
     const unsigned mbits = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
@@ -695,7 +720,7 @@ __device__ __forceinline__ void right_site(Ctx<D, PREC>& x) {
     constexpr int omout = LayoutOf<D>::lay.mout[C * (D + 1) + I];
     if (x.zero || x.bad) return;
     right_step<st.K, st.S, st.pb, st.kq, st.ncol, st.tall, st.gid, st.rmode, st.nkind,
-               PREC == MLD_MIXED_TF32 ? 1 : 0>(
+               SwizzledBlocks<D, PREC, C, I>::value ? 1 : 0>(
         x.arena + omout, x.arena + ogin, x.arena + otout, x.mps + st.offN, x.lane);
     __syncwarp();
 }
@@ -896,10 +921,8 @@ bool launch_dp(const ExactArgs& a, cudaStream_t s, int warps_per_block) {
     return cudaGetLastError() == cudaSuccess;
 }
 
-// Distances whose mixed-precision kernel (split-TF32 tensor-core products,
-// swizzled blocks) is faster than the FP32 one; at the others the products
-// are too small for the split and the fragment traffic to pay, and a
-// mixed-precision request runs the FP32 kernel.
+// Distances with data-site products of the tensor-core size; at the others
+// a mixed-precision request runs the FP32 kernel.
 template <int D>
 constexpr bool kTensorPays = D == 9 || D == 11;
 
