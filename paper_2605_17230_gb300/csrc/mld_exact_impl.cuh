@@ -150,6 +150,19 @@ __device__ __forceinline__ float gemm_tf32(const float* __restrict__ C, const fl
     weights8<PAR>(w, 0, wa[0]);
     weights8<PAR>(w, 1, wa[1]);
     float mx = 0.f;
+    // with one tile group, the split B fragments of the whole site stay in
+    // registers across the row blocks
+    constexpr bool BHOLD = NTG == NT && NT * KS <= 8;
+    unsigned bhh[BHOLD ? KS : 1][BHOLD ? NT : 1][4];
+    if constexpr (BHOLD) {
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                split_tf32(A[(8 * ks + t) * NCOLA + nt * 8 + g], bhh[ks][nt][0], bhh[ks][nt][1]);
+                split_tf32(A[(8 * ks + t + 4) * NCOLA + nt * 8 + g], bhh[ks][nt][2], bhh[ks][nt][3]);
+            }
+    }
 #pragma unroll 1
     for (int kb = 0; kb < KB; ++kb) {
         const int r0 = kb * 16 + g, r1 = r0 + 8;
@@ -179,8 +192,12 @@ __device__ __forceinline__ float gemm_tf32(const float* __restrict__ C, const fl
                 for (int j = 0; j < NTG; ++j) {
                     const int nt = n0 + j;
                     unsigned bh0, bl0, bh1, bl1;
-                    split_tf32(A[(8 * ks + t) * NCOLA + nt * 8 + g], bh0, bl0);
-                    split_tf32(A[(8 * ks + t + 4) * NCOLA + nt * 8 + g], bh1, bl1);
+                    if constexpr (BHOLD) {
+                        bh0 = bhh[ks][nt][0]; bl0 = bhh[ks][nt][1]; bh1 = bhh[ks][nt][2]; bl1 = bhh[ks][nt][3];
+                    } else {
+                        split_tf32(A[(8 * ks + t) * NCOLA + nt * 8 + g], bh0, bl0);
+                        split_tf32(A[(8 * ks + t + 4) * NCOLA + nt * 8 + g], bh1, bl1);
+                    }
 #pragma unroll
                     for (int a = 0; a < PAM; ++a) {
                         mma_tf32(acc[j][a], al[a][0], al[a][1], al[a][2], al[a][3], bh0, bh1);
