@@ -778,22 +778,30 @@ __device__ void column_sandwich(int d, int c, const float* __restrict__ L, const
         float env[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) env[k] = 0.f;
-        for (int idx = lane; idx < size; idx += 32) {
-            const int br = (idx >> r) & 1, br1 = (idx >> (r + 1)) & 1, ar1 = (idx >> (d + 1)) & 1;
-            const int base = (idx & ~bit1 & ~spare) | (ar1 << (r + 1));
-            const float g = Gn[idx];
-            float f = 0.f;
+        // the states in eight groups by the factor's bits (a_{r+1}, b_r,
+        // b_{r+1}), so that each group's environment entries are fixed
+        // registers: idx = low | b_r << r | b_{r+1} << (r+1) | mid << (r+2)
+        // | a_{r+1} << (d+1), and F0 holds a_{r+1} at bit r+1, a_r at d+1
+        (void)bit1;
+        const int nrest = size >> 3;
 #pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                const float fo = F0[base | (a << (d + 1))];
-                const float w = qweight(wq, par, a, ar1, br, br1);
-                f = fmaf(fo, w, f);
-                const int k = a | (ar1 << 1) | (br << 2) | (br1 << 3);
-#pragma unroll
-                for (int kk = 0; kk < 16; ++kk)
-                    if (kk == k) env[kk] = fmaf(fo, g, env[kk]);
+        for (int combo = 0; combo < 8; ++combo) {
+            const int ar1 = combo & 1, br = (combo >> 1) & 1, br1 = (combo >> 2) & 1;
+            const float w0 = qweight(wq, par, 0, ar1, br, br1), w1 = qweight(wq, par, 1, ar1, br, br1);
+            float e0 = 0.f, e1 = 0.f;
+            for (int rs = lane; rs < nrest; rs += 32) {
+                const int low = rs & ((1 << r) - 1), mid = rs >> r;
+                const int core = low | (br << r) | (mid << (r + 2));
+                const int idx = core | (br1 << (r + 1)) | (ar1 << (d + 1));
+                const int fb = core | (ar1 << (r + 1));
+                const float g = Gn[idx];
+                const float fa0 = F0[fb], fa1 = F0[fb | spare];
+                F1[idx] = fmaf(fa0, w0, fa1 * w1);
+                e0 = fmaf(fa0, g, e0);
+                e1 = fmaf(fa1, g, e1);
             }
-            F1[idx] = f;
+            env[0 | (ar1 << 1) | (br << 2) | (br1 << 3)] += e0;
+            env[1 | (ar1 << 1) | (br << 2) | (br1 << 3)] += e1;
         }
         // bucket (a, a', b, b') -> (u, v) of this factor
         float eu[4] = {0.f, 0.f, 0.f, 0.f};
