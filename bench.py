@@ -246,10 +246,10 @@ def run_mixed(args):
 
 # Truncating points (chi below the exact bond 2^floor(d/2)): (d, chi, syndromes per point).
 # The large-d points decode one wave of resident warps each (the kernel keeps one
-# (syndrome, class) per warp in a global-memory workspace), a bounded sample of the
-# 16,384-syndrome workload.
-LARGE_POINTS = [(9, 8, 65536), (11, 16, 16384), (17, 32, 608), (17, 64, 608), (25, 32, 608)]
-LARGE_POINTS_ALL = LARGE_POINTS + [(17, 128, 476), (25, 64, 524), (25, 128, 154)]
+# (syndrome, l_Z) per warp in a global-memory workspace: 2,432 warps, 1,216 syndromes),
+# a bounded sample of the 16,384-syndrome workload.
+LARGE_POINTS = [(9, 8, 65536), (11, 16, 16384), (17, 32, 1216), (17, 64, 1216), (25, 32, 1216)]
+LARGE_POINTS_ALL = LARGE_POINTS + [(17, 128, 952), (25, 64, 1048), (25, 128, 308)]
 
 
 def run_large(args):

@@ -1,6 +1,7 @@
 // Boundary-MPS coset contraction on sm_103a (FP32 path) and the C-ABI.
 //
-// One warp owns one (syndrome, class) unit and keeps its whole state in
+// One warp owns one (syndrome, l_Z) unit -- both classes l_X = 0, 1, which
+// share columns 0..d-2 (see decode_unit) -- and keeps its whole state in
 // shared memory: the per-qubit weights, the boundary MPS, two carry buffers
 // and the Householder store. A unit runs, for every qubit column c
 // (Sec. 3.2.1, boundary MPS of the generator-picture network, Eq. 7):
@@ -339,7 +340,8 @@ __device__ bool jacobi(float* X, int L, int ldx, int nv, float* acc, int lane) {
 }
 
 // ------------------------------------------------------------------ kernel
-// One (syndrome, class) unit on one warp, with its state at ws (shared
+// One (syndrome, class) unit on one warp (the adjoint's unit; with pair, a
+// (syndrome, l_Z) unit as below), with its state at ws (shared
 // memory, or this warp's slice of the global workspace); returns ln Z.
 // rotate: sweep the half-turn image of the problem (qubit (r,c) takes the
 // data of qubit (d-1-r, d-1-c)); the layout maps onto itself, so the same
