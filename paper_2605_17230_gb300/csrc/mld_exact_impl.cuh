@@ -390,7 +390,7 @@ __device__ __forceinline__ float left_cols4(const float* __restrict__ C, const f
 // half the factor weights are fixed registers.
 template <int K, int PAM, int DL, int PA, int DR, int PB, int NCOL, int KQP, int CID, int OKIND, int LAST,
           int TEN, int PAR, int SWC, int SWM>
-__device__ __noinline__ float left_step(const float* __restrict__ C, const float* __restrict__ A,
+__device__ __forceinline__ float left_step(const float* __restrict__ C, const float* __restrict__ A,
                                         float* __restrict__ M, const float4 w, int lane) {
     constexpr int NCOLA = PA * DR;
     constexpr int LDC = PAM * DL;
@@ -583,7 +583,7 @@ __device__ __forceinline__ float t_relabel(const float* __restrict__ Mq, const f
 // carry G, then IDENT (carry = T, written to t) or DENSE (site = T, written
 // straight into the MPS buffer; carry = identity).
 template <int ROWS, int S, int PB, int KQ, int NC, int TALL, int GID, int RMODE, int NKIND, int SW>
-__device__ __noinline__ void right_step(const float* __restrict__ Mq, const float* __restrict__ g,
+__device__ __forceinline__ void right_step(const float* __restrict__ Mq, const float* __restrict__ g,
                                         float* __restrict__ t, float* __restrict__ site, int lane) {
     constexpr int COLS = PB * S;
     float* dst = (RMODE == R_DENSE) ? site : t;
@@ -662,6 +662,25 @@ __device__ __noinline__ void right_step(const float* __restrict__ Mq, const floa
     }
 }
 
+// Steps of at most this many outputs are inlined into the sweep; larger ones
+// are calls shared by every site of the same shape. The calls of small steps
+// cost more than their work (d=7: 1.55x, d=9: 1.2x once inlined); at d=13
+// inlining raises register pressure past its 255 and halves the speed.
+template <int D>
+constexpr int kInlineOutputs = D <= 11 ? 1024 : 0;
+
+template <int K, int PAM, int DL, int PA, int DR, int PB, int NCOL, int KQP, int CID, int OKIND, int LAST,
+          int TEN, int PAR, int SWC, int SWM>
+__device__ __noinline__ float left_step_call(const float* __restrict__ C, const float* __restrict__ A,
+                                             float* __restrict__ M, const float4 w, int lane) {
+    return left_step<K, PAM, DL, PA, DR, PB, NCOL, KQP, CID, OKIND, LAST, TEN, PAR, SWC, SWM>(C, A, M, w, lane);
+}
+template <int ROWS, int S, int PB, int KQ, int NC, int TALL, int GID, int RMODE, int NKIND, int SW>
+__device__ __noinline__ void right_step_call(const float* __restrict__ Mq, const float* __restrict__ g,
+                                             float* __restrict__ t, float* __restrict__ site, int lane) {
+    right_step<ROWS, S, PB, KQ, NC, TALL, GID, RMODE, NKIND, SW>(Mq, g, t, site, lane);
+}
+
 template <int D, int PREC>
 struct Ctx {
     float* wts;
@@ -715,8 +734,14 @@ __device__ __forceinline__ void left_site(Ctx<D, PREC>& x) {
     constexpr int TEN = TensorStep<D, PREC, C, I>::value ? 1 : 0;
     constexpr int SWC = (I > 0 && SwizzledBlocks<D, PREC, C, (I > 0 ? I - 1 : 0)>::value) ? 1 : 0;
     constexpr int SWM = SwizzledBlocks<D, PREC, C, I>::value ? 1 : 0;
-    const float mx = left_step<st.K, st.pam, st.Dl, st.pa, st.Dr, st.pb, st.ncol, st.kq_prev, st.cid, st.okind,
-                               (I == D), TEN, st.parity, SWC, SWM>(cin, x.mps + st.offA, M, w, x.lane);
+    constexpr bool SMALL = st.K * st.pa * st.Dr * st.pb <= kInlineOutputs<D>;
+    float mx;
+    if constexpr (SMALL)
+        mx = left_step<st.K, st.pam, st.Dl, st.pa, st.Dr, st.pb, st.ncol, st.kq_prev, st.cid, st.okind,
+                       (I == D), TEN, st.parity, SWC, SWM>(cin, x.mps + st.offA, M, w, x.lane);
+    else
+        mx = left_step_call<st.K, st.pam, st.Dl, st.pa, st.Dr, st.pb, st.ncol, st.kq_prev, st.cid, st.okind,
+                            (I == D), TEN, st.parity, SWC, SWM>(cin, x.mps + st.offA, M, w, x.lane);
     // max |M| over the warp as the integer maximum of the bit patterns (the
     // order of non-negative floats); its biased exponent gives frexp's
     const unsigned mbits = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
@@ -736,9 +761,14 @@ __device__ __forceinline__ void right_site(Ctx<D, PREC>& x) {
     constexpr int otout = LayoutOf<D>::lay.tout[C * (D + 1) + I];
     constexpr int omout = LayoutOf<D>::lay.mout[C * (D + 1) + I];
     if (x.zero || x.bad) return;
-    right_step<st.K, st.S, st.pb, st.kq, st.ncol, st.tall, st.gid, st.rmode, st.nkind,
-               SwizzledBlocks<D, PREC, C, I>::value ? 1 : 0>(
-        x.arena + omout, x.arena + ogin, x.arena + otout, x.mps + st.offN, x.lane);
+    if constexpr (st.K * st.pb * st.S <= kInlineOutputs<D>)
+        right_step<st.K, st.S, st.pb, st.kq, st.ncol, st.tall, st.gid, st.rmode, st.nkind,
+                   SwizzledBlocks<D, PREC, C, I>::value ? 1 : 0>(
+            x.arena + omout, x.arena + ogin, x.arena + otout, x.mps + st.offN, x.lane);
+    else
+        right_step_call<st.K, st.S, st.pb, st.kq, st.ncol, st.tall, st.gid, st.rmode, st.nkind,
+                        SwizzledBlocks<D, PREC, C, I>::value ? 1 : 0>(
+            x.arena + omout, x.arena + ogin, x.arena + otout, x.mps + st.offN, x.lane);
     __syncwarp();
 }
 
