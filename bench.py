@@ -38,8 +38,8 @@ METRIC = "syndromes/s at d=9 χ=32 (4 cosets), mixed-precision vs FP32, |ΔlogP|
 # DRAM bytes per syndrome of the decode kernel (dram__bytes_read.sum + write.sum of one ncu
 # capture of 8,192 syndromes, profiles/decode_exact_d9_chi32_full.md), valid only for the kernel
 # sources they were taken on: any change to them makes the traffic unknown (null).
-TRAFFIC_SOURCES_SHA = "f309ee97e1a78b67"
-TRAFFIC_BYTES_PER_SYNDROME = {0: (273.152e3 + 1.536e3) / 8192, 2: (273.408e3 + 4.352e3) / 8192}
+TRAFFIC_SOURCES_SHA = "3d9a42386b4f2832"
+TRAFFIC_BYTES_PER_SYNDROME = {0: (282.880e3 + 0.512e3) / 8192, 2: (284.672e3 + 3.328e3) / 8192}
 
 
 # sources of the headline kernel (decode_exact_kernel<9, *>): its plan, layout and templates
