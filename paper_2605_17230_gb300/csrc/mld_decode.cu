@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "mld_exact.h"
+#include "mld_grad.h"
 #include "mld_internal.h"
 
 extern "C" mld_status mld_code_build_host(int d, mld_code** out);
@@ -1228,13 +1229,38 @@ mld_status mld_decode_grad(const mld_code* Cc, const float* noise, const uint64_
     const mld::Plan& P = pd->plan;
     if (P.svd_sites != 0) return MLD_ERR_UNSUPPORTED;       // exact environments need untruncated chi
     const int d = C->d, n = C->n;
-    const int64_t full = (int64_t)1 << (d + 1), size = full << 1;
-    const int64_t per_warp = P.floats_per_warp + 2 * (d - 1) * full + 2 * full + (d + 1) * size + 2 * size + full +
-                             ((4 * d + 1) & ~1) + 8 * n;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return MLD_ERR_CUDA;
+    if (mld::grad_dense_supported(d)) {
+        // dense states on chip: one block per (syndrome, class) unit
+        const int64_t blocks = mld::grad_dense_blocks(d, sms, B);
+        if (blocks < 1) return MLD_ERR_CUDA;
+        const size_t bytes = (size_t)blocks * mld::grad_dense_workspace_floats(d) * sizeof(float);
+        if (bytes > C->gradws_bytes) {
+            cudaFree(C->d_gradws);
+            C->d_gradws = nullptr;
+            C->gradws_bytes = 0;
+            if (cudaMalloc(&C->d_gradws, bytes) != cudaSuccess) return MLD_ERR_NOMEM;
+            C->gradws_bytes = bytes;
+        }
+        mld::GradDenseArgs ga;
+        ga.dmask = C->d_dmask;
+        ga.noise = noise;
+        ga.syn = syn;
+        ga.dlogP = dlogP;
+        ga.logP = logP;
+        ga.dnoise = dnoise;
+        ga.lws = C->d_gradws;
+        ga.B = B;
+        ga.words = C->words;
+        return mld::launch_grad_dense(d, ga, blocks, reinterpret_cast<cudaStream_t>(stream)) ? MLD_OK
+                                                                                              : MLD_ERR_CUDA;
+    }
+    const int64_t full = (int64_t)1 << (d + 1), size = full << 1;
+    const int64_t per_warp = P.floats_per_warp + 2 * (d - 1) * full + 2 * full + (d + 1) * size + 2 * size + full +
+                             ((4 * d + 1) & ~1) + 8 * n;
     const int W = 4;
     int64_t nw = (int64_t)sms * 16;
     const int64_t need = ((4 * B + W - 1) / W) * W;
