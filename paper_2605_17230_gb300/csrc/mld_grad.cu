@@ -7,25 +7,29 @@
 // entries (one plaquette variable per row, absent plaquettes pinned to 0), so
 // the states are kept dense on chip. One thread block owns one (syndrome,
 // class) unit:
-//   forward   L_{c+1} = T_c L_c for c = 0..d-1, T_c applied one qubit factor
-//             at a time to states over d+2 bits and rescaled by a power of two
-//             per column; L_1..L_{d-1} go to the block's global slice, and
+//   forward   L_{c+1} = T_c L_c for c = 0..d-1, T_c applied qubit factor by
+//             qubit factor to states over d+2 bits and rescaled by a power of
+//             two per column; L_1..L_{d-1} go to the block's global slice, and
 //             ln Z_l = ln sum L_d + the accumulated exponents.
 //   backward  for c = d-1..0: the transposed factors carry R_{c+1} back
-//             through column c (G_d..G_0, all kept in shared memory) and G_0
+//             through column c (the states G_r kept in shared memory) and G_0
 //             gives R_c; then the factors are re-applied from L_c, and each
 //             factor's environment is the contraction of the state before it
-//             with G after it, bucketed by the factor's four plaquette
-//             variables.
-// <R_{c+1}|T_c|L_c> = sum_k env_k w_k of any one factor (Euler's identity for
+//             with G after it, bucketed by the factor's weight slot.
+// <R_{c+1}|T_c|L_c> = sum_j env_j w_j of any one factor (Euler's identity for
 // a linear function), so every ratio env / Z is scale-free.
 //
 // State layout before factor r (qubit (r, c)) of column c, bit positions of
 // a (d+2)-bit index: bits 0..r hold beta_0..beta_r (corner column c+1), bits
 // r+1..d hold alpha_{r+1}..alpha_d (corner column c), bit d+1 holds alpha_r.
 // Factor r sums alpha_r out, brings beta_{r+1} in and moves alpha_{r+1} to
-// bit d+1; it touches bits r, r+1 and d+1 only, so a thread owns the eight
-// entries of one assignment of the other bits ("rest").
+// bit d+1, touching bits r, r+1 and d+1 only; factors r and r+1 together
+// touch bits r, r+1, r+2 and d+1. So the factors are applied in pairs
+// (r, r+1), r even, each thread holding in registers the sixteen entries of
+// one assignment of the other bits (a "rest"); d odd leaves factor d-1 as a
+// single step over eight entries per rest. Only the states before even
+// factors (and after the last) are stored; the state between the two
+// factors of a pair is recomputed in registers where it is needed.
 #include <math.h>
 #include <stdint.h>
 
@@ -37,18 +41,20 @@ namespace {
 
 template <int D>
 struct GradShape {
+    static_assert(D % 2 == 1, "odd distances only");
     static constexpr int N = D * D;
     static constexpr int HALF = 1 << (D + 1);       // states over one corner column
     static constexpr int SIZE = HALF << 1;          // states inside a column (one more bit)
-    static constexpr int REST = SIZE >> 3;          // eight entries per thread and factor
-    static constexpr int NT = REST >= 256 ? 256 : (REST >= 64 ? 64 : 32);
+    static constexpr int REST1 = SIZE >> 3;         // rests of a single step (eight entries each)
+    static constexpr int REST2 = SIZE >> 4;         // rests of a pair step (sixteen entries each)
+    static constexpr int NT = REST2 >= 128 ? 128 : 32;
     static constexpr int NW = NT / 32;
+    static constexpr int NG = (D + 1) / 2 + 1;      // stored G states: r = 0, 2, .., d-1 and d
     // shared memory (floats)
-    static constexpr int off_w = 0;                          // 4N factor weights w_q[u + 2v]
-    static constexpr int off_g = (4 * N + 3) & ~3;           // G_0..G_d, SIZE each
-    static constexpr int off_f0 = off_g + (D + 1) * SIZE;     // forward state (ping)
-    static constexpr int off_f1 = off_f0 + SIZE;              // forward state (pong)
-    static constexpr int off_r = off_f1 + SIZE;               // HALF: L_{c+1} staging, R_{c+1}
+    static constexpr int off_w = 0;                          // 4N factor weights (slot order Wp)
+    static constexpr int off_g = (4 * N + 3) & ~3;           // NG states of SIZE
+    static constexpr int off_f = off_g + NG * SIZE;           // SIZE: the state before factor 0
+    static constexpr int off_r = off_f + SIZE;                // HALF: L_{c+1} staging, R_{c+1}
     static constexpr int off_red = off_r + HALF;              // D x NW x 4 per-warp environment sums
     static constexpr int off_env = off_red + D * NW * 4;      // D x 4 environments of a column
     static constexpr int off_misc = off_env + D * 4;          // 32: per-warp reductions
@@ -57,8 +63,13 @@ struct GradShape {
     static constexpr int floats = off_acc + 8 * N;
     static constexpr int lfloats = (D - 1) * HALF;            // global: L_1..L_{d-1}
     // blocks per SM that shared memory allows (the register budget is held to it)
-    static constexpr int MINB = (227 * 1024) / (floats * 4 + 1024) < 8 ? (227 * 1024) / (floats * 4 + 1024) : 8;
+    static constexpr int FIT = (227 * 1024) / (floats * 4 + 1024);
+    static constexpr int MINB = FIT < 16 ? FIT : 16;
 };
+
+// G state slot of the state before factor r (r even, or r = d).
+template <int D>
+__device__ __forceinline__ constexpr int gslot(int r) { return r == D ? (D + 1) / 2 : r / 2; }
 
 // Rows i whose plaquette (i, j) is a check (the others are pinned to 0).
 template <int D>
@@ -73,38 +84,34 @@ __device__ __forceinline__ int present_rows(int j) {
 // alpha_r ^ beta_{r+1} and v0 = alpha_{r+1} ^ beta_r: for parity (r + c) even
 // these are the X and Z powers (u, v) of the factor p_q[E_q X^u Z^v]; for odd
 // parity the two exchange roles, so Wp[j] = w_q[j with bits 0 and 1 swapped].
-// Entry k = a | a'<<1 | b<<2 | b'<<3 of the factor then reads Wp[jk(k)].
-__device__ __forceinline__ constexpr int jk(int k) {
-    return ((k & 1) ^ ((k >> 3) & 1)) + 2 * (((k >> 1) & 1) ^ ((k >> 2) & 1));
-}
+// The factor's entry (a, a', b, b') = (alpha_r, alpha_{r+1}, beta_r,
+// beta_{r+1}) reads Wp[jw(a, a', b, b')].
+__device__ __forceinline__ constexpr int jw(int a, int ap, int b, int bp) { return (a ^ bp) + 2 * (ap ^ b); }
+
 template <int D>
 __device__ __forceinline__ void factor_weights(const float* w, int r, int c, float (&Wp)[4]) {
     const float4 v = *reinterpret_cast<const float4*>(w + 4 * (r * D + c));
     Wp[0] = v.x; Wp[1] = v.y; Wp[2] = v.z; Wp[3] = v.w;
 }
 
-__device__ __forceinline__ int rest_core(int rs, int r) {
-    return (rs & ((1 << r) - 1)) | ((rs >> r) << (r + 2));
-}
-
-// Shared-memory position of entry e of the state before factor r (d >= 7).
-// The 32 lanes of a warp own 32 consecutive rests, i.e. vary the five lowest
-// index bits outside {r, r+1, d+1}; for r <= 4 two of those bits are bank
-// bits, so a plain layout puts a warp on 8 or 16 banks. XORing bits 5 and 6
-// into the bank bits with the masks below makes the lane -> bank map a
-// bijection both for factor r-1 (which writes the state) and for factor r
-// (which reads it); each mask pair was chosen so that, together with the
-// bank bits left free by the two factors, it spans all five bank bits.
-__device__ __forceinline__ int swz_mask5(int r) {
-    return r == 0 ? 1 : r == 1 ? 5 : r == 2 ? 10 : r == 3 ? 20 : r == 4 ? 8 : 0;
-}
-__device__ __forceinline__ int swz_mask6(int r) {
-    return r <= 1 ? 2 : r == 2 ? 4 : r == 3 ? 8 : r <= 5 ? 16 : 0;
+// Shared-memory position of entry e of a stored state with layout index lay
+// (the state before factor lay; d >= 7). The 32 lanes of a warp own 32
+// consecutive rests, i.e. vary the five lowest index bits that the step
+// leaves fixed; when the step touches bank bits (0..4), a plain layout puts
+// the warp on 4 to 16 banks. XORing bits 5, 6 and 7 into the bank bits with
+// these masks makes the lane -> bank map a bijection for both steps that
+// access the state (the pair or single step that writes it and the one that
+// reads it).
+__device__ __forceinline__ constexpr int swz_mask(int lay, int bit) {
+    return bit == 5 ? (lay == 0 ? 1 : lay == 2 ? 9 : lay == 4 ? 4 : 0)
+         : bit == 6 ? (lay == 0 ? 2 : lay == 2 ? 18 : lay == 4 ? 8 : 0)
+                    : (lay == 0 || lay == 2 ? 4 : lay == 4 || lay == 6 ? 16 : 0);
 }
 template <int D>
-__device__ __forceinline__ int phys(int e, int r) {
+__device__ __forceinline__ int phys(int e, int lay) {
     if (D < 7) return e;
-    return e ^ (((e >> 5) & 1) ? swz_mask5(r) : 0) ^ (((e >> 6) & 1) ? swz_mask6(r) : 0);
+    return e ^ (((e >> 5) & 1) ? swz_mask(lay, 5) : 0) ^ (((e >> 6) & 1) ? swz_mask(lay, 6) : 0) ^
+           (((e >> 7) & 1) ? swz_mask(lay, 7) : 0);
 }
 
 // Index of the corner-column state entry that feeds entry e of the state
@@ -113,6 +120,157 @@ template <int D>
 __device__ __forceinline__ int left_index(int e) {
     constexpr int HALF = GradShape<D>::HALF;
     return (e & (HALF - 1) & ~1) | (e >> (D + 1));
+}
+
+// ------------------------------------------------------------- single steps
+// Entry k of a rest: bit r = k & 1, bit r+1 = (k >> 1) & 1, bit d+1 = k >> 2.
+// phys is linear over GF(2), so the offsets are one swizzled base XOR
+// constants.
+template <int D>
+__device__ __forceinline__ void single_offsets(int rs, int r, int lay, int (&o)[8]) {
+    constexpr int PS = GradShape<D>::HALF;
+    const int core = (rs & ((1 << r) - 1)) | ((rs >> r) << (r + 2));
+    const int base = phys<D>(core, lay);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) o[k] = base ^ phys<D>((k & 1) * (1 << r) + ((k >> 1) & 1) * (2 << r) + (k >> 2) * PS, lay);
+}
+
+// F_{r+1}[b, b', a'] = sum_a F_r[b, a', a] w(a, a', b, b')
+template <int D>
+__device__ __forceinline__ void single_forward(const float* __restrict__ Fr, float* __restrict__ Fn,
+                                               const float (&Wp)[4], int r, int rs) {
+    int oi[8], oo[8];
+    single_offsets<D>(rs, r, r, oi);
+    single_offsets<D>(rs, r, r + 1, oo);
+    float x[8];   // x[b | a'<<1 | a<<2]
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = Fr[oi[k]];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {   // k = b | b'<<1 | a'<<2
+        const int b = k & 1, bp = (k >> 1) & 1, ap = k >> 2, i0 = b | (ap << 1);
+        Fn[oo[k]] = fmaf(x[i0], Wp[jw(0, ap, b, bp)], x[i0 | 4] * Wp[jw(1, ap, b, bp)]);
+    }
+}
+
+// G_r[b, a', a] = sum_b' G_{r+1}[b, b', a'] w(a, a', b, b')
+template <int D>
+__device__ __forceinline__ void single_backward(const float* __restrict__ Gn, float* __restrict__ Gr,
+                                                const float (&Wp)[4], int r, int rs) {
+    int oi[8], oo[8];
+    single_offsets<D>(rs, r, r + 1, oi);
+    single_offsets<D>(rs, r, r, oo);
+    float y[8];   // y[b | b'<<1 | a'<<2]
+#pragma unroll
+    for (int k = 0; k < 8; ++k) y[k] = Gn[oi[k]];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {   // k = b | a'<<1 | a<<2
+        const int b = k & 1, ap = (k >> 1) & 1, a = k >> 2, i0 = b | (ap << 2);
+        Gr[oo[k]] = fmaf(y[i0], Wp[jw(a, ap, b, 0)], y[i0 | 2] * Wp[jw(a, ap, b, 1)]);
+    }
+}
+
+// e[jw(a, a', b, b')] += F_r[b, a', a] G_{r+1}[b, b', a']
+template <int D>
+__device__ __forceinline__ void single_environment(const float* __restrict__ Fr, const float* __restrict__ Gn,
+                                                   int r, int rs, float (&e)[4]) {
+    int o0[8], o1[8];
+    single_offsets<D>(rs, r, r, o0);
+    single_offsets<D>(rs, r, r + 1, o1);
+    float x[8], y[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        x[k] = Fr[o0[k]];   // x[b | a'<<1 | a<<2]
+        y[k] = Gn[o1[k]];   // y[b | b'<<1 | a'<<2]
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const int a = k & 1, ap = (k >> 1) & 1, b = (k >> 2) & 1, bp = (k >> 3) & 1;
+        e[jw(a, ap, b, bp)] = fmaf(x[b | (ap << 1) | (a << 2)], y[b | (bp << 1) | (ap << 2)], e[jw(a, ap, b, bp)]);
+    }
+}
+
+// --------------------------------------------------------------- pair steps
+// Entry g of a rest: bit r = g & 1, bit r+1 = (g >> 1) & 1, bit r+2 =
+// (g >> 2) & 1, bit d+1 = g >> 3. Before factor r the four bits hold
+// (beta_r, alpha_{r+1}, alpha_{r+2}, alpha_r); between the two factors
+// (beta_r, beta_{r+1}, alpha_{r+2}, alpha_{r+1}); after factor r+1
+// (beta_r, beta_{r+1}, beta_{r+2}, alpha_{r+2}).
+template <int D>
+__device__ __forceinline__ void pair_offsets(int rs, int r, int lay, int (&o)[16]) {
+    constexpr int PS = GradShape<D>::HALF;
+    const int core = (rs & ((1 << r) - 1)) | ((rs >> r) << (r + 3));
+    const int base = phys<D>(core, lay);
+#pragma unroll
+    for (int g = 0; g < 16; ++g)
+        o[g] = base ^ phys<D>((g & 1) * (1 << r) + ((g >> 1) & 1) * (2 << r) + ((g >> 2) & 1) * (4 << r) +
+                                  (g >> 3) * PS, lay);
+}
+
+__device__ __forceinline__ constexpr int g4(int b0, int b1, int b2, int b3) { return b0 | (b1 << 1) | (b2 << 2) | (b3 << 3); }
+
+// factor r on the sixteen entries: Y = state between the factors from X
+__device__ __forceinline__ void pair_first(const float (&X)[16], const float (&W)[4], float (&Y)[16]) {
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {   // m = (b_r, b_{r+1}, a_{r+2}, a_{r+1})
+        const int br = m & 1, br1 = (m >> 1) & 1, ar2 = (m >> 2) & 1, ar1 = m >> 3;
+        Y[m] = fmaf(X[g4(br, ar1, ar2, 0)], W[jw(0, ar1, br, br1)], X[g4(br, ar1, ar2, 1)] * W[jw(1, ar1, br, br1)]);
+    }
+}
+// factor r+1: Z = state after the pair from Y
+__device__ __forceinline__ void pair_second(const float (&Y)[16], const float (&W)[4], float (&Z)[16]) {
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {   // m = (b_r, b_{r+1}, b_{r+2}, a_{r+2})
+        const int br = m & 1, br1 = (m >> 1) & 1, br2 = (m >> 2) & 1, ar2 = m >> 3;
+        Z[m] = fmaf(Y[g4(br, br1, ar2, 0)], W[jw(0, ar2, br1, br2)], Y[g4(br, br1, ar2, 1)] * W[jw(1, ar2, br1, br2)]);
+    }
+}
+// transposed factor r+1: Gy (between the factors) from Gz (after the pair)
+__device__ __forceinline__ void pair_second_t(const float (&Gz)[16], const float (&W)[4], float (&Gy)[16]) {
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {   // m = (b_r, b_{r+1}, a_{r+2}, a_{r+1})
+        const int br = m & 1, br1 = (m >> 1) & 1, ar2 = (m >> 2) & 1, ar1 = m >> 3;
+        Gy[m] = fmaf(Gz[g4(br, br1, 0, ar2)], W[jw(ar1, ar2, br1, 0)], Gz[g4(br, br1, 1, ar2)] * W[jw(ar1, ar2, br1, 1)]);
+    }
+}
+// transposed factor r: Gx (before the pair) from Gy
+__device__ __forceinline__ void pair_first_t(const float (&Gy)[16], const float (&W)[4], float (&Gx)[16]) {
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {   // m = (b_r, a_{r+1}, a_{r+2}, a_r)
+        const int br = m & 1, ar1 = (m >> 1) & 1, ar2 = (m >> 2) & 1, ar = m >> 3;
+        Gx[m] = fmaf(Gy[g4(br, 0, ar2, ar1)], W[jw(ar, ar1, br, 0)], Gy[g4(br, 1, ar2, ar1)] * W[jw(ar, ar1, br, 1)]);
+    }
+}
+
+// Sum of 8 (4) per-lane values over the warp, scattered: lane l returns the
+// total of slot (l >> 2) & 7 ((l >> 3) & 3).
+__device__ __forceinline__ float reduce_scatter8(float (&v)[8], int lane) {
+#pragma unroll
+    for (int h = 4; h >= 1; h >>= 1) {
+        const bool hi = (lane & (4 * h)) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float send = hi ? v[i] : v[i + h];
+            const float keep = hi ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4 * h);
+        }
+    }
+    float t = v[0] + __shfl_xor_sync(0xffffffffu, v[0], 2);
+    return t + __shfl_xor_sync(0xffffffffu, t, 1);
+}
+__device__ __forceinline__ float reduce_scatter4(float (&v)[4], int lane) {
+#pragma unroll
+    for (int h = 2; h >= 1; h >>= 1) {
+        const bool hi = (lane & (8 * h)) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float send = hi ? v[i] : v[i + h];
+            const float keep = hi ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8 * h);
+        }
+    }
+    float t = v[0] + __shfl_xor_sync(0xffffffffu, v[0], 4);
+    t += __shfl_xor_sync(0xffffffffu, t, 2);
+    return t + __shfl_xor_sync(0xffffffffu, t, 1);
 }
 
 template <int NW>
@@ -148,120 +306,15 @@ __device__ __forceinline__ float inv_pow2_of(float m, int* e) {
     return __int_as_float((127 - ex) << 23);
 }
 
-// Shared-memory offsets of the eight entries of rest `core` in the layout of
-// state index `lay`: o[k] holds the entry with bit r = k & 1, bit r+1 =
-// (k >> 1) & 1 and bit d+1 = k >> 2. phys is linear over GF(2), so the
-// offsets are one swizzled base XOR constants.
-template <int D>
-__device__ __forceinline__ void entry_offsets(int core, int r, int lay, int (&o)[8]) {
-    constexpr int PS = GradShape<D>::HALF;
-    const int base = phys<D>(core, lay);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) o[k] = base ^ phys<D>((k & 1) * (1 << r) + ((k >> 1) & 1) * (2 << r) + (k >> 2) * PS, lay);
-}
-
-// Forward factor r: F_{r+1} from F_r (the eight entries of one rest).
-//   F_{r+1}[b, b', a'] = sum_a F_r[b, a', a] w(a, a', b, b')
-template <int D>
-__device__ __forceinline__ void factor_forward(const float* __restrict__ Fr, float* __restrict__ Fn,
-                                               const float (&Wp)[4], int r, int rs) {
-    const int core = rest_core(rs, r);
-    int oi[8], oo[8];
-    entry_offsets<D>(core, r, r, oi);
-    entry_offsets<D>(core, r, r + 1, oo);
-    float x[8];   // x[b | a'<<1 | a<<2]
-#pragma unroll
-    for (int k = 0; k < 8; ++k) x[k] = Fr[oi[k]];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {   // k = b | b'<<1 | a'<<2
-        const int b = k & 1, bp = (k >> 1) & 1, ap = k >> 2;
-        const int i0 = b | (ap << 1), wk = (ap << 1) | (b << 2) | (bp << 3);
-        Fn[oo[k]] = fmaf(x[i0], Wp[jk(wk)], x[i0 | 4] * Wp[jk(wk | 1)]);
-    }
-}
-
-// Transposed factor r: G_r from G_{r+1}.
-//   G_r[b, a', a] = sum_b' G_{r+1}[b, b', a'] w(a, a', b, b')
-template <int D>
-__device__ __forceinline__ void factor_backward(const float* __restrict__ Gn, float* __restrict__ Gr,
-                                                const float (&Wp)[4], int r, int rs) {
-    const int core = rest_core(rs, r);
-    int oi[8], oo[8];
-    entry_offsets<D>(core, r, r + 1, oi);
-    entry_offsets<D>(core, r, r, oo);
-    float y[8];   // y[b | b'<<1 | a'<<2]
-#pragma unroll
-    for (int k = 0; k < 8; ++k) y[k] = Gn[oi[k]];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {   // k = b | a'<<1 | a<<2
-        const int b = k & 1, ap = (k >> 1) & 1, a = k >> 2;
-        const int i0 = b | (ap << 2), wk = a | (ap << 1) | (b << 2);
-        Gr[oo[k]] = fmaf(y[i0], Wp[jk(wk)], y[i0 | 2] * Wp[jk(wk | 8)]);
-    }
-}
-
-// Environment of factor r, accumulated per weight slot j (e[j] += sum of
-// F_r x G_{r+1} over the entries k with jk(k) = j), and, unless r is the
-// column's last factor, the forward step.
-template <int D>
-__device__ __forceinline__ void factor_environment(const float* __restrict__ Fr, const float* __restrict__ Gn,
-                                                   float* __restrict__ Fn, const float (&Wp)[4], int r,
-                                                   int rs, bool forward, float (&e)[4]) {
-    const int core = rest_core(rs, r);
-    int o0[8], o1[8];
-    entry_offsets<D>(core, r, r, o0);
-    entry_offsets<D>(core, r, r + 1, o1);
-    float x[8], y[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        x[k] = Fr[o0[k]];   // x[b | a'<<1 | a<<2]
-        y[k] = Gn[o1[k]];   // y[b | b'<<1 | a'<<2]
-    }
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        const int a = k & 1, ap = (k >> 1) & 1, b = (k >> 2) & 1, bp = (k >> 3) & 1;
-        e[jk(k)] = fmaf(x[b | (ap << 1) | (a << 2)], y[b | (bp << 1) | (ap << 2)], e[jk(k)]);
-    }
-    if (forward) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int b = k & 1, bp = (k >> 1) & 1, ap = k >> 2;
-            const int i0 = b | (ap << 1), wk = (ap << 1) | (b << 2) | (bp << 3);
-            Fn[o1[k]] = fmaf(x[i0], Wp[jk(wk)], x[i0 | 4] * Wp[jk(wk | 1)]);
-        }
-    }
-}
-
-// Sum of four per-lane values over the warp, scattered: lane l returns the
-// total of slot (l >> 3) & 3.
-__device__ __forceinline__ float reduce_scatter4(float (&v)[4], int lane) {
-    {
-        const bool hi = (lane & 16) != 0;
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const float send = hi ? v[i] : v[i + 2];
-            const float keep = hi ? v[i + 2] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-        }
-    }
-    const bool hi = (lane & 8) != 0;
-    float t = (hi ? v[1] : v[0]) + __shfl_xor_sync(0xffffffffu, hi ? v[0] : v[1], 8);
-    t += __shfl_xor_sync(0xffffffffu, t, 4);
-    t += __shfl_xor_sync(0xffffffffu, t, 2);
-    t += __shfl_xor_sync(0xffffffffu, t, 1);
-    return t;
-}
-
 template <int D>
 __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_dense_kernel(GradDenseArgs g) {
     using S = GradShape<D>;
-    constexpr int N = S::N, HALF = S::HALF, SIZE = S::SIZE, REST = S::REST, NT = S::NT, NW = S::NW;
+    constexpr int N = S::N, HALF = S::HALF, SIZE = S::SIZE, NT = S::NT, NW = S::NW;
     extern __shared__ float4 smem4[];
     float* sm = reinterpret_cast<float*>(smem4);
     float* wts = sm + S::off_w;
-    float* G = sm + S::off_g;
-    float* F0 = sm + S::off_f0;
-    float* F1 = sm + S::off_f1;
+    float* G = sm + S::off_g;              // G + gslot(r) * SIZE: the state before factor r
+    float* Fs = sm + S::off_f;
     float* Rs = sm + S::off_r;
     float* red = sm + S::off_red;
     float* env = sm + S::off_env;
@@ -270,8 +323,7 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
     double* acc = reinterpret_cast<double*>(sm + S::off_acc);
     float* Lg = g.lws + (size_t)blockIdx.x * S::lfloats;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int rs = tid;                    // this thread's rest (REST <= NT)
-    const bool owns = rs < REST;
+    const bool owns2 = tid < S::REST2;
 
     for (int e = tid; e < 4 * N; e += NT) acc[e] = 0.0;
 
@@ -305,22 +357,42 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
         }
         {
             const int pm0 = present_rows<D>(0);
-            for (int e = tid; e < SIZE; e += NT) F0[phys<D>(e, 0)] = (left_index<D>(e) & ~pm0) == 0 ? 1.f : 0.f;
+            for (int e = tid; e < SIZE; e += NT) Fs[phys<D>(e, 0)] = (left_index<D>(e) & ~pm0) == 0 ? 1.f : 0.f;
         }
         __syncthreads();
 
         // ---------------------------------------------------------------- forward
-        float* Fa = F0;
-        float* Fb = F1;
+        // the states ping-pong between Fs and G slot 0 (free until the backward pass)
         int eL = 0;
         float total = 0.f;
         bool dead = false;
         for (int c = 0; c < D; ++c) {
+            float* Fa = Fs;
+            float* Fb = G;
 #pragma unroll
-            for (int r = 0; r < D; ++r) {
-                float wr[4];
-                factor_weights<D>(wts, r, c, wr);
-                if (owns) factor_forward<D>(Fa, Fb, wr, r, rs);
+            for (int r = 0; r + 1 < D; r += 2) {
+                float W0[4], W1[4];
+                factor_weights<D>(wts, r, c, W0);
+                factor_weights<D>(wts, r + 1, c, W1);
+                if (owns2) {
+                    int oi[16], oo[16];
+                    pair_offsets<D>(tid, r, r, oi);
+                    pair_offsets<D>(tid, r, r + 2, oo);
+                    float X[16], Y[16], Z[16];
+#pragma unroll
+                    for (int m = 0; m < 16; ++m) X[m] = Fa[oi[m]];
+                    pair_first(X, W0, Y);
+                    pair_second(Y, W1, Z);
+#pragma unroll
+                    for (int m = 0; m < 16; ++m) Fb[oo[m]] = Z[m];
+                }
+                __syncthreads();
+                float* t = Fa; Fa = Fb; Fb = t;
+            }
+            {
+                float W[4];
+                factor_weights<D>(wts, D - 1, c, W);
+                for (int rs = tid; rs < S::REST1; rs += NT) single_forward<D>(Fa, Fb, W, D - 1, rs);
                 __syncthreads();
                 float* t = Fa; Fa = Fb; Fb = t;
             }
@@ -341,7 +413,7 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
             int ex = 0;
             const float s = inv_pow2_of(m, &ex);
             eL += ex;
-            for (int e = tid; e < SIZE; e += NT) Fa[phys<D>(e, 0)] = Rs[left_index<D>(e)] * s;
+            for (int e = tid; e < SIZE; e += NT) Fs[phys<D>(e, 0)] = Rs[left_index<D>(e)] * s;
             for (int bi = tid; bi < HALF; bi += NT) Lg[c * HALF + bi] = Rs[bi] * s;
             __syncthreads();
         }
@@ -358,7 +430,7 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
         for (int c = D - 1; c >= 0; --c) {
             {
                 const int pmn = present_rows<D>(c + 1);
-                float* GD = G + D * SIZE;
+                float* GD = G + gslot<D>(D) * SIZE;
                 for (int e = tid; e < SIZE; e += NT) {
                     const int bi = e & (HALF - 1);
                     GD[phys<D>(e, D)] = c == D - 1 ? ((bi & ~pmn) == 0 ? 1.f : 0.f) : Rs[bi];
@@ -366,22 +438,40 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
                 const int pm0 = present_rows<D>(0);
                 for (int e = tid; e < SIZE; e += NT) {
                     const int li = left_index<D>(e);
-                    F0[phys<D>(e, 0)] = c == 0 ? ((li & ~pm0) == 0 ? 1.f : 0.f) : Lg[(c - 1) * HALF + li];
+                    Fs[phys<D>(e, 0)] = c == 0 ? ((li & ~pm0) == 0 ? 1.f : 0.f) : Lg[(c - 1) * HALF + li];
                 }
             }
             __syncthreads();
+            {
+                float W[4];
+                factor_weights<D>(wts, D - 1, c, W);
+                for (int rs = tid; rs < S::REST1; rs += NT)
+                    single_backward<D>(G + gslot<D>(D) * SIZE, G + gslot<D>(D - 1) * SIZE, W, D - 1, rs);
+                __syncthreads();
+            }
 #pragma unroll
-            for (int r = D - 1; r >= 1; --r) {
-                float wr[4];
-                factor_weights<D>(wts, r, c, wr);
-                if (owns) factor_backward<D>(G + (r + 1) * SIZE, G + r * SIZE, wr, r, rs);
+            for (int r = D - 3; r >= 0; r -= 2) {
+                if (r == 0 && c == 0) break;       // R_0 is not needed
+                float W0[4], W1[4];
+                factor_weights<D>(wts, r, c, W0);
+                factor_weights<D>(wts, r + 1, c, W1);
+                if (owns2) {
+                    int oi[16], oo[16];
+                    pair_offsets<D>(tid, r, r + 2, oi);
+                    pair_offsets<D>(tid, r, r, oo);
+                    float Gz[16], Gy[16], Gx[16];
+                    const float* Gn = G + gslot<D>(r + 2) * SIZE;
+#pragma unroll
+                    for (int m = 0; m < 16; ++m) Gz[m] = Gn[oi[m]];
+                    pair_second_t(Gz, W1, Gy);
+                    pair_first_t(Gy, W0, Gx);
+                    float* Go = G + gslot<D>(r) * SIZE;
+#pragma unroll
+                    for (int m = 0; m < 16; ++m) Go[oo[m]] = Gx[m];
+                }
                 __syncthreads();
             }
             if (c > 0) {
-                float wr[4];
-                factor_weights<D>(wts, 0, c, wr);
-                if (owns) factor_backward<D>(G + SIZE, G, wr, 0, rs);
-                __syncthreads();
                 // R_c = sum over beta_0 of G_0, rescaled
                 const int pmc = present_rows<D>(c);
                 float tmax = 0.f;
@@ -396,18 +486,66 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
                 const float s = (m > 0.f && m < INFINITY) ? inv_pow2_of(m, &ex) : 1.f;
                 for (int ai = tid; ai < HALF; ai += NT) Rs[ai] *= s;
             }
-            // re-apply the factors from L_c with each factor's environment
-            float* Fa2 = F0;
-            float* Fb2 = F1;
+            // re-apply the factors from L_c with each factor's environment; the
+            // state after pair r goes to the slot of G_r, which pair r-2 (or
+            // the extraction of R_c) has consumed
+            const float* Fa = Fs;
 #pragma unroll
-            for (int r = 0; r < D; ++r) {
-                float wr[4], e[4] = {0.f, 0.f, 0.f, 0.f};
-                factor_weights<D>(wts, r, c, wr);
-                if (owns) factor_environment<D>(Fa2, G + (r + 1) * SIZE, Fb2, wr, r, rs, r < D - 1, e);
-                const float tot = reduce_scatter4(e, lane);
-                if ((lane & 7) == 0) red[(r * NW + warp) * 4 + (lane >> 3)] = tot;
+            for (int r = 0; r + 1 < D; r += 2) {
+                float W0[4], W1[4];
+                factor_weights<D>(wts, r, c, W0);
+                factor_weights<D>(wts, r + 1, c, W1);
+                float e[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // factor r, then factor r+1
+                float* Fb = G + gslot<D>(r) * SIZE;
+                if (owns2) {
+                    int o0[16], o2[16];
+                    pair_offsets<D>(tid, r, r, o0);
+                    pair_offsets<D>(tid, r, r + 2, o2);
+                    const float* Gn = G + gslot<D>(r + 2) * SIZE;
+                    float X[16], Gz[16], Y[16], Gy[16];
+#pragma unroll
+                    for (int m = 0; m < 16; ++m) {
+                        X[m] = Fa[o0[m]];
+                        Gz[m] = Gn[o2[m]];
+                    }
+                    pair_first(X, W0, Y);
+                    pair_second_t(Gz, W1, Gy);
+#pragma unroll
+                    for (int m = 0; m < 32; ++m) {
+                        // factor r: sum over alpha_{r+2} of X (b_r, a_{r+1}, a_{r+2}, a_r) Gy (b_r, b_{r+1}, a_{r+2}, a_{r+1})
+                        const int br = m & 1, ar1 = (m >> 1) & 1, ar2 = (m >> 2) & 1, ar = (m >> 3) & 1, br1 = m >> 4;
+                        const int j = jw(ar, ar1, br, br1);
+                        e[j] = fmaf(X[g4(br, ar1, ar2, ar)], Gy[g4(br, br1, ar2, ar1)], e[j]);
+                    }
+#pragma unroll
+                    for (int m = 0; m < 32; ++m) {
+                        // factor r+1: sum over beta_r of Y (b_r, b_{r+1}, a_{r+2}, a_{r+1}) Gz (b_r, b_{r+1}, b_{r+2}, a_{r+2})
+                        const int br = m & 1, br1 = (m >> 1) & 1, ar2 = (m >> 2) & 1, ar1 = (m >> 3) & 1, br2 = m >> 4;
+                        const int j = 4 + jw(ar1, ar2, br1, br2);
+                        e[j] = fmaf(Y[g4(br, br1, ar2, ar1)], Gz[g4(br, br1, br2, ar2)], e[j]);
+                    }
+                    if (r + 2 < D) {
+                        float Z[16];
+                        pair_second(Y, W1, Z);
+#pragma unroll
+                        for (int m = 0; m < 16; ++m) Fb[o2[m]] = Z[m];
+                    }
+                }
+                const float tot = reduce_scatter8(e, lane);
+                if ((lane & 3) == 0) {
+                    const int slot = lane >> 2;
+                    red[((r + (slot >> 2)) * NW + warp) * 4 + (slot & 3)] = tot;
+                }
                 __syncthreads();
-                float* t = Fa2; Fa2 = Fb2; Fb2 = t;
+                Fa = Fb;
+            }
+            {
+                float e[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int rs = tid; rs < S::REST1; rs += NT)
+                    single_environment<D>(Fa, G + gslot<D>(D) * SIZE, D - 1, rs, e);
+                const float tot = reduce_scatter4(e, lane);
+                if ((lane & 7) == 0) red[((D - 1) * NW + warp) * 4 + (lane >> 3)] = tot;
+                __syncthreads();
             }
             for (int t = tid; t < D * 4; t += NT) {
                 float s = 0.f;
