@@ -304,43 +304,53 @@ def run_large(args):
 
 def run_grad(args):
     """Adjoint of the sweep on the d=7 workload with per-qubit biased noise:
-    gradient of sum_b ln Pr(l_true | s_b) over 65,536 syndromes."""
+    gradient of sum_b ln Pr(l_true | s_b) over 65,536 syndromes (and the same
+    at d=9, chi=32 over 16,384 syndromes, reported as d9_value)."""
     import torch
     import paper_2605_17230_gb300 as mld
-    d, n, chi, Bg = 7, 49, 32, 65536
-    noise = synth.lognormal_biased(n, seed=3).astype(np.float32)
-    E = synth.sample_errors(d, noise, Bg, seed=4)
-    syn = synth.syndromes_of(d, E)
-    code = mld.Code(d)
-    nz = torch.tensor(noise, device="cuda")
-    sy = torch.tensor(syn.view(np.int64), device="cuda")
-    cls = torch.tensor(synth.true_class(d, E).astype(np.int64), device="cuda")
-    lp, _ = code.decode(nz, sy, chi)
-    up = torch.zeros_like(lp)
-    up.scatter_(1, cls[:, None], 1.0)
-    up -= torch.softmax(lp, dim=1)                # d/d lnZ of ln Pr(l_true|s)
-    dn = torch.zeros((n, 4), dtype=torch.float64, device="cuda")
-    for _ in range(max(1, args.warmup)):
-        mld.mld_decode_grad(code.handle, nz, sy, Bg, chi, up, None, dn)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        mld.mld_decode_grad(code.handle, nz, sy, Bg, chi, up, None, dn)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+
+    def one(d, chi, Bg):
+        n = d * d
+        noise = synth.lognormal_biased(n, seed=3).astype(np.float32)
+        E = synth.sample_errors(d, noise, Bg, seed=4)
+        syn = synth.syndromes_of(d, E)
+        code = mld.Code(d)
+        nz = torch.tensor(noise, device="cuda")
+        sy = torch.tensor(syn.view(np.int64), device="cuda")
+        cls = torch.tensor(synth.true_class(d, E).astype(np.int64), device="cuda")
+        lp, _ = code.decode(nz, sy, chi)
+        up = torch.zeros_like(lp)
+        up.scatter_(1, cls[:, None], 1.0)
+        up -= torch.softmax(lp, dim=1)                # d/d lnZ of ln Pr(l_true|s)
+        dn = torch.zeros((n, 4), dtype=torch.float64, device="cuda")
+        for _ in range(max(1, args.warmup)):
+            mld.mld_decode_grad(code.handle, nz, sy, Bg, chi, up, None, dn)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            mld.mld_decode_grad(code.handle, nz, sy, Bg, chi, up, None, dn)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        t0 = torch.cuda.Event(enable_timing=True); t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(args.steps):
+            code.decode(nz, sy, chi)
+        t1.record()
+        torch.cuda.synchronize()
+        return ms, Bg / (ms / 1e3), Bg / (t0.elapsed_time(t1) / args.steps / 1e3)
+
+    Bg = args.batch if args.batch != B else 65536
+    ms, value, fwd = one(7, 32, Bg)
     line = {"metric": "syndromes/s of the adjoint (d=7, chi=32, per-qubit biased noise)", "workload": "grad",
-            "value": Bg / (ms / 1e3), "unit": "syndromes/s", "ms_per_step": ms, "syndromes": Bg,
+            "value": value, "unit": "syndromes/s", "ms_per_step": ms, "syndromes": Bg,
             "steps": args.steps, "data": "synthetic", "dtype": "f32 contraction, f64 accumulation",
-            "forward_only_value": None}
-    t0 = torch.cuda.Event(enable_timing=True); t1 = torch.cuda.Event(enable_timing=True)
-    t0.record()
-    for _ in range(args.steps):
-        code.decode(nz, sy, chi)
-    t1.record()
-    torch.cuda.synchronize()
-    line["forward_only_value"] = Bg / (t0.elapsed_time(t1) / args.steps / 1e3)
+            "forward_only_value": fwd}
+    if args.batch == B:
+        _, v9, f9 = one(9, 32, 16384)
+        line["d9_value"] = v9
+        line["d9_forward_only_value"] = f9
     print(json.dumps(line), flush=True)
 
 
