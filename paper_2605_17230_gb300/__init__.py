@@ -12,6 +12,7 @@ Names follow the C ABI: ``mld_code_create_rotated``, ``mld_decode``,
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -21,7 +22,8 @@ from . import build as _build
 __all__ = ["MLD_OK", "MLD_FP32", "MLD_MIXED_BF16", "MLD_MIXED_TF32", "MLD_NOISE_TABLE",
            "MLD_NOISE_DEPOL", "MldError", "Code", "load", "library_path", "mld_code_create_rotated",
            "mld_decode", "mld_decode_host", "mld_decode_status", "mld_decode_launches",
-           "mld_status_string", "EXPORTED_SYMBOLS"]
+           "mld_status_string", "EXPORTED_SYMBOLS", "log_coset_probabilities", "estimate_noise",
+           "noise_table_from_logits"]
 
 MLD_OK = 0
 MLD_FP32, MLD_MIXED_BF16, MLD_MIXED_TF32 = 0, 1, 2
@@ -343,3 +345,43 @@ def log_coset_probabilities(code, noise, syndromes, chi):
     if _LogZ is None:
         _LogZ = _logz_function()
     return _LogZ.apply(noise, code, syndromes, chi)
+
+
+
+def noise_table_from_logits(z):
+    """Per-qubit Pauli table [n][4] (I, X, Y, Z) from three logits per qubit:
+    p_P = exp(z_P) / (1 + sum_P' exp(z_P')), p_I = 1 / (1 + sum_P' exp(z_P'))."""
+    import torch
+    e = torch.exp(z)
+    den = 1.0 + e.sum(dim=1, keepdim=True)
+    return torch.cat([1.0 / den, e / den], dim=1)
+
+
+def estimate_noise(code, syndromes, chi, steps=200, lr=0.08, init_rate=0.05, logits=None):
+    """Maximum-likelihood per-qubit Pauli rates from unlabelled syndromes
+    (Sec. 3.2.4, Eq. 10): minimises L = -mean_b ln sum_l Z_l(s_b), the
+    marginal likelihood of the observed syndromes, over three logits per
+    qubit with Adam. Every step is one forward sweep and one adjoint sweep
+    over the whole batch on the GPU (chi must not truncate).
+
+    syndromes: int64 CUDA tensor [B][words]. Starts from the uniform table
+    with total rate init_rate per qubit unless `logits` ([n][3], float64) is
+    given. Returns (table [n][4] float64, logits [n][3], losses [steps])."""
+    import torch
+    n = code.n
+    if logits is None:
+        z0 = math.log(init_rate / 3.0 / (1.0 - init_rate))
+        logits = torch.full((n, 3), z0, dtype=torch.float64, device=syndromes.device)
+    z = logits.detach().clone().requires_grad_(True)
+    opt = torch.optim.Adam([z], lr=lr)
+    losses = []
+    for _ in range(steps):
+        opt.zero_grad()
+        lp = log_coset_probabilities(code, noise_table_from_logits(z), syndromes, chi)
+        loss = -torch.logsumexp(lp, dim=1).mean()
+        loss.backward()
+        opt.step()
+        losses.append(loss.detach())
+    z = z.detach()
+    hist = torch.stack(losses).cpu().numpy() if losses else np.zeros(0)
+    return noise_table_from_logits(z), z, hist
