@@ -8,7 +8,9 @@ it and the two share no code (only ``synth`` feeds both the same inputs).
 evaluated by variable elimination), brute force over all Paulis, stabiliser
 group enumeration and the derivative contractions. ``mps.py`` holds the
 boundary-MPS method of Sec. 3.2.1 in FP64 with numpy's QR and SVD, used to
-check truncated bond dimensions.
+check truncated bond dimensions. ``dem_qubit_table`` and
+``dem_bruteforce_table`` state what the detector picture (Sec. 3.2.2)
+computes for a code-capacity error-mechanism model.
 """
 from __future__ import annotations
 
@@ -187,3 +189,60 @@ def syndrome_index(bits: np.ndarray) -> np.ndarray:
     """Integer index of syndrome bit rows (bit k -> 2^k), for small codes."""
     bits = np.asarray(bits, dtype=np.uint64)
     return (bits << np.arange(bits.shape[-1], dtype=np.uint64)).sum(axis=-1)
+
+
+# --------------------------------------------------------------------------
+# Code-capacity detector error models (the detector picture, Sec. 3.2.2).
+# A model is a list of independent error mechanisms m: Pauli pauli[m]
+# (code x + 2z: 1 = X, 2 = Z, 3 = Y) on qubit qubit[m], present with
+# probability p[m]. These functions state what the detector-picture network
+# contracts to; neither builds that network.
+
+_CODE_TO_ROW = (0, 1, 3, 2)        # Pauli code x + 2z -> noise-row index (I, X, Y, Z)
+
+
+def dem_qubit_table(d: int, qubit, pauli, p) -> np.ndarray:
+    """Per-qubit Pauli table [n][4] (I, X, Y, Z) of a mechanism list: the
+    mechanisms on one qubit are independent and compose by Pauli product
+    (XOR of the codes), so the qubit's Pauli is distributed as the product
+    of independent factors (1 - p_m) I + p_m P_m; mechanisms on different
+    qubits are independent, so Pr(E) is the product of the rows."""
+    n = d * d
+    dist = np.zeros((n, 4), np.float64)            # indexed by Pauli code
+    dist[:, 0] = 1.0
+    for q, c, pm in zip(np.asarray(qubit, np.int64), np.asarray(pauli, np.int64), np.asarray(p, np.float64)):
+        if not (0 <= q < n and 1 <= c <= 3 and 0.0 <= pm <= 1.0):
+            raise ValueError(f"bad mechanism ({q}, {c}, {pm})")
+        old = dist[q].copy()
+        for code in range(4):
+            dist[q, code] = (1.0 - pm) * old[code] + pm * old[code ^ c]
+    tab = np.zeros((n, 4), np.float64)
+    for code in range(4):
+        tab[:, _CODE_TO_ROW[code]] = dist[:, code]
+    return tab
+
+
+def dem_bruteforce_table(d: int, qubit, pauli, p, chunk: int = 1 << 16) -> np.ndarray:
+    """Z[s][l] over all 2^m syndromes of a mechanism list, by its definition:
+    the sum over all 2^M configurations b of the mechanisms of
+    prod_m p_m^{b_m} (1 - p_m)^{1 - b_m}, each configuration filed under the
+    syndrome and logical class of the Pauli it produces (Eq. 3 read in the
+    detector picture of Sec. 3.2.2). Small models only (M <= 22)."""
+    n, m, _ = code_info(d)
+    qubit = np.asarray(qubit, np.int64)
+    pauli = np.asarray(pauli, np.uint8)
+    p = np.asarray(p, np.float64)
+    M = len(p)
+    if M > 22:
+        raise ValueError("too many mechanisms for enumeration")
+    Z = np.zeros((1 << m, 4), np.float64)
+    for lo in range(0, 1 << M, chunk):
+        b = ((np.arange(lo, min(lo + chunk, 1 << M), dtype=np.int64)[:, None] >> np.arange(M)) & 1).astype(bool)
+        E = np.zeros((b.shape[0], n), np.uint8)
+        w = np.ones(b.shape[0], np.float64)
+        for k in range(M):
+            E[b[:, k], qubit[k]] ^= pauli[k]
+            w *= np.where(b[:, k], p[k], 1.0 - p[k])
+        bits, cls = syndrome_class(d, E)
+        np.add.at(Z, (syndrome_index(bits).astype(np.int64), cls.astype(np.int64)), w)
+    return Z

@@ -329,3 +329,60 @@ def test_golden_d5_group_enumeration():
     ref = np.array([[float(v) for v in r[1:5]] for r in rows])
     logP, _ = oracle.decode(5, synth.depolarizing(25, 0.12), syn)
     np.testing.assert_allclose(logP, ref, rtol=0, atol=1e-11)
+
+
+# ---------------------------------------------------------------- detector error models (Sec. 3.2.2)
+
+def test_dem_qubit_table_closed_forms():
+    """Closed forms of composing independent mechanisms on one qubit."""
+    d, n = 3, 9
+    # one X mechanism: (1 - p, p, 0, 0)
+    t = oracle.dem_qubit_table(d, [4], [1], [0.2])
+    np.testing.assert_allclose(t[4], [0.8, 0.2, 0.0, 0.0], atol=1e-15)
+    np.testing.assert_allclose(t[0], [1.0, 0.0, 0.0, 0.0], atol=0)
+    # independent X and Z (code capacity with independent flips): product form
+    px, pz = 0.11, 0.07
+    t = oracle.dem_qubit_table(d, [2, 2], [1, 2], [px, pz])
+    np.testing.assert_allclose(t[2], [(1 - px) * (1 - pz), px * (1 - pz), px * pz, (1 - px) * pz], atol=1e-15)
+    # two X mechanisms: odd number fires
+    t = oracle.dem_qubit_table(d, [1, 1], [1, 1], [0.1, 0.3])
+    np.testing.assert_allclose(t[1], [0.9 * 0.7 + 0.1 * 0.3, 0.1 * 0.7 + 0.9 * 0.3, 0, 0], atol=1e-15)
+    # X, Y, Z mechanisms: enumerate the eight on/off patterns by hand
+    ps = (0.05, 0.02, 0.08)
+    t = oracle.dem_qubit_table(d, [7, 7, 7], [1, 3, 2], ps)
+    want = np.zeros(4)
+    for bx in (0, 1):
+        for by in (0, 1):
+            for bz in (0, 1):
+                w = (ps[0] if bx else 1 - ps[0]) * (ps[1] if by else 1 - ps[1]) * (ps[2] if bz else 1 - ps[2])
+                x = bx ^ by
+                z = bz ^ by
+                want[{(0, 0): 0, (1, 0): 1, (1, 1): 2, (0, 1): 3}[(x, z)]] += w
+    np.testing.assert_allclose(t[7], want, atol=1e-15)
+    assert abs(t.sum(axis=1) - 1).max() < 1e-15
+    with pytest.raises(ValueError):
+        oracle.dem_qubit_table(d, [n], [1], [0.1])
+    with pytest.raises(ValueError):
+        oracle.dem_qubit_table(d, [0], [0], [0.1])
+
+
+def test_dem_definition_equals_generator_picture():
+    """Summing over mechanism configurations (the detector picture's sum)
+    equals the generator picture's coset sums with the composed per-qubit
+    table, for every syndrome and class: by brute force over all 4^n Paulis
+    and by the dense variable-elimination contraction."""
+    d = 3
+    rng = np.random.default_rng(5)
+    q = np.repeat(np.arange(9), 2)
+    pauli = rng.integers(1, 4, q.size)
+    p = rng.uniform(0.01, 0.3, q.size)
+    Zd = oracle.dem_bruteforce_table(d, q, pauli, p)
+    tab = oracle.dem_qubit_table(d, q, pauli, p)
+    Zg = oracle.bruteforce_table(d, tab)
+    assert abs(Zd.sum() - 1.0) < 1e-12
+    np.testing.assert_allclose(Zd, Zg, rtol=1e-12, atol=1e-300)
+    m = 8
+    bits = ((np.arange(1 << m)[:, None] >> np.arange(m)) & 1).astype(np.uint8)
+    syn = np.array([synth.pack_bits(b[None])[0] for b in bits])
+    lp, _ = oracle.decode(d, tab, syn)
+    np.testing.assert_allclose(lp, np.log(Zd), rtol=0, atol=1e-11)
