@@ -229,6 +229,33 @@ mld_status mld_decode_status(const mld_code* code);
  * SVD work, which depends on the data, is not included. Host only. */
 mld_status mld_decode_flops(const mld_code* code, int chi, int precision, double* flops_per_syndrome);
 
+/* Detector-picture MLD of a code-capacity detector error model (Sec. 3.2.2:
+ * the network of error-mechanism tensors diag(1-p, p), one parity tensor
+ * delta(XOR of incident bits = s_j) per detector and the logical parity
+ * tensors, contracted without reference to a stabiliser coset).
+ * The model is n_mech independent mechanisms; mechanism m applies Pauli
+ * mech_pauli[m] (code x + 2z: 1 = X, 2 = Z, 3 = Y) to qubit mech_qubit[m]
+ * (index r*d + c) with probability mech_p[m]. These three are HOST arrays,
+ * read before the call returns. Z_l(s) sums the probability of every
+ * mechanism configuration whose syndrome is s and whose logical parities
+ * (x-parity on Z_L's support, row 0; z-parity on X_L's support, column 0)
+ * equal those of the class-l representative, l = l_X + 2 l_Z as in
+ * mld_decode; the result equals mld_decode with each qubit's table the
+ * distribution of the product of its mechanisms.
+ *   syndromes  device uint64[B][words]
+ *   logP       device double[B][4]: ln Z_l(s) (-inf for an impossible class)
+ *   argmax     device uint8[B] or NULL (ties -> lowest class)
+ * The contraction is exact: one thread block per syndrome keeps the dense
+ * boundary state over the open detectors' partial parities and both
+ * logical parities, all four classes in one sweep; FP32 with power-of-two
+ * rescaling per column, ln Z in FP64. d <= 9 (MLD_ERR_UNSUPPORTED
+ * otherwise); MLD_ERR_INVALID_ARG for a mechanism with a qubit outside
+ * [0, n), a code outside 1..3 or p outside [0, 1]. Asynchronous on stream;
+ * no device allocation. */
+mld_status mld_decode_dem(const mld_code* code, const int32_t* mech_qubit, const int32_t* mech_pauli,
+                          const double* mech_p, int32_t n_mech, const uint64_t* syndromes, int64_t B,
+                          double* logP, uint8_t* argmax, void* stream);
+
 /* Number of kernel launches one mld_decode call makes (for accounting). */
 int mld_decode_launches(void);
 

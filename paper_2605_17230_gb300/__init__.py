@@ -34,7 +34,7 @@ EXPORTED_SYMBOLS = ["mld_code_create_rotated", "mld_code_destroy", "mld_code_inf
                     "mld_decode", "mld_decode_host", "mld_decode_status", "mld_decode_launches",
                     "mld_decode_flops", "mld_decode_noalloc", "mld_decode_batch", "mld_graph_create",
                     "mld_graph_launch", "mld_graph_destroy", "mld_autotune", "mld_decode_grad",
-                    "mld_status_string"]
+                    "mld_decode_dem", "mld_status_string"]
 
 _lib = None
 
@@ -100,6 +100,8 @@ def load(build_if_missing: bool = True):
     lib.mld_autotune.restype = I
     lib.mld_decode_grad.argtypes = [P, P, P, L, I, P, P, P, P]
     lib.mld_decode_grad.restype = I
+    lib.mld_decode_dem.argtypes = [P, P, P, P, I, P, L, P, P, P]
+    lib.mld_decode_dem.restype = I
     lib.mld_decode_launches.argtypes = []
     lib.mld_decode_launches.restype = I
     lib.mld_status_string.argtypes = [I]
@@ -232,6 +234,18 @@ class Code:
         mld_decode_host(self.handle, noise, mode, syn, B, chi, precision, logP, am)
         return logP, am
 
+    def decode_dem(self, mech_qubit, mech_pauli, mech_p, syndromes, with_argmax=True, stream=None):
+        """Detector-picture decode of a code-capacity mechanism list (numpy or
+        sequences: qubit index, Pauli code x + 2z, probability) for syndromes
+        on the GPU. Returns (logP float64 [B][4], argmax uint8 [B] or None)."""
+        import torch
+        B = syndromes.shape[0]
+        dev = syndromes.device
+        logP = torch.empty((B, 4), dtype=torch.float64, device=dev)
+        am = torch.empty((B,), dtype=torch.uint8, device=dev) if with_argmax else None
+        mld_decode_dem(self.handle, mech_qubit, mech_pauli, mech_p, syndromes.contiguous(), B, logP, am, stream)
+        return logP, am
+
     def flops(self, chi, precision=MLD_FP32) -> float:
         """Counted flops per syndrome (four classes) of the executed schedule."""
         v = ctypes.c_double()
@@ -307,6 +321,22 @@ def mld_decode_grad(code, noise, syndromes, B, chi, dlogP, logP, dnoise, stream=
     _check(load().mld_decode_grad(ctypes.c_void_p(code), _ptr(noise), _ptr(syndromes), int(B), int(chi),
                                   _ptr(dlogP), _ptr(logP), _ptr(dnoise), ctypes.c_void_p(int(stream))),
            "mld_decode_grad")
+
+
+def mld_decode_dem(code, mech_qubit, mech_pauli, mech_p, syndromes, B, logP, argmax=None, stream=None):
+    """C-ABI mld_decode_dem: mechanism arrays on the host, syndromes and outputs
+    torch CUDA tensors."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    q = np.ascontiguousarray(mech_qubit, dtype=np.int32)
+    c = np.ascontiguousarray(mech_pauli, dtype=np.int32)
+    p = np.ascontiguousarray(mech_p, dtype=np.float64)
+    if not (q.shape == c.shape == p.shape and q.ndim == 1):
+        raise ValueError("mechanism arrays must be 1-D and of one length")
+    f = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check(load().mld_decode_dem(ctypes.c_void_p(code), f(q), f(c), f(p), int(q.size), _ptr(syndromes), int(B),
+                                 _ptr(logP), _ptr(argmax), ctypes.c_void_p(int(stream))), "mld_decode_dem")
 
 
 def _logz_function():

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "mld_exact.h"
+#include "mld_dem.h"
 #include "mld_grad.h"
 #include "mld_internal.h"
 
@@ -988,6 +989,13 @@ const mld_code::PlanDev* get_plan(mld_code* C, int chi, mld_status* st) {
 }
 
 }  // namespace
+
+namespace mld {
+mld_status ensure_code_device(mld_code* C) {
+    std::lock_guard<std::mutex> lock(g_plan_mutex);
+    return ensure_device(C);
+}
+}  // namespace mld
 
 extern "C" {
 
