@@ -157,6 +157,34 @@ def per_syndrome_depolarizing(B: int, seed: int, lo: float, hi: float) -> np.nda
     return lo + (hi - lo) * u
 
 
+def mechanism_model(d: int, seed: int, median: float = 0.03, sigma: float = 0.5):
+    """Code-capacity error-mechanism list: an X, a Y and a Z mechanism on every
+    qubit (index r*d + c; Pauli code x + 2z: X = 1, Y = 3, Z = 2), each with
+    probability median*exp(sigma*N(0,1)) clipped to [1e-4, 0.3]. Normals by
+    Box-Muller from the counter generator (counters b = 3 and 4, q = mechanism).
+    Returns (qubit int32 [3n], pauli int32 [3n], p float64 [3n])."""
+    n = d * d
+    m = np.arange(3 * n, dtype=np.uint64)
+    u1 = uniforms(seed, 3, m)
+    u2 = uniforms(seed, 4, m)
+    g = np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)
+    p = np.clip(median * np.exp(sigma * g), 1e-4, 0.3)
+    return (np.repeat(np.arange(n), 3).astype(np.int32), np.tile(np.array([1, 3, 2], np.int32), n), p)
+
+
+def sample_mechanisms(d: int, qubit, pauli, p, B: int, seed: int, b0: int = 0) -> np.ndarray:
+    """Errors E [B][n] (Pauli codes x + 2z) drawn from a mechanism list:
+    mechanism m fires in sample b when uniforms(seed, b0 + b, m) < p_m, and the
+    fired mechanisms' Paulis multiply (codes XOR) on their qubits."""
+    n = d * d
+    E = np.zeros((B, n), dtype=np.uint8)
+    bs = np.arange(b0, b0 + B, dtype=np.uint64)
+    for m, (q, c, pm) in enumerate(zip(qubit, pauli, p)):
+        fire = uniforms(seed, bs, np.uint64(m)) < pm
+        E[fire, int(q)] ^= np.uint8(c)
+    return E
+
+
 # -------------------------------------------------------------- sampling ---
 
 _PAPER_TO_CODE = np.array([0, 1, 3, 2], dtype=np.uint8)   # I, X, Y, Z -> x + 2z

@@ -386,3 +386,17 @@ def test_dem_definition_equals_generator_picture():
     syn = np.array([synth.pack_bits(b[None])[0] for b in bits])
     lp, _ = oracle.decode(d, tab, syn)
     np.testing.assert_allclose(lp, np.log(Zd), rtol=0, atol=1e-11)
+
+
+def test_mechanism_sampler_matches_composed_table():
+    """The seeded mechanism sampler's per-qubit Pauli frequencies agree with
+    the oracle's composition of the same mechanisms (within 5 sigma)."""
+    d, B = 3, 200000
+    q, c, p = synth.mechanism_model(d, seed=11, median=0.08)
+    E = synth.sample_mechanisms(d, q, c, p, B, seed=12)
+    tab = oracle.dem_qubit_table(d, q, c, p)
+    code_to_row = np.array([0, 1, 3, 2])
+    for qq in range(d * d):
+        f = np.bincount(code_to_row[E[:, qq]], minlength=4) / B
+        sig = np.sqrt(tab[qq] * (1 - tab[qq]) / B)
+        assert (np.abs(f - tab[qq]) <= 5 * sig + 1e-12).all(), (qq, f, tab[qq])
