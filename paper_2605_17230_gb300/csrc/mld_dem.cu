@@ -82,91 +82,183 @@ __host__ __device__ constexpr int dem_face_bit(int d, int i, int j, int e) {
     return !dem_face_present(d, i, j) ? 0 : (((i + j) & 1) == 0 ? (e >> 1) & 1 : e & 1);
 }
 
-// Shared-memory position of entry e of the state before qubit row lay
-// (d >= 7): bits 5 and 6 XORed into the bank bits so that the 32 lanes of a
-// warp, which own 32 consecutive rests (the five lowest bits outside the
-// touched positions lay-1, lay, lay+1, d+1 and the observables), hit 32
-// banks both in the step that writes the state and in the one that reads it.
-__device__ __forceinline__ constexpr int dem_swz(int lay, int bit) {
+// Shared-memory position of entry e of a stored state (d >= 7). The 32 lanes
+// of a warp own 32 consecutive rests, i.e. vary the five lowest index bits
+// that the step leaves fixed; a step that touches bank bits (0..4) would put
+// the warp on 4 to 16 banks, so bits 5..7 are XORed into the bank bits with
+// masks chosen per stored state such that the lane -> bank map is a
+// bijection for the step writing the state and the step reading it.
+// Column 0 runs single qubit steps (touching r, r+1, d+1; states before
+// every row r stored); the other columns run pairs of rows (touching r, r+1,
+// r+2, d+1; states before even rows stored) and a single last row.
+__device__ __forceinline__ constexpr int swz_single(int lay, int bit) {
     return bit == 5 ? (lay == 0 ? 1 : lay == 1 ? 5 : lay == 2 ? 10 : lay == 3 ? 20 : lay == 4 ? 8 : 0)
-                    : (lay <= 1 ? 2 : lay == 2 ? 4 : lay == 3 ? 8 : lay <= 5 ? 16 : 0);
+         : bit == 6 ? (lay <= 1 ? 2 : lay == 2 ? 4 : lay == 3 ? 8 : lay <= 5 ? 16 : 0)
+                    : 0;
 }
-template <int D>
+__device__ __forceinline__ constexpr int swz_pair(int lay, int bit) {
+    return bit == 5 ? (lay == 0 ? 1 : lay == 2 ? 9 : lay == 4 ? 4 : 0)
+         : bit == 6 ? (lay == 0 ? 2 : lay == 2 ? 18 : lay == 4 ? 8 : 0)
+                    : (lay == 0 || lay == 2 ? 4 : lay == 4 || lay == 6 ? 16 : 0);
+}
+template <int D, bool PAIR>
 __device__ __forceinline__ int dem_phys(int e, int lay) {
     if (D < 7) return e;
-    return e ^ (((e >> 5) & 1) ? dem_swz(lay, 5) : 0) ^ (((e >> 6) & 1) ? dem_swz(lay, 6) : 0);
+    const int m5 = PAIR ? swz_pair(lay, 5) : swz_single(lay, 5);
+    const int m6 = PAIR ? swz_pair(lay, 6) : swz_single(lay, 6);
+    const int m7 = PAIR ? swz_pair(lay, 7) : swz_single(lay, 7);
+    return e ^ (((e >> 5) & 1) ? m5 : 0) ^ (((e >> 6) & 1) ? m6 : 0) ^ (((e >> 7) & 1) ? m7 : 0);
 }
 
 // Insert a zero bit at position p (positions must be inserted in ascending order).
 __device__ __forceinline__ constexpr int insert_zero(int x, int p) { return (x & ((1 << p) - 1)) | ((x >> p) << (p + 1)); }
+__device__ __forceinline__ constexpr int lbit(int l) { return l >= 0 ? 1 << l : 0; }
 
-// Qubit (R, c) of a column of kind KIND: 0 = column 0, 1 = interior even,
-// 2 = interior odd, 3 = column d-1. Face presence and types depend only on
-// the kind, so every bit pattern below is a compile-time constant; CR is a
-// column of the same kind.
-template <int D, int KIND, int R>
-__device__ __forceinline__ void dem_qubit_step(const float* __restrict__ Fin, float* __restrict__ Fout,
-                                               const float (&w)[4], int sr, int tid) {
+// Qubit (R, c) on entries held in registers. Local bit LA holds g_R, LB
+// f_{R+1}, LS the spare f_R, LOX / LOZ the observables (-1 if the qubit does
+// not feed them); other local bits pass through. Afterwards LA holds g_R,
+// LB g_{R+1} and LS f_{R+1}. CR is a column of the same kind as c (face
+// presence and types are compile-time); sr is the syndrome bit of face (R, c).
+template <int D, int CR, int R, int NE, int LA, int LB, int LS, int LOX, int LOZ>
+__device__ __forceinline__ void qubit_apply(const float (&in)[NE], float (&out)[NE], const float (&w)[4], int sr) {
+    constexpr int MS = 1 << LS;
+    constexpr int MASK = lbit(LA) | lbit(LB) | MS | lbit(LOX) | lbit(LOZ);
+    // the delta on f_R: the input's spare bit must be sr ^ bit(e);
+    // v1[li] / v0[li] is the entry (spare bit of li clear) whose spare bit is sr ^ 1 / sr
+    float v0[NE], v1[NE];
+#pragma unroll
+    for (int li = 0; li < NE; ++li) {
+        if (li & MS) continue;
+        v0[li] = sr ? in[li | MS] : in[li];
+        v1[li] = sr ? in[li] : in[li | MS];
+    }
+#pragma unroll
+    for (int lo = 0; lo < NE; ++lo) {
+        const int gr = (lo >> LA) & 1, gr1 = (lo >> LB) & 1, fr1 = (lo >> LS) & 1;
+        const int ox = LOX >= 0 ? (lo >> (LOX >= 0 ? LOX : 0)) & 1 : 0;
+        const int oz = LOZ >= 0 ? (lo >> (LOZ >= 0 ? LOZ : 0)) & 1 : 0;
+        const int base = lo & ~MASK;
+        float acc = 0.f;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (dem_face_bit(D, R + 1, CR + 1, e) != gr1) continue;        // g_{R+1} starts at bit(e)
+            const int src = base | ((gr ^ dem_face_bit(D, R, CR + 1, e)) << LA) |     // g_R
+                            ((fr1 ^ dem_face_bit(D, R + 1, CR, e)) << LB) |            // f_{R+1}
+                            (LOX >= 0 ? (ox ^ (e & 1)) << (LOX >= 0 ? LOX : 0) : 0) |
+                            (LOZ >= 0 ? (oz ^ (e >> 1)) << (LOZ >= 0 ? LOZ : 0) : 0);
+            acc = fmaf(w[e], dem_face_bit(D, R, CR, e) ? v1[src] : v0[src], acc);
+        }
+        out[lo] = acc;
+    }
+}
+
+template <int KIND>
+__device__ __forceinline__ constexpr int kind_column(int d) { return KIND == 0 ? 0 : KIND == 1 ? 2 : KIND == 2 ? 1 : d - 1; }
+
+// Single qubit step R of a column of kind KIND (0 = column 0, 1 = interior
+// even, 2 = interior odd, 3 = column d-1): local bits 0 = position R,
+// 1 = R+1, 2 = spare, then the observables the qubit feeds.
+template <int D, int KIND, int R, bool PAIR>
+__device__ __forceinline__ void dem_single(const float* __restrict__ Fin, float* __restrict__ Fout,
+                                           const float (&w)[4], int sr, int tid) {
     using S = DemShape<D>;
-    constexpr int CR = KIND == 0 ? 0 : KIND == 1 ? 2 : KIND == 2 ? 1 : D - 1;
-    constexpr bool OX = R == 0;            // row 0: x-bits feed the Z_L observable
-    constexpr bool OZ = KIND == 0;         // column 0: z-bits feed the X_L observable
+    constexpr int CR = kind_column<KIND>(D);
+    constexpr bool OX = R == 0, OZ = KIND == 0;
     constexpr int T = 3 + (OX ? 1 : 0) + (OZ ? 1 : 0), NE = 1 << T;
     constexpr int REST = S::SIZE >> T;
-    // local index bits: 0 -> position R, 1 -> R+1, 2 -> spare, then OX, then OZ
-    constexpr int POS3 = OX ? S::OXP : S::OZP;
+    constexpr int L3 = OX ? 3 : -1, L4 = OZ ? (OX ? 4 : 3) : -1;
     for (int rs = tid; rs < REST; rs += S::NT) {
         int core = insert_zero(insert_zero(insert_zero(rs, R), R + 1), S::SP);
-        if (T >= 4) core = insert_zero(core, POS3);
-        if (T >= 5) core = insert_zero(core, S::OZP);
-        const int bin = dem_phys<D>(core, R), bout = dem_phys<D>(core, R + 1);
-        float in[NE];
+        if (OX) core = insert_zero(core, S::OXP);
+        if (OZ) core = insert_zero(core, S::OZP);
+        const int bin = dem_phys<D, PAIR>(core, R), bout = dem_phys<D, PAIR>(core, R + 1);
+        float in[NE], out[NE];
 #pragma unroll
         for (int li = 0; li < NE; ++li) {
             const int off = ((li & 1) << R) | (((li >> 1) & 1) << (R + 1)) | (((li >> 2) & 1) << S::SP) |
-                            (T >= 4 ? ((li >> 3) & 1) << POS3 : 0) | (T >= 5 ? ((li >> 4) & 1) << S::OZP : 0);
-            in[li] = Fin[bin ^ dem_phys<D>(off, R)];
+                            (OX ? ((li >> 3) & 1) << S::OXP : 0) | (OZ ? ((li >> (OX ? 4 : 3)) & 1) << S::OZP : 0);
+            in[li] = Fin[bin ^ dem_phys<D, PAIR>(off, R)];
         }
-        // the delta on f_R: the input's spare bit must be s(R, c) ^ bit(e);
-        // v[li with the spare bit cleared][b] is the entry whose spare bit is sr ^ b
-        float v[NE][2];
-#pragma unroll
-        for (int li = 0; li < NE; ++li) {
-            if (li & 4) continue;
-            v[li][0] = sr ? in[li | 4] : in[li];
-            v[li][1] = sr ? in[li] : in[li | 4];
-        }
+        qubit_apply<D, CR, R, NE, 0, 1, 2, L3, L4>(in, out, w, sr);
 #pragma unroll
         for (int lo = 0; lo < NE; ++lo) {
-            const int gr = lo & 1, gr1 = (lo >> 1) & 1, fr1 = (lo >> 2) & 1;
-            const int ox = OX ? (lo >> 3) & 1 : 0, oz = OZ ? (lo >> (OX ? 4 : 3)) & 1 : 0;
-            float acc = 0.f;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                if (dem_face_bit(D, R + 1, CR + 1, e) != gr1) continue;        // g_{R+1} starts at bit(e)
-                const int src = (gr ^ dem_face_bit(D, R, CR + 1, e)) |            // g_R
-                                ((fr1 ^ dem_face_bit(D, R + 1, CR, e)) << 1) |     // f_{R+1}
-                                (OX ? ((ox ^ (e & 1)) << 3) : 0) |
-                                (OZ ? ((oz ^ (e >> 1)) << (OX ? 4 : 3)) : 0);
-                acc = fmaf(w[e], v[src][dem_face_bit(D, R, CR, e)], acc);
-            }
             const int off = ((lo & 1) << R) | (((lo >> 1) & 1) << (R + 1)) | (((lo >> 2) & 1) << S::SP) |
-                            (T >= 4 ? ((lo >> 3) & 1) << POS3 : 0) | (T >= 5 ? ((lo >> 4) & 1) << S::OZP : 0);
-            Fout[bout ^ dem_phys<D>(off, R + 1)] = acc;
+                            (OX ? ((lo >> 3) & 1) << S::OXP : 0) | (OZ ? ((lo >> (OX ? 4 : 3)) & 1) << S::OZP : 0);
+            Fout[bout ^ dem_phys<D, PAIR>(off, R + 1)] = out[lo];
         }
     }
 }
 
+// Qubits R and R+1 (R even) of a column of kind 1..3 in one pass: local
+// bits 0 = position R, 1 = R+1, 2 = R+2, 3 = spare, 4 = the Z_L observable
+// (row 0 only).
+template <int D, int KIND, int R>
+__device__ __forceinline__ void dem_pair(const float* __restrict__ Fin, float* __restrict__ Fout, const float (&w0)[4],
+                                         const float (&w1)[4], int s0, int s1, int tid) {
+    using S = DemShape<D>;
+    constexpr int CR = kind_column<KIND>(D);
+    constexpr bool OX = R == 0;
+    constexpr int T = 4 + (OX ? 1 : 0), NE = 1 << T;
+    constexpr int REST = S::SIZE >> T;
+    for (int rs = tid; rs < REST; rs += S::NT) {
+        int core = insert_zero(insert_zero(insert_zero(insert_zero(rs, R), R + 1), R + 2), S::SP);
+        if (OX) core = insert_zero(core, S::OXP);
+        const int bin = dem_phys<D, true>(core, R), bout = dem_phys<D, true>(core, R + 2);
+        float in[NE], mid[NE], out[NE];
+#pragma unroll
+        for (int li = 0; li < NE; ++li) {
+            const int off = ((li & 1) << R) | (((li >> 1) & 1) << (R + 1)) | (((li >> 2) & 1) << (R + 2)) |
+                            (((li >> 3) & 1) << S::SP) | (OX ? ((li >> 4) & 1) << S::OXP : 0);
+            in[li] = Fin[bin ^ dem_phys<D, true>(off, R)];
+        }
+        qubit_apply<D, CR, R, NE, 0, 1, 3, OX ? 4 : -1, -1>(in, mid, w0, s0);
+        qubit_apply<D, CR, R + 1, NE, 1, 2, 3, -1, -1>(mid, out, w1, s1);
+#pragma unroll
+        for (int lo = 0; lo < NE; ++lo) {
+            const int off = ((lo & 1) << R) | (((lo >> 1) & 1) << (R + 1)) | (((lo >> 2) & 1) << (R + 2)) |
+                            (((lo >> 3) & 1) << S::SP) | (OX ? ((lo >> 4) & 1) << S::OXP : 0);
+            Fout[bout ^ dem_phys<D, true>(off, R + 2)] = out[lo];
+        }
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void qubit_weights(const DemParams& prm, int r, int c, float (&w)[4]) {
+    const float* pq = prm.P[r * D + c];
+    w[0] = pq[0]; w[1] = pq[1]; w[2] = pq[2]; w[3] = pq[3];
+}
+
+// Column 0: single steps for every row.
+template <int D, int R>
+__device__ __forceinline__ void dem_column0(float*& Fa, float*& Fb, const DemParams& prm, const int* sf, int tid) {
+    if constexpr (R < D) {
+        float w[4];
+        qubit_weights<D>(prm, R, 0, w);
+        dem_single<D, 0, R, false>(Fa, Fb, w, sf[R], tid);
+        __syncthreads();
+        float* t = Fa; Fa = Fb; Fb = t;
+        dem_column0<D, R + 1>(Fa, Fb, prm, sf, tid);
+    }
+}
+
+// Columns 1..d-1: pairs of rows, then the last row alone.
 template <int D, int KIND, int R>
 __device__ __forceinline__ void dem_column(float*& Fa, float*& Fb, const DemParams& prm, const int* sf, int c,
                                            int tid) {
-    if constexpr (R < D) {
-        const float* pq = prm.P[R * D + c];
-        const float w[4] = {pq[0], pq[1], pq[2], pq[3]};
-        dem_qubit_step<D, KIND, R>(Fa, Fb, w, sf[c * (D + 1) + R], tid);
+    if constexpr (R + 1 < D) {
+        float w0[4], w1[4];
+        qubit_weights<D>(prm, R, c, w0);
+        qubit_weights<D>(prm, R + 1, c, w1);
+        dem_pair<D, KIND, R>(Fa, Fb, w0, w1, sf[c * (D + 1) + R], sf[c * (D + 1) + R + 1], tid);
         __syncthreads();
         float* t = Fa; Fa = Fb; Fb = t;
-        dem_column<D, KIND, R + 1>(Fa, Fb, prm, sf, c, tid);
+        dem_column<D, KIND, R + 2>(Fa, Fb, prm, sf, c, tid);
+    } else if constexpr (R < D) {
+        float w[4];
+        qubit_weights<D>(prm, R, c, w);
+        dem_single<D, KIND, R, true>(Fa, Fb, w, sf[c * (D + 1) + R], tid);
+        __syncthreads();
+        float* t = Fa; Fa = Fb; Fb = t;
     }
 }
 
@@ -217,7 +309,7 @@ __global__ void __launch_bounds__(DemShape<D>::NT, DemShape<D>::MINB) dem_dense_
         // column 0 starts with every parity 0
         for (int e = tid; e < SIZE; e += NT) F0[e] = 0.f;
         __syncthreads();
-        if (tid == 0) F0[dem_phys<D>(0, 0)] = 1.f;
+        if (tid == 0) F0[0] = 1.f;                       // entry 0 sits at 0 in every layout
         __syncthreads();
 
         float* Fa = F0;
@@ -225,7 +317,7 @@ __global__ void __launch_bounds__(DemShape<D>::NT, DemShape<D>::MINB) dem_dense_
         int eL = 0;
         bool dead = false;
         for (int c = 0; c < D; ++c) {
-            if (c == 0) dem_column<D, 0, 0>(Fa, Fb, prm, sf, c, tid);
+            if (c == 0) dem_column0<D, 0>(Fa, Fb, prm, sf, tid);
             else if (c == D - 1) dem_column<D, 3, 0>(Fa, Fb, prm, sf, c, tid);
             else if (c & 1) dem_column<D, 2, 0>(Fa, Fb, prm, sf, c, tid);
             else dem_column<D, 1, 0>(Fa, Fb, prm, sf, c, tid);
@@ -238,9 +330,9 @@ __global__ void __launch_bounds__(DemShape<D>::NT, DemShape<D>::MINB) dem_dense_
                 float v = 0.f;
                 if (!(e & 1)) {
                     const int old = (e & (HALF - 1) & ~1) | ((e >> S::SP) & 1) | (sD << S::SP) | (e & (3 << S::OXP));
-                    v = Fa[dem_phys<D>(old, D)];
+                    v = Fa[dem_phys<D, true>(old, D)];             // layout d is the plain one
                 }
-                Fb[dem_phys<D>(e, 0)] = v;
+                Fb[dem_phys<D, true>(e, 0)] = v;
                 tmax = fmaxf(tmax, v);
             }
             const float m = dem_block_max<NW>(tmax, misc, tid);
@@ -250,7 +342,7 @@ __global__ void __launch_bounds__(DemShape<D>::NT, DemShape<D>::MINB) dem_dense_
             ex = ex < -126 ? -126 : (ex > 126 ? 126 : ex);
             eL += ex;
             const float s = __int_as_float((127 - ex) << 23);
-            for (int e = tid; e < SIZE; e += NT) Fb[dem_phys<D>(e, 0)] *= s;
+            for (int e = tid; e < SIZE; e += NT) Fb[dem_phys<D, true>(e, 0)] *= s;
             __syncthreads();
             float* t = Fa; Fa = Fb; Fb = t;
         }
@@ -264,7 +356,7 @@ __global__ void __launch_bounds__(DemShape<D>::NT, DemShape<D>::MINB) dem_dense_
                 const int base = g | (sf[(D - 1) * (D + 1) + D] << S::SP);         // delta of face (d, d-1)
                 for (int l = 0; l < 4; ++l) {
                     const int ox = ox0 ^ (l & 1), oz = oz0 ^ (l >> 1);
-                    const float z = Fa[dem_phys<D>(base | (ox << S::OXP) | (oz << S::OZP), D)];
+                    const float z = Fa[dem_phys<D, true>(base | (ox << S::OXP) | (oz << S::OZP), D)];
                     lz[l] = z > 0.f ? log((double)z) + (double)eL * 0.69314718055994530942 : -INFINITY;
                 }
             }
