@@ -123,7 +123,11 @@ mld_status mld_code_layout(const mld_code* code, int32_t* stab_type, int32_t* st
  * All arrays are caller-owned device memory; the call is asynchronous and
  * allocates nothing per call after the first call for a given (code, chi)
  * (which uploads the column plan). Status of the device work: see
- * mld_decode_status. B = 0 is a no-op. */
+ * mld_decode_status; a noise row that is not a probability distribution
+ * (an entry negative or non-finite, or the row's sum off 1 by more than
+ * 1e-6) or a depolarizing strength outside [0, 1] is reported there as
+ * MLD_ERR_INVALID_ARG (checked on the device before the decode, so the call
+ * itself stays asynchronous). B = 0 is a no-op. */
 mld_status mld_decode(const mld_code* code, const float* noise, int noise_mode,
                       const uint64_t* syndromes, int64_t B, int chi, int precision,
                       double* logP, uint8_t* argmax, void* stream);
@@ -154,8 +158,9 @@ mld_status mld_decode_host(const mld_code* code, const float* noise, int noise_m
  *   (the device must be current); make that first call before any stream
  *   capture.
  *   Arguments as mld_decode. check_status != 0 synchronises the stream and
- *   returns the device status (MLD_OK or MLD_ERR_NUMERIC); 0 returns as soon
- *   as the work is enqueued. */
+ *   returns the device status (MLD_OK, MLD_ERR_INVALID_ARG for invalid noise
+ *   values as in mld_decode, or MLD_ERR_NUMERIC); 0 returns as soon as the
+ *   work is enqueued. */
 mld_status mld_decode_noalloc(const mld_code* code, const float* noise, int noise_mode,
                               const uint64_t* syndromes, int64_t B, int chi, int precision,
                               double* logP, uint8_t* argmax, void* stream, int check_status);
@@ -215,9 +220,10 @@ mld_status mld_autotune(const mld_code* code, int chi, int precision, int64_t sa
 mld_status mld_decode_grad(const mld_code* code, const float* noise, const uint64_t* syndromes, int64_t B,
                            int chi, const double* dlogP, double* logP, double* dnoise, void* stream);
 
-/* Read and clear the device status word written by earlier mld_decode calls
- * on this code (the caller must have synchronised their streams):
- * MLD_OK, MLD_ERR_TIMEOUT or MLD_ERR_NUMERIC. */
+/* Read and clear the device status word written by earlier mld_decode and
+ * mld_decode_grad calls on this code (the caller must have synchronised
+ * their streams): MLD_OK, MLD_ERR_INVALID_ARG (invalid noise values),
+ * MLD_ERR_NUMERIC or MLD_ERR_TIMEOUT, in that order of precedence. */
 mld_status mld_decode_status(const mld_code* code);
 
 /* Counted floating-point operations per syndrome (all four classes) of the
@@ -256,7 +262,8 @@ mld_status mld_decode_dem(const mld_code* code, const int32_t* mech_qubit, const
                           const double* mech_p, int32_t n_mech, const uint64_t* syndromes, int64_t B,
                           double* logP, uint8_t* argmax, void* stream);
 
-/* Number of kernel launches one mld_decode call makes (for accounting). */
+/* Number of kernel launches one mld_decode call with an argmax output makes
+ * (the noise check, the sweep, the argmax; for accounting). */
 int mld_decode_launches(void);
 
 /* Static description of a status code. */

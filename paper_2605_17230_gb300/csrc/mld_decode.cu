@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "mld_exact.h"
+#include "mld_checks.h"
 #include "mld_dem.h"
 #include "mld_grad.h"
 #include "mld_internal.h"
@@ -930,6 +931,29 @@ __global__ void __launch_bounds__(128) grad_kernel(DecodeArgs a, GradArgs g) {
         if (acc[e] != 0.0) atomicAdd(g.dnoise + e, acc[e]);
 }
 
+__global__ void noise_check_kernel(const float* __restrict__ noise, int mode, int64_t count, int* status) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        bool ok;
+        if (mode == MLD_NOISE_TABLE) {
+            const float4 v = reinterpret_cast<const float4*>(noise)[i];
+            const float sum = (v.x + v.y) + (v.z + v.w);
+            ok = v.x >= 0.f && v.y >= 0.f && v.z >= 0.f && v.w >= 0.f && fabsf(sum - 1.f) <= 1e-6f;   // NaN fails
+        } else {
+            const float p = noise[i];
+            ok = p >= 0.f && p <= 1.f;
+        }
+        if (!ok) atomicOr(status, 1 << MLD_ERR_INVALID_ARG);
+    }
+}
+
+bool launch_noise_check(const float* noise, int noise_mode, int64_t count, int* status, cudaStream_t s) {
+    if (count <= 0) return true;
+    int64_t blocks = (count + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    noise_check_kernel<<<(unsigned)blocks, 256, 0, s>>>(noise, noise_mode, count, status);
+    return cudaGetLastError() == cudaSuccess;
+}
+
 __global__ void argmax_kernel(const double* __restrict__ logP, uint8_t* __restrict__ am, int64_t B) {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
@@ -1051,7 +1075,7 @@ mld_status mld_code_layout(const mld_code* C, int32_t* type, int32_t* sup, uint8
     return MLD_OK;
 }
 
-int mld_decode_launches(void) { return 2; }
+int mld_decode_launches(void) { return 3; }
 
 mld_status mld_decode_flops(const mld_code* C, int chi, int precision, double* out) {
     if (!C || chi < 1 || !out) return MLD_ERR_INVALID_ARG;
@@ -1190,6 +1214,8 @@ mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, co
     }
     const size_t smem = gws ? 0 : (a.qgws ? (size_t)a.per_warp * sizeof(float) : pw) * W;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!mld::launch_noise_check(noise, noise_mode, noise_mode == MLD_NOISE_TABLE ? C->n : B, C->d_status, s))
+        return MLD_ERR_CUDA;
     if (exact) {
         mld::ExactArgs ea;
         ea.dmask = C->d_dmask;
@@ -1237,6 +1263,8 @@ mld_status mld_decode_grad(const mld_code* Cc, const float* noise, const uint64_
     const mld::Plan& P = pd->plan;
     if (P.svd_sites != 0) return MLD_ERR_UNSUPPORTED;       // exact environments need untruncated chi
     const int d = C->d, n = C->n;
+    if (!mld::launch_noise_check(noise, MLD_NOISE_TABLE, n, C->d_status, reinterpret_cast<cudaStream_t>(stream)))
+        return MLD_ERR_CUDA;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -1318,6 +1346,7 @@ mld_status mld_decode_status(const mld_code* C) {
     int h = 0;
     if (cudaMemcpy(&h, C->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MLD_ERR_CUDA;
     if (cudaMemset(C->d_status, 0, sizeof(int)) != cudaSuccess) return MLD_ERR_CUDA;
+    if (h & (1 << MLD_ERR_INVALID_ARG)) return MLD_ERR_INVALID_ARG;
     if (h & (1 << MLD_ERR_NUMERIC)) return MLD_ERR_NUMERIC;
     if (h & (1 << MLD_ERR_TIMEOUT)) return MLD_ERR_TIMEOUT;
     return MLD_OK;

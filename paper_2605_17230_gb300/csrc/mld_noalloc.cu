@@ -13,6 +13,7 @@
 
 #include <mutex>
 
+#include "mld_checks.h"
 #include "mld_exact.h"
 #include "mld_internal.h"
 
@@ -98,6 +99,9 @@ extern "C" mld_status mld_decode_noalloc(const mld_code* C, const float* noise, 
     if (cudaMemcpyAsync(scratch + kStatusSlot, C->dmask.data(), table_bytes, cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
         return MLD_ERR_CUDA;
+    if (!mld::launch_noise_check(noise, noise_mode, noise_mode == MLD_NOISE_TABLE ? C->n : B,
+                                 reinterpret_cast<int*>(scratch), s))
+        return MLD_ERR_CUDA;
     mld::ExactArgs ea;
     ea.dmask = reinterpret_cast<const uint64_t*>(scratch + kStatusSlot);
     ea.noise = noise;
@@ -116,6 +120,7 @@ extern "C" mld_status mld_decode_noalloc(const mld_code* C, const float* noise, 
     if (cudaMemcpyAsync(&h, scratch, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return MLD_ERR_CUDA;
+    if (h & (1 << MLD_ERR_INVALID_ARG)) return MLD_ERR_INVALID_ARG;
     if (h & (1 << MLD_ERR_NUMERIC)) return MLD_ERR_NUMERIC;
     if (h & (1 << MLD_ERR_TIMEOUT)) return MLD_ERR_TIMEOUT;
     return MLD_OK;

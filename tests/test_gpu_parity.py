@@ -332,3 +332,48 @@ def test_d17_truncated_close_to_exact(mld):
     best = np.argmax(ref, axis=1)
     assert np.all(np.abs(lp[np.arange(4), best] - ref[np.arange(4), best]) < 5e-2)
     assert np.array_equal(am, best)
+
+
+def test_invalid_noise_reported_through_status(mld):
+    """A noise row that is not a probability distribution (sum off by more
+    than 1e-6, a negative or non-finite entry) or a depolarizing strength
+    outside [0, 1] sets MLD_ERR_INVALID_ARG in the device status word, which
+    mld_decode_status returns and clears; valid inputs leave it at MLD_OK.
+    Also through the adjoint and the allocation-free entry point."""
+    d, n = 5, 25
+    C = mld.Code(d)
+    good = synth.depolarizing(n, 0.1).astype(np.float32)
+    syn = synth.syndromes_of(d, synth.sample_errors(d, good, 8, seed=3))
+    sy = torch.tensor(syn.view(np.int64), device="cuda")
+    INVALID = 1
+    bads = []
+    t = good.copy(); t[3, 0] += 0.1; bads.append(t)                  # row sums to 1.1
+    t = good.copy(); t[0, 1] = -0.01; t[0, 0] += 0.01; bads.append(t)  # negative entry, sum 1
+    t = good.copy(); t[7, 2] = np.nan; bads.append(t)
+    for t in bads:
+        C.decode(torch.tensor(t, device="cuda"), sy, 8)
+        torch.cuda.synchronize()
+        assert C.status() == INVALID
+        assert C.status() == 0                                         # read clears it
+    C.decode(torch.tensor(good, device="cuda"), sy, 8)
+    torch.cuda.synchronize()
+    assert C.status() == 0
+    p = np.full(8, 0.1, np.float32)
+    C.decode(torch.tensor(p, device="cuda"), sy, 8)
+    torch.cuda.synchronize()
+    assert C.status() == 0
+    p[5] = 1.5
+    C.decode(torch.tensor(p, device="cuda"), sy, 8)
+    torch.cuda.synchronize()
+    assert C.status() == INVALID
+    dn = torch.zeros((n, 4), dtype=torch.float64, device="cuda")
+    up = torch.ones((8, 4), dtype=torch.float64, device="cuda")
+    mld.mld_decode_grad(C.handle, torch.tensor(bads[0], device="cuda"), sy, 8, 8, up, None, dn)
+    torch.cuda.synchronize()
+    assert C.status() == INVALID
+    lp = torch.empty((8, 4), dtype=torch.float64, device="cuda")
+    with pytest.raises(mld.MldError):
+        mld.mld_decode_noalloc(C.handle, torch.tensor(bads[0], device="cuda"), mld.MLD_NOISE_TABLE, sy, 8, 8,
+                               mld.MLD_FP32, lp)
+    mld.mld_decode_noalloc(C.handle, torch.tensor(good, device="cuda"), mld.MLD_NOISE_TABLE, sy, 8, 8,
+                           mld.MLD_FP32, lp)
