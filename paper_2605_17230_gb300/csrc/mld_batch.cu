@@ -6,6 +6,7 @@
 #include <mutex>
 #include <vector>
 
+#include "mld_checks.h"
 #include "mld_internal.h"
 
 namespace {
@@ -50,6 +51,7 @@ struct mld_graph {
 extern "C" {
 
 mld_status mld_decode_batch(const mld_job* jobs, int n_jobs, void* stream) {
+    mld::NvtxRange trace("mld_decode_batch");
     if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return MLD_ERR_INVALID_ARG;
     for (int i = 0; i < n_jobs; ++i)
         if (!jobs[i].code) return MLD_ERR_INVALID_ARG;
@@ -119,6 +121,7 @@ mld_status mld_graph_create(const mld_job* jobs, int n_jobs, mld_graph** out) {
 }
 
 mld_status mld_graph_launch(mld_graph* g, void* stream) {
+    mld::NvtxRange trace("mld_graph_launch");
     if (!g || !g->exec) return MLD_ERR_INVALID_ARG;
     return cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? MLD_OK : MLD_ERR_CUDA;
 }

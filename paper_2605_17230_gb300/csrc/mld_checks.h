@@ -1,7 +1,8 @@
-// Device-side validation of decode inputs.
+// Device-side validation of decode inputs, and host-side trace ranges.
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 namespace mld {
@@ -13,5 +14,15 @@ namespace mld {
 // MLD_ERR_INVALID_ARG of the status word for any violation. False if the
 // launch failed.
 bool launch_noise_check(const float* noise, int noise_mode, int64_t count, int* status, cudaStream_t s);
+
+// Named range on the calling thread's NVTX timeline around a C-ABI call
+// (profilers show the enqueue of each decode; with no tool attached the
+// push and pop cost a few nanoseconds).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 }  // namespace mld

@@ -1090,6 +1090,7 @@ mld_status mld_decode_flops(const mld_code* C, int chi, int precision, double* o
 
 mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, const uint64_t* syn,
                       int64_t B, int chi, int precision, double* logP, uint8_t* argmax, void* stream) {
+    mld::NvtxRange trace("mld_decode");
     mld_code* C = const_cast<mld_code*>(Cc);
     if (!C || B < 0 || chi < 1) return MLD_ERR_INVALID_ARG;
     if (noise_mode != MLD_NOISE_TABLE && noise_mode != MLD_NOISE_DEPOL) return MLD_ERR_INVALID_ARG;
@@ -1252,6 +1253,7 @@ mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, co
 
 mld_status mld_decode_grad(const mld_code* Cc, const float* noise, const uint64_t* syn, int64_t B, int chi,
                            const double* dlogP, double* logP, double* dnoise, void* stream) {
+    mld::NvtxRange trace("mld_decode_grad");
     mld_code* C = const_cast<mld_code*>(Cc);
     if (!C || B < 0 || chi < 1) return MLD_ERR_INVALID_ARG;
     if (B == 0) return MLD_OK;
@@ -1354,6 +1356,7 @@ mld_status mld_decode_status(const mld_code* C) {
 
 mld_status mld_decode_host(const mld_code* Cc, const float* noise, int noise_mode, const uint64_t* syn,
                            int64_t B, int chi, int precision, double* logP, uint8_t* argmax) {
+    mld::NvtxRange trace("mld_decode_host");
     mld_code* C = const_cast<mld_code*>(Cc);
     if (!C || B < 0) return MLD_ERR_INVALID_ARG;
     if (B == 0) return MLD_OK;

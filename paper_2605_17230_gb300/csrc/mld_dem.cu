@@ -37,6 +37,7 @@
 
 #include <vector>
 
+#include "mld_checks.h"
 #include "mld_dem.h"
 
 namespace mld {
@@ -397,6 +398,7 @@ extern "C" mld_status mld_decode_dem(const mld_code* Cc, const int32_t* mech_qub
                                      const double* mech_p, int32_t n_mech, const uint64_t* syndromes, int64_t B,
                                      double* logP, uint8_t* argmax, void* stream) {
     using namespace mld;
+    NvtxRange trace("mld_decode_dem");
     mld_code* C = const_cast<mld_code*>(Cc);
     if (!C || n_mech < 0 || B < 0) return MLD_ERR_INVALID_ARG;
     if (n_mech > 0 && (!mech_qubit || !mech_pauli || !mech_p)) return MLD_ERR_INVALID_ARG;

@@ -1,4 +1,6 @@
 // Dense adjoint of the untruncated sweep, d = 3..9: d ln Z_l / d p_{q,P}.
+// (Each block sums its units' gradients in a fixed order and a second
+// kernel adds the blocks' sums in block order: reruns are bit-identical.)
 //
 // Z is linear in every qubit factor, so dZ/dw_q is the environment of that
 // factor (Sec. 3.2.4: the contraction is differentiable in the local error
@@ -62,6 +64,7 @@ struct GradShape {
     static constexpr int off_acc = (off_rep + N + 1) & ~1;    // 4N doubles: dL/dp of this block
     static constexpr int floats = off_acc + 8 * N;
     static constexpr int lfloats = (D - 1) * HALF;            // global: L_1..L_{d-1}
+    static constexpr int slice = lfloats + 8 * N;              // + the block's 4N double partial sums
     // blocks per SM that shared memory allows (the register budget is held to it)
     static constexpr int FIT = (227 * 1024) / (floats * 4 + 1024);
     static constexpr int MINB = FIT < 16 ? FIT : 16;
@@ -321,7 +324,7 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
     float* misc = sm + S::off_misc;
     int* rep = reinterpret_cast<int*>(sm + S::off_rep);
     double* acc = reinterpret_cast<double*>(sm + S::off_acc);
-    float* Lg = g.lws + (size_t)blockIdx.x * S::lfloats;
+    float* Lg = g.lws + (size_t)blockIdx.x * S::slice;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool owns2 = tid < S::REST2;
 
@@ -573,8 +576,28 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
         __syncthreads();
     }
     __syncthreads();
-    for (int e = tid; e < 4 * N; e += NT)
-        if (acc[e] != 0.0) atomicAdd(g.dnoise + e, acc[e]);
+    // the block's sums go to its own slot; grad_reduce_kernel adds the slots
+    // in block order, so a rerun gives the same bits
+    double* part = reinterpret_cast<double*>(Lg + S::lfloats);
+    for (int e = tid; e < 4 * N; e += NT) part[e] = acc[e];
+}
+
+// One block per gradient entry e: thread t sums the slots t, t + 256, ... in
+// order, then a fixed-shape tree adds the 256 partial sums (deterministic).
+__global__ void __launch_bounds__(256) grad_reduce_kernel(const float* __restrict__ ws, int64_t slice,
+                                                          int64_t lfloats, int64_t blocks,
+                                                          double* __restrict__ dnoise) {
+    __shared__ double part[256];
+    const int e = blockIdx.x, t = threadIdx.x;
+    double s = 0.0;
+    for (int64_t b = t; b < blocks; b += 256) s += reinterpret_cast<const double*>(ws + b * slice + lfloats)[e];
+    part[t] = s;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (t < h) part[t] += part[t + h];
+        __syncthreads();
+    }
+    if (t == 0) dnoise[e] += part[0];
 }
 
 template <int D>
@@ -601,6 +624,8 @@ bool launch_d(const GradDenseArgs& a, int64_t blocks, cudaStream_t s) {
         cudaSuccess)
         return false;
     grad_dense_kernel<D><<<(unsigned)blocks, S::NT, bytes, s>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return false;
+    grad_reduce_kernel<<<4 * S::N, 256, 0, s>>>(a.lws, S::slice, S::lfloats, blocks, a.dnoise);
     return cudaGetLastError() == cudaSuccess;
 }
 
@@ -620,10 +645,10 @@ int64_t grad_dense_blocks(int d, int sms, int64_t B) {
 
 int64_t grad_dense_workspace_floats(int d) {
     switch (d) {
-        case 3: return GradShape<3>::lfloats;
-        case 5: return GradShape<5>::lfloats;
-        case 7: return GradShape<7>::lfloats;
-        case 9: return GradShape<9>::lfloats;
+        case 3: return GradShape<3>::slice;
+        case 5: return GradShape<5>::slice;
+        case 7: return GradShape<7>::slice;
+        case 9: return GradShape<9>::slice;
     }
     return 0;
 }

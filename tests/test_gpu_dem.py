@@ -134,3 +134,15 @@ def test_dem_degenerate_inputs(mld):
     big = mld.Code(11)
     with pytest.raises(mld.MldError):
         big.decode_dem([0], [1], [0.1], torch.zeros((1, 2), dtype=torch.int64, device="cuda"))
+
+
+def test_dem_rerun_bit_identical(mld):
+    d, B = 7, 4096
+    q, c, p = _model(d, seed=70)
+    E = synth.sample_errors(d, oracle.dem_qubit_table(d, q, c, p), B, seed=71)
+    sy = torch.tensor(synth.syndromes_of(d, E).view(np.int64), device="cuda")
+    code = mld.Code(d)
+    a, _ = code.decode_dem(q, c, p, sy)
+    b, _ = code.decode_dem(q, c, p, sy)
+    torch.cuda.synchronize()
+    assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())

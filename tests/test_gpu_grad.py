@@ -82,6 +82,25 @@ def test_gradient_many_units_per_block(mld, d, chi, B):
     np.testing.assert_allclose(lp0.cpu().numpy(), lz.reshape(-1, 4), rtol=0, atol=1e-5)
 
 
+def test_gradient_rerun_bit_identical(mld):
+    """The dense adjoint sums each block's units in order and the blocks'
+    sums in block order: the same call twice gives the same bits."""
+    d, chi, B = 7, 8, 1024
+    n, noise, E, syn = _setup(d, B, seed=77)
+    code = mld.Code(d)
+    up = torch.tensor(np.random.default_rng(77).normal(size=(B, 4)), device="cuda")
+    nz = torch.tensor(noise, device="cuda")
+    sy = torch.tensor(syn.view(np.int64), device="cuda")
+    outs = []
+    for _ in range(2):
+        dn = torch.zeros((n, 4), dtype=torch.float64, device="cuda")
+        lp = torch.zeros((B, 4), dtype=torch.float64, device="cuda")
+        mld.mld_decode_grad(code.handle, nz, sy, B, chi, up, lp, dn)
+        torch.cuda.synchronize()
+        outs.append((dn.cpu().numpy(), lp.cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
 def test_gradient_d11_checkpoint_path(mld):
     """d = 11 (beyond the dense on-chip states): MPS checkpoints and the
     half-turn image's sweep, against the oracle's exact derivative."""
