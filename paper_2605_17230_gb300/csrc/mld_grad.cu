@@ -51,20 +51,20 @@ struct GradShape {
     static constexpr int REST2 = SIZE >> 4;         // rests of a pair step (sixteen entries each)
     static constexpr int NT = REST2 >= 128 ? 128 : 32;
     static constexpr int NW = NT / 32;
-    static constexpr int NG = (D + 1) / 2 + 1;      // stored G states: r = 0, 2, .., d-1 and d
+    static constexpr int NG = (D + 1) / 2;          // stored G states: r = 0, 2, .., d-1
     // shared memory (floats)
     static constexpr int off_w = 0;                          // 4N factor weights (slot order Wp)
     static constexpr int off_g = (4 * N + 3) & ~3;           // NG states of SIZE
-    static constexpr int off_f = off_g + NG * SIZE;           // SIZE: the state before factor 0
-    static constexpr int off_r = off_f + SIZE;                // HALF: L_{c+1} staging, R_{c+1}
-    static constexpr int off_red = off_r + HALF;              // D x NW x 4 per-warp environment sums
+    static constexpr int off_l = off_g + NG * SIZE;           // HALF: L_c for the environment pass
+    static constexpr int off_ra = off_l + HALF;               // HALF: R_{c+1} (and staging)
+    static constexpr int off_rb = off_ra + HALF;              // HALF: R_c being formed
+    static constexpr int off_red = off_rb + HALF;             // D x NW x 4 per-warp environment sums
     static constexpr int off_env = off_red + D * NW * 4;      // D x 4 environments of a column
     static constexpr int off_misc = off_env + D * 4;          // 32: per-warp reductions
     static constexpr int off_rep = off_misc + 32;             // N ints: representative x + 2z
-    static constexpr int off_acc = (off_rep + N + 1) & ~1;    // 4N doubles: dL/dp of this block
-    static constexpr int floats = off_acc + 8 * N;
+    static constexpr int floats = off_rep + N;
     static constexpr int lfloats = (D - 1) * HALF;            // global: L_1..L_{d-1}
-    static constexpr int slice = lfloats + 8 * N;              // + the block's 4N double partial sums
+    static constexpr int slice = lfloats + 8 * N;              // + the block's 4N double gradient sums
     // blocks per SM that shared memory allows (the register budget is held to it)
     static constexpr int FIT = (227 * 1024) / (floats * 4 + 1024);
     static constexpr int MINB = FIT < 16 ? FIT : 16;
@@ -155,16 +155,19 @@ __device__ __forceinline__ void single_forward(const float* __restrict__ Fr, flo
     }
 }
 
-// G_r[b, a', a] = sum_b' G_{r+1}[b, b', a'] w(a, a', b, b')
-template <int D>
+// G_r[b, a', a] = sum_b' G_{r+1}[b, b', a'] w(a, a', b, b'). For the
+// column's last factor, G_{r+1} = G_d is R_{c+1} for both values of the
+// spare bit: read from the R buffer (HALF entries, plain layout).
+template <int D, bool GR>
 __device__ __forceinline__ void single_backward(const float* __restrict__ Gn, float* __restrict__ Gr,
                                                 const float (&Wp)[4], int r, int rs) {
+    constexpr int HALF = GradShape<D>::HALF;
     int oi[8], oo[8];
     single_offsets<D>(rs, r, r + 1, oi);
     single_offsets<D>(rs, r, r, oo);
     float y[8];   // y[b | b'<<1 | a'<<2]
 #pragma unroll
-    for (int k = 0; k < 8; ++k) y[k] = Gn[oi[k]];
+    for (int k = 0; k < 8; ++k) y[k] = GR ? Gn[oi[k] & (HALF - 1)] : Gn[oi[k]];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {   // k = b | a'<<1 | a<<2
         const int b = k & 1, ap = (k >> 1) & 1, a = k >> 2, i0 = b | (ap << 2);
@@ -172,18 +175,19 @@ __device__ __forceinline__ void single_backward(const float* __restrict__ Gn, fl
     }
 }
 
-// e[jw(a, a', b, b')] += F_r[b, a', a] G_{r+1}[b, b', a']
-template <int D>
+// e[jw(a, a', b, b')] += F_r[b, a', a] G_{r+1}[b, b', a'] (G as in single_backward)
+template <int D, bool GR>
 __device__ __forceinline__ void single_environment(const float* __restrict__ Fr, const float* __restrict__ Gn,
                                                    int r, int rs, float (&e)[4]) {
+    constexpr int HALF = GradShape<D>::HALF;
     int o0[8], o1[8];
     single_offsets<D>(rs, r, r, o0);
     single_offsets<D>(rs, r, r + 1, o1);
     float x[8], y[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        x[k] = Fr[o0[k]];   // x[b | a'<<1 | a<<2]
-        y[k] = Gn[o1[k]];   // y[b | b'<<1 | a'<<2]
+        x[k] = Fr[o0[k]];                                     // x[b | a'<<1 | a<<2]
+        y[k] = GR ? Gn[o1[k] & (HALF - 1)] : Gn[o1[k]];       // y[b | b'<<1 | a'<<2]
     }
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
@@ -317,14 +321,15 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
     float* sm = reinterpret_cast<float*>(smem4);
     float* wts = sm + S::off_w;
     float* G = sm + S::off_g;              // G + gslot(r) * SIZE: the state before factor r
-    float* Fs = sm + S::off_f;
-    float* Rs = sm + S::off_r;
+    float* Lb = sm + S::off_l;
+    float* Rcur = sm + S::off_ra;
+    float* Rnxt = sm + S::off_rb;
     float* red = sm + S::off_red;
     float* env = sm + S::off_env;
     float* misc = sm + S::off_misc;
     int* rep = reinterpret_cast<int*>(sm + S::off_rep);
-    double* acc = reinterpret_cast<double*>(sm + S::off_acc);
     float* Lg = g.lws + (size_t)blockIdx.x * S::slice;
+    double* acc = reinterpret_cast<double*>(Lg + S::lfloats);   // this block's dL/dp, summed in unit order
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool owns2 = tid < S::REST2;
 
@@ -360,18 +365,18 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
         }
         {
             const int pm0 = present_rows<D>(0);
-            for (int e = tid; e < SIZE; e += NT) Fs[phys<D>(e, 0)] = (left_index<D>(e) & ~pm0) == 0 ? 1.f : 0.f;
+            for (int e = tid; e < SIZE; e += NT) G[phys<D>(e, 0)] = (left_index<D>(e) & ~pm0) == 0 ? 1.f : 0.f;
         }
         __syncthreads();
 
         // ---------------------------------------------------------------- forward
-        // the states ping-pong between Fs and G slot 0 (free until the backward pass)
+        // the states ping-pong between G slots 0 and 1 (free until the backward pass)
         int eL = 0;
         float total = 0.f;
         bool dead = false;
         for (int c = 0; c < D; ++c) {
-            float* Fa = Fs;
-            float* Fb = G;
+            float* Fa = G;
+            float* Fb = G + SIZE;
 #pragma unroll
             for (int r = 0; r + 1 < D; r += 2) {
                 float W0[4], W1[4];
@@ -403,7 +408,7 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
             float tmax = 0.f, tsum = 0.f;
             for (int bi = tid; bi < HALF; bi += NT) {
                 const float v = (bi & ~pmn) == 0 ? Fa[phys<D>(bi, D)] + Fa[phys<D>(bi | HALF, D)] : 0.f;
-                Rs[bi] = v;
+                Rcur[bi] = v;
                 tmax = fmaxf(tmax, v);
                 tsum += v;
             }
@@ -416,8 +421,8 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
             int ex = 0;
             const float s = inv_pow2_of(m, &ex);
             eL += ex;
-            for (int e = tid; e < SIZE; e += NT) Fs[phys<D>(e, 0)] = Rs[left_index<D>(e)] * s;
-            for (int bi = tid; bi < HALF; bi += NT) Lg[c * HALF + bi] = Rs[bi] * s;
+            for (int e = tid; e < SIZE; e += NT) G[phys<D>(e, 0)] = Rcur[left_index<D>(e)] * s;
+            for (int bi = tid; bi < HALF; bi += NT) Lg[c * HALF + bi] = Rcur[bi] * s;
             __syncthreads();
         }
         const double lz = (!dead && total > 0.f && total < INFINITY)
@@ -430,26 +435,22 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
         }
 
         // ---------------------------------------------------------------- backward
+        {
+            const int pmd = present_rows<D>(D);
+            for (int bi = tid; bi < HALF; bi += NT) Rcur[bi] = (bi & ~pmd) == 0 ? 1.f : 0.f;   // R_d
+        }
         for (int c = D - 1; c >= 0; --c) {
             {
-                const int pmn = present_rows<D>(c + 1);
-                float* GD = G + gslot<D>(D) * SIZE;
-                for (int e = tid; e < SIZE; e += NT) {
-                    const int bi = e & (HALF - 1);
-                    GD[phys<D>(e, D)] = c == D - 1 ? ((bi & ~pmn) == 0 ? 1.f : 0.f) : Rs[bi];
-                }
                 const int pm0 = present_rows<D>(0);
-                for (int e = tid; e < SIZE; e += NT) {
-                    const int li = left_index<D>(e);
-                    Fs[phys<D>(e, 0)] = c == 0 ? ((li & ~pm0) == 0 ? 1.f : 0.f) : Lg[(c - 1) * HALF + li];
-                }
+                for (int bi = tid; bi < HALF; bi += NT)
+                    Lb[bi] = c == 0 ? ((bi & ~pm0) == 0 ? 1.f : 0.f) : Lg[(c - 1) * HALF + bi];
             }
             __syncthreads();
             {
                 float W[4];
                 factor_weights<D>(wts, D - 1, c, W);
                 for (int rs = tid; rs < S::REST1; rs += NT)
-                    single_backward<D>(G + gslot<D>(D) * SIZE, G + gslot<D>(D - 1) * SIZE, W, D - 1, rs);
+                    single_backward<D, true>(Rcur, G + gslot<D>(D - 1) * SIZE, W, D - 1, rs);
                 __syncthreads();
             }
 #pragma unroll
@@ -475,24 +476,25 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
                 __syncthreads();
             }
             if (c > 0) {
-                // R_c = sum over beta_0 of G_0, rescaled
+                // R_c = sum over beta_0 of G_0, rescaled (R_{c+1} stays in Rcur for the pass below)
                 const int pmc = present_rows<D>(c);
                 float tmax = 0.f;
                 for (int ai = tid; ai < HALF; ai += NT) {
                     const int e = (ai & ~1) | ((ai & 1) << (D + 1));
                     const float v = (ai & ~pmc) == 0 ? G[phys<D>(e, 0)] + G[phys<D>(e | 1, 0)] : 0.f;
-                    Rs[ai] = v;
+                    Rnxt[ai] = v;
                     tmax = fmaxf(tmax, v);
                 }
                 const float m = block_max_nonneg<NW>(tmax, misc, tid);
                 int ex = 0;
                 const float s = (m > 0.f && m < INFINITY) ? inv_pow2_of(m, &ex) : 1.f;
-                for (int ai = tid; ai < HALF; ai += NT) Rs[ai] *= s;
+                for (int ai = tid; ai < HALF; ai += NT) Rnxt[ai] *= s;
             }
             // re-apply the factors from L_c with each factor's environment; the
             // state after pair r goes to the slot of G_r, which pair r-2 (or
-            // the extraction of R_c) has consumed
-            const float* Fa = Fs;
+            // the extraction of R_c) has consumed; the first pair reads L_c
+            // itself (beta_0 free, alpha_0 at bit d+1)
+            const float* Fa = nullptr;
 #pragma unroll
             for (int r = 0; r + 1 < D; r += 2) {
                 float W0[4], W1[4];
@@ -506,10 +508,20 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
                     pair_offsets<D>(tid, r, r + 2, o2);
                     const float* Gn = G + gslot<D>(r + 2) * SIZE;
                     float X[16], Gz[16], Y[16], Gy[16];
+                    if (r == 0) {
+                        const int core = tid << 3;     // rest bits above positions 0, 1, 2 (bit d+1 from g)
 #pragma unroll
-                    for (int m = 0; m < 16; ++m) {
-                        X[m] = Fa[o0[m]];
-                        Gz[m] = Gn[o2[m]];
+                        for (int m = 0; m < 16; ++m) {
+                            const int lg = core | (m & 7) | ((m >> 3) << (D + 1));
+                            X[m] = Lb[left_index<D>(lg)];
+                            Gz[m] = Gn[o2[m]];
+                        }
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < 16; ++m) {
+                            X[m] = Fa[o0[m]];
+                            Gz[m] = Gn[o2[m]];
+                        }
                     }
                     pair_first(X, W0, Y);
                     pair_second_t(Gz, W1, Gy);
@@ -527,12 +539,10 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
                         const int j = 4 + jw(ar1, ar2, br1, br2);
                         e[j] = fmaf(Y[g4(br, br1, ar2, ar1)], Gz[g4(br, br1, br2, ar2)], e[j]);
                     }
-                    if (r + 2 < D) {
-                        float Z[16];
-                        pair_second(Y, W1, Z);
+                    float Z[16];
+                    pair_second(Y, W1, Z);
 #pragma unroll
-                        for (int m = 0; m < 16; ++m) Fb[o2[m]] = Z[m];
-                    }
+                    for (int m = 0; m < 16; ++m) Fb[o2[m]] = Z[m];
                 }
                 const float tot = reduce_scatter8(e, lane);
                 if ((lane & 3) == 0) {
@@ -544,8 +554,7 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
             }
             {
                 float e[4] = {0.f, 0.f, 0.f, 0.f};
-                for (int rs = tid; rs < S::REST1; rs += NT)
-                    single_environment<D>(Fa, G + gslot<D>(D) * SIZE, D - 1, rs, e);
+                for (int rs = tid; rs < S::REST1; rs += NT) single_environment<D, true>(Fa, Rcur, D - 1, rs, e);
                 const float tot = reduce_scatter4(e, lane);
                 if ((lane & 7) == 0) red[((D - 1) * NW + warp) * 4 + (lane >> 3)] = tot;
                 __syncthreads();
@@ -572,14 +581,12 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
                     acc[4 * q + (xx ? (zz ? 2 : 1) : (zz ? 3 : 0))] += up * (double)(eu / zc);
                 }
             }
+            float* t = Rcur; Rcur = Rnxt; Rnxt = t;
         }
         __syncthreads();
     }
-    __syncthreads();
-    // the block's sums go to its own slot; grad_reduce_kernel adds the slots
-    // in block order, so a rerun gives the same bits
-    double* part = reinterpret_cast<double*>(Lg + S::lfloats);
-    for (int e = tid; e < 4 * N; e += NT) part[e] = acc[e];
+    // acc is the block's slot: grad_reduce_kernel adds the slots in block
+    // order, so a rerun gives the same bits
 }
 
 // One block per gradient entry e: thread t sums the slots t, t + 256, ... in
