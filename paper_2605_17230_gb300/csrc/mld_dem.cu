@@ -68,7 +68,8 @@ struct DemShape {
     static constexpr int NT = D >= 9 ? 128 : (D >= 7 ? 64 : 32);
     static constexpr int NW = NT / 32;
     static constexpr int NF = (D + 1) * (D + 1);
-    static constexpr int off_f0 = 0, off_f1 = SIZE, off_sf = 2 * SIZE, off_misc = off_sf + ((NF + 3) & ~3);
+    static constexpr int off_f = 0, off_sf = SIZE, off_misc = off_sf + ((NF + 3) & ~3);   // one state, updated in place
+    static constexpr int PER = SIZE / NT;                           // entries per thread in a column transition
     static constexpr int floats = off_misc + 32;
     static constexpr int FIT = (227 * 1024) / (floats * 4 + 1024);
     static constexpr int REGS = 65536 / (NT * 96);                // keep room for ~96 registers a thread
@@ -83,32 +84,18 @@ __host__ __device__ constexpr int dem_face_bit(int d, int i, int j, int e) {
     return !dem_face_present(d, i, j) ? 0 : (((i + j) & 1) == 0 ? (e >> 1) & 1 : e & 1);
 }
 
-// Shared-memory position of entry e of a stored state (d >= 7). The 32 lanes
-// of a warp own 32 consecutive rests, i.e. vary the five lowest index bits
-// that the step leaves fixed; a step that touches bank bits (0..4) would put
-// the warp on 4 to 16 banks, so bits 5..7 are XORed into the bank bits with
-// masks chosen per stored state such that the lane -> bank map is a
-// bijection for the step writing the state and the step reading it.
-// Column 0 runs single qubit steps (touching r, r+1, d+1; states before
-// every row r stored); the other columns run pairs of rows (touching r, r+1,
-// r+2, d+1; states before even rows stored) and a single last row.
-__device__ __forceinline__ constexpr int swz_single(int lay, int bit) {
-    return bit == 5 ? (lay == 0 ? 1 : lay == 1 ? 5 : lay == 2 ? 10 : lay == 3 ? 20 : lay == 4 ? 8 : 0)
-         : bit == 6 ? (lay <= 1 ? 2 : lay == 2 ? 4 : lay == 3 ? 8 : lay <= 5 ? 16 : 0)
-                    : 0;
-}
-__device__ __forceinline__ constexpr int swz_pair(int lay, int bit) {
-    return bit == 5 ? (lay == 0 ? 1 : lay == 2 ? 9 : lay == 4 ? 4 : 0)
-         : bit == 6 ? (lay == 0 ? 2 : lay == 2 ? 18 : lay == 4 ? 8 : 0)
-                    : (lay == 0 || lay == 2 ? 4 : lay == 4 || lay == 6 ? 16 : 0);
-}
-template <int D, bool PAIR>
-__device__ __forceinline__ int dem_phys(int e, int lay) {
+// Shared-memory position of entry e of the state (d >= 7). Every step
+// updates its rests' entries in place, so one layout serves the whole sweep.
+// The 32 lanes of a warp own 32 consecutive rests, i.e. vary the five lowest
+// index bits the step leaves fixed; where a step touches bank bits (0..4),
+// bits 5, 6 and 7 are XORed into the bank bits (masks 9, 18 and 28) so that
+// the lane -> bank map is a bijection for every step pattern of the sweep:
+// column 0's row 0 and its pairs of odd rows, the other columns' pairs of
+// even rows and their last row.
+template <int D>
+__device__ __forceinline__ int dem_phys(int e) {
     if (D < 7) return e;
-    const int m5 = PAIR ? swz_pair(lay, 5) : swz_single(lay, 5);
-    const int m6 = PAIR ? swz_pair(lay, 6) : swz_single(lay, 6);
-    const int m7 = PAIR ? swz_pair(lay, 7) : swz_single(lay, 7);
-    return e ^ (((e >> 5) & 1) ? m5 : 0) ^ (((e >> 6) & 1) ? m6 : 0) ^ (((e >> 7) & 1) ? m7 : 0);
+    return e ^ (((e >> 5) & 1) ? 9 : 0) ^ (((e >> 6) & 1) ? 18 : 0) ^ (((e >> 7) & 1) ? 28 : 0);
 }
 
 // Insert a zero bit at position p (positions must be inserted in ascending order).
@@ -157,11 +144,10 @@ template <int KIND>
 __device__ __forceinline__ constexpr int kind_column(int d) { return KIND == 0 ? 0 : KIND == 1 ? 2 : KIND == 2 ? 1 : d - 1; }
 
 // Single qubit step R of a column of kind KIND (0 = column 0, 1 = interior
-// even, 2 = interior odd, 3 = column d-1): local bits 0 = position R,
-// 1 = R+1, 2 = spare, then the observables the qubit feeds.
-template <int D, int KIND, int R, bool PAIR>
-__device__ __forceinline__ void dem_single(const float* __restrict__ Fin, float* __restrict__ Fout,
-                                           const float (&w)[4], int sr, int tid) {
+// even, 2 = interior odd, 3 = column d-1), in place: local bits 0 = position
+// R, 1 = R+1, 2 = spare, then the observables the qubit feeds.
+template <int D, int KIND, int R>
+__device__ __forceinline__ void dem_single(float* __restrict__ F, const float (&w)[4], int sr, int tid) {
     using S = DemShape<D>;
     constexpr int CR = kind_column<KIND>(D);
     constexpr bool OX = R == 0, OZ = KIND == 0;
@@ -172,54 +158,52 @@ __device__ __forceinline__ void dem_single(const float* __restrict__ Fin, float*
         int core = insert_zero(insert_zero(insert_zero(rs, R), R + 1), S::SP);
         if (OX) core = insert_zero(core, S::OXP);
         if (OZ) core = insert_zero(core, S::OZP);
-        const int bin = dem_phys<D, PAIR>(core, R), bout = dem_phys<D, PAIR>(core, R + 1);
+        const int base = dem_phys<D>(core);
+        int o[NE];
         float in[NE], out[NE];
 #pragma unroll
         for (int li = 0; li < NE; ++li) {
             const int off = ((li & 1) << R) | (((li >> 1) & 1) << (R + 1)) | (((li >> 2) & 1) << S::SP) |
                             (OX ? ((li >> 3) & 1) << S::OXP : 0) | (OZ ? ((li >> (OX ? 4 : 3)) & 1) << S::OZP : 0);
-            in[li] = Fin[bin ^ dem_phys<D, PAIR>(off, R)];
+            o[li] = base ^ dem_phys<D>(off);
+            in[li] = F[o[li]];
         }
         qubit_apply<D, CR, R, NE, 0, 1, 2, L3, L4>(in, out, w, sr);
 #pragma unroll
-        for (int lo = 0; lo < NE; ++lo) {
-            const int off = ((lo & 1) << R) | (((lo >> 1) & 1) << (R + 1)) | (((lo >> 2) & 1) << S::SP) |
-                            (OX ? ((lo >> 3) & 1) << S::OXP : 0) | (OZ ? ((lo >> (OX ? 4 : 3)) & 1) << S::OZP : 0);
-            Fout[bout ^ dem_phys<D, PAIR>(off, R + 1)] = out[lo];
-        }
+        for (int lo = 0; lo < NE; ++lo) F[o[lo]] = out[lo];
     }
 }
 
-// Qubits R and R+1 (R even) of a column of kind 1..3 in one pass: local
-// bits 0 = position R, 1 = R+1, 2 = R+2, 3 = spare, 4 = the Z_L observable
-// (row 0 only).
+// Qubits R and R+1 of a column in one pass, in place: local bits 0 =
+// position R, 1 = R+1, 2 = R+2, 3 = spare, 4 = the observable the rows feed
+// (Z_L's x-parity on row 0 of columns 1..d-1; X_L's z-parity on every row of
+// column 0, where the pairs start at row 1).
 template <int D, int KIND, int R>
-__device__ __forceinline__ void dem_pair(const float* __restrict__ Fin, float* __restrict__ Fout, const float (&w0)[4],
-                                         const float (&w1)[4], int s0, int s1, int tid) {
+__device__ __forceinline__ void dem_pair(float* __restrict__ F, const float (&w0)[4], const float (&w1)[4], int s0,
+                                         int s1, int tid) {
     using S = DemShape<D>;
     constexpr int CR = kind_column<KIND>(D);
-    constexpr bool OX = R == 0;
-    constexpr int T = 4 + (OX ? 1 : 0), NE = 1 << T;
+    constexpr bool OZ = KIND == 0, OX = !OZ && R == 0;
+    constexpr int POS4 = OZ ? S::OZP : S::OXP;
+    constexpr int T = 4 + ((OX || OZ) ? 1 : 0), NE = 1 << T;
     constexpr int REST = S::SIZE >> T;
     for (int rs = tid; rs < REST; rs += S::NT) {
         int core = insert_zero(insert_zero(insert_zero(insert_zero(rs, R), R + 1), R + 2), S::SP);
-        if (OX) core = insert_zero(core, S::OXP);
-        const int bin = dem_phys<D, true>(core, R), bout = dem_phys<D, true>(core, R + 2);
+        if (T == 5) core = insert_zero(core, POS4);
+        const int base = dem_phys<D>(core);
+        int o[NE];
         float in[NE], mid[NE], out[NE];
 #pragma unroll
         for (int li = 0; li < NE; ++li) {
             const int off = ((li & 1) << R) | (((li >> 1) & 1) << (R + 1)) | (((li >> 2) & 1) << (R + 2)) |
-                            (((li >> 3) & 1) << S::SP) | (OX ? ((li >> 4) & 1) << S::OXP : 0);
-            in[li] = Fin[bin ^ dem_phys<D, true>(off, R)];
+                            (((li >> 3) & 1) << S::SP) | (T == 5 ? ((li >> 4) & 1) << POS4 : 0);
+            o[li] = base ^ dem_phys<D>(off);
+            in[li] = F[o[li]];
         }
-        qubit_apply<D, CR, R, NE, 0, 1, 3, OX ? 4 : -1, -1>(in, mid, w0, s0);
-        qubit_apply<D, CR, R + 1, NE, 1, 2, 3, -1, -1>(mid, out, w1, s1);
+        qubit_apply<D, CR, R, NE, 0, 1, 3, OX ? 4 : -1, OZ ? 4 : -1>(in, mid, w0, s0);
+        qubit_apply<D, CR, R + 1, NE, 1, 2, 3, -1, OZ ? 4 : -1>(mid, out, w1, s1);
 #pragma unroll
-        for (int lo = 0; lo < NE; ++lo) {
-            const int off = ((lo & 1) << R) | (((lo >> 1) & 1) << (R + 1)) | (((lo >> 2) & 1) << (R + 2)) |
-                            (((lo >> 3) & 1) << S::SP) | (OX ? ((lo >> 4) & 1) << S::OXP : 0);
-            Fout[bout ^ dem_phys<D, true>(off, R + 2)] = out[lo];
-        }
+        for (int lo = 0; lo < NE; ++lo) F[o[lo]] = out[lo];
     }
 }
 
@@ -229,37 +213,40 @@ __device__ __forceinline__ void qubit_weights(const DemParams& prm, int r, int c
     w[0] = pq[0]; w[1] = pq[1]; w[2] = pq[2]; w[3] = pq[3];
 }
 
-// Column 0: single steps for every row.
+// Column 0: row 0 alone (it feeds both observables), then pairs of rows.
 template <int D, int R>
-__device__ __forceinline__ void dem_column0(float*& Fa, float*& Fb, const DemParams& prm, const int* sf, int tid) {
-    if constexpr (R < D) {
+__device__ __forceinline__ void dem_column0(float* F, const DemParams& prm, const int* sf, int tid) {
+    if constexpr (R == 0) {
         float w[4];
-        qubit_weights<D>(prm, R, 0, w);
-        dem_single<D, 0, R, false>(Fa, Fb, w, sf[R], tid);
+        qubit_weights<D>(prm, 0, 0, w);
+        dem_single<D, 0, 0>(F, w, sf[0], tid);
         __syncthreads();
-        float* t = Fa; Fa = Fb; Fb = t;
-        dem_column0<D, R + 1>(Fa, Fb, prm, sf, tid);
+        dem_column0<D, 1>(F, prm, sf, tid);
+    } else if constexpr (R + 1 < D) {
+        float w0[4], w1[4];
+        qubit_weights<D>(prm, R, 0, w0);
+        qubit_weights<D>(prm, R + 1, 0, w1);
+        dem_pair<D, 0, R>(F, w0, w1, sf[R], sf[R + 1], tid);
+        __syncthreads();
+        dem_column0<D, R + 2>(F, prm, sf, tid);
     }
 }
 
 // Columns 1..d-1: pairs of rows, then the last row alone.
 template <int D, int KIND, int R>
-__device__ __forceinline__ void dem_column(float*& Fa, float*& Fb, const DemParams& prm, const int* sf, int c,
-                                           int tid) {
+__device__ __forceinline__ void dem_column(float* F, const DemParams& prm, const int* sf, int c, int tid) {
     if constexpr (R + 1 < D) {
         float w0[4], w1[4];
         qubit_weights<D>(prm, R, c, w0);
         qubit_weights<D>(prm, R + 1, c, w1);
-        dem_pair<D, KIND, R>(Fa, Fb, w0, w1, sf[c * (D + 1) + R], sf[c * (D + 1) + R + 1], tid);
+        dem_pair<D, KIND, R>(F, w0, w1, sf[c * (D + 1) + R], sf[c * (D + 1) + R + 1], tid);
         __syncthreads();
-        float* t = Fa; Fa = Fb; Fb = t;
-        dem_column<D, KIND, R + 2>(Fa, Fb, prm, sf, c, tid);
+        dem_column<D, KIND, R + 2>(F, prm, sf, c, tid);
     } else if constexpr (R < D) {
         float w[4];
         qubit_weights<D>(prm, R, c, w);
-        dem_single<D, KIND, R, true>(Fa, Fb, w, sf[c * (D + 1) + R], tid);
+        dem_single<D, KIND, R>(F, w, sf[c * (D + 1) + R], tid);
         __syncthreads();
-        float* t = Fa; Fa = Fb; Fb = t;
     }
 }
 
@@ -280,8 +267,7 @@ __global__ void __launch_bounds__(DemShape<D>::NT, DemShape<D>::MINB) dem_dense_
     constexpr int N = S::N, HALF = S::HALF, SIZE = S::SIZE, NT = S::NT, NW = S::NW;
     extern __shared__ float4 smem4[];
     float* sm = reinterpret_cast<float*>(smem4);
-    float* F0 = sm + S::off_f0;
-    float* F1 = sm + S::off_f1;
+    float* F = sm + S::off_f;
     int* sf = reinterpret_cast<int*>(sm + S::off_sf);     // syndrome bit of face (i, j) at j (d+1) + i
     float* misc = sm + S::off_misc;
     const int tid = threadIdx.x;
@@ -308,33 +294,35 @@ __global__ void __launch_bounds__(DemShape<D>::NT, DemShape<D>::MINB) dem_dense_
         const int ox0 = __syncthreads_count(ox_bit) & 1;
         const int oz0 = __syncthreads_count(oz_bit) & 1;
         // column 0 starts with every parity 0
-        for (int e = tid; e < SIZE; e += NT) F0[e] = 0.f;
+        for (int e = tid; e < SIZE; e += NT) F[e] = 0.f;
         __syncthreads();
-        if (tid == 0) F0[0] = 1.f;                       // entry 0 sits at 0 in every layout
+        if (tid == 0) F[0] = 1.f;                     // entry 0 sits at position 0
         __syncthreads();
 
-        float* Fa = F0;
-        float* Fb = F1;
         int eL = 0;
         bool dead = false;
         for (int c = 0; c < D; ++c) {
-            if (c == 0) dem_column0<D, 0>(Fa, Fb, prm, sf, tid);
-            else if (c == D - 1) dem_column<D, 3, 0>(Fa, Fb, prm, sf, c, tid);
-            else if (c & 1) dem_column<D, 2, 0>(Fa, Fb, prm, sf, c, tid);
-            else dem_column<D, 1, 0>(Fa, Fb, prm, sf, c, tid);
+            if (c == 0) dem_column0<D, 0>(F, prm, sf, tid);
+            else if (c == D - 1) dem_column<D, 3, 0>(F, prm, sf, c, tid);
+            else if (c & 1) dem_column<D, 2, 0>(F, prm, sf, c, tid);
+            else dem_column<D, 1, 0>(F, prm, sf, c, tid);
             if (c == D - 1) break;
             // the delta of face (d, c), then corner column c+1 becomes the left column:
-            // position 0 = new g_0 (parity 0), 1..d = f_1..f_d, spare = f_0
+            // position 0 = new g_0 (parity 0), 1..d = f_1..f_d, spare = f_0. A gather,
+            // so every thread loads its entries, the block max is the barrier, then
+            // the rescaled entries are stored.
             const int sD = sf[c * (D + 1) + D];
+            float v[S::PER];
             float tmax = 0.f;
-            for (int e = tid; e < SIZE; e += NT) {
-                float v = 0.f;
+#pragma unroll
+            for (int k = 0; k < S::PER; ++k) {
+                const int e = tid + k * NT;
+                v[k] = 0.f;
                 if (!(e & 1)) {
                     const int old = (e & (HALF - 1) & ~1) | ((e >> S::SP) & 1) | (sD << S::SP) | (e & (3 << S::OXP));
-                    v = Fa[dem_phys<D, true>(old, D)];             // layout d is the plain one
+                    v[k] = F[dem_phys<D>(old)];
                 }
-                Fb[dem_phys<D, true>(e, 0)] = v;
-                tmax = fmaxf(tmax, v);
+                tmax = fmaxf(tmax, v[k]);
             }
             const float m = dem_block_max<NW>(tmax, misc, tid);
             if (!(m > 0.f) || !(m < INFINITY)) { dead = true; break; }
@@ -343,9 +331,9 @@ __global__ void __launch_bounds__(DemShape<D>::NT, DemShape<D>::MINB) dem_dense_
             ex = ex < -126 ? -126 : (ex > 126 ? 126 : ex);
             eL += ex;
             const float s = __int_as_float((127 - ex) << 23);
-            for (int e = tid; e < SIZE; e += NT) Fb[dem_phys<D, true>(e, 0)] *= s;
+#pragma unroll
+            for (int k = 0; k < S::PER; ++k) F[dem_phys<D>(tid + k * NT)] = v[k] * s;
             __syncthreads();
-            float* t = Fa; Fa = Fb; Fb = t;
         }
         if (tid == 0) {
             double lz[4];
@@ -357,7 +345,7 @@ __global__ void __launch_bounds__(DemShape<D>::NT, DemShape<D>::MINB) dem_dense_
                 const int base = g | (sf[(D - 1) * (D + 1) + D] << S::SP);         // delta of face (d, d-1)
                 for (int l = 0; l < 4; ++l) {
                     const int ox = ox0 ^ (l & 1), oz = oz0 ^ (l >> 1);
-                    const float z = Fa[dem_phys<D, true>(base | (ox << S::OXP) | (oz << S::OZP), D)];
+                    const float z = F[dem_phys<D>(base | (ox << S::OXP) | (oz << S::OZP))];
                     lz[l] = z > 0.f ? log((double)z) + (double)eL * 0.69314718055994530942 : -INFINITY;
                 }
             }
