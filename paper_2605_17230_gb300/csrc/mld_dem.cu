@@ -72,7 +72,8 @@ struct DemShape {
     static constexpr int PER = SIZE / NT;                           // entries per thread in a column transition
     static constexpr int floats = off_misc + 32;
     static constexpr int FIT = (227 * 1024) / (floats * 4 + 1024);
-    static constexpr int REGS = 65536 / (NT * 96);                // keep room for ~96 registers a thread
+    // keep room for ~96 registers a thread at d = 9 (fewer spill there), ~84 below
+    static constexpr int REGS = 65536 / (NT * (D >= 9 ? 96 : 84));
     static constexpr int MINB = FIT < REGS ? (FIT < 16 ? FIT : 16) : (REGS < 16 ? REGS : 16);
 };
 
