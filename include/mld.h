@@ -211,13 +211,12 @@ mld_status mld_autotune(const mld_code* code, int chi, int precision, int64_t sa
  *   dnoise     device double[n][4]: dL/dp_{q,P} (all four entries of a row
  *              treated as independent) is ADDED to it.
  * Each qubit factor's environment is contracted exactly, so chi must not
- * truncate (MLD_ERR_UNSUPPORTED otherwise) and d <= 11. For d <= 9 the left
- * and right boundary states are kept dense on chip (the right states are
- * carried back through each column by the transposed factors); d = 11 uses
- * checkpointed MPS left states and the sweep of the half-turn image for the
- * right states. FP32 contraction, FP64 accumulation (for d <= 9 in a fixed
- * order, so reruns give the same bits). Asynchronous on stream;
- * uses a device workspace owned by the code object (not reentrant per code). */
+ * truncate (MLD_ERR_UNSUPPORTED otherwise) and d <= 11. The left and right
+ * boundary states are kept dense on chip (the right states are carried back
+ * through each column by the transposed factors). FP32 contraction, FP64
+ * accumulation in a fixed order, so reruns give the same bits. Asynchronous
+ * on stream; uses a device workspace owned by the code object (not reentrant
+ * per code). */
 mld_status mld_decode_grad(const mld_code* code, const float* noise, const uint64_t* syndromes, int64_t B,
                            int chi, const double* dlogP, double* logP, double* dnoise, void* stream);
 

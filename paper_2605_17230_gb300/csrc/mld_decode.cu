@@ -343,15 +343,9 @@ __device__ bool jacobi(float* X, int L, int ldx, int nv, float* acc, int lane) {
 }
 
 // ------------------------------------------------------------------ kernel
-// One (syndrome, class) unit on one warp (the adjoint's unit; with pair, a
-// (syndrome, l_Z) unit as below), with its state at ws (shared
-// memory, or this warp's slice of the global workspace); returns ln Z.
-// rotate: sweep the half-turn image of the problem (qubit (r,c) takes the
-// data of qubit (d-1-r, d-1-c)); the layout maps onto itself, so the same
-// plan runs the original columns from right to left. ckpt (optional): after
-// each column c < d-1 the boundary MPS is expanded to the dense vector over
-// corner column c+1 (index bit i = plaquette row i, 2^(d+1) floats) and
-// stored at ckpt + c*2^(d+1), with xbuf (2*2^(d+1) floats) as scratch.
+// One (syndrome, class) unit on one warp (with pair, a (syndrome, l_Z) unit
+// as below), with its state at ws (shared memory, or this warp's slice of the
+// global workspace); returns ln Z.
 //
 // pair (optional): the unit is (syndrome, l_Z) = unit >> 1, unit & 1 and both
 // classes l_X = 0, 1 are decoded, ln Z into pair[0] and pair[1]. X_L is then
@@ -362,9 +356,7 @@ __device__ bool jacobi(float* X, int L, int ldx, int nv, float* acc, int lane) {
 // sites after its old ones). At truncated chi the approximation depends on
 // the representative: this one is E_{l,s} with X_L on column d-1.
 __device__ __forceinline__ double decode_unit(const DecodeArgs& a, float* ws, int64_t unit, int lane,
-                                              bool rotate = false, float* ckpt = nullptr,
-                                              float* xbuf = nullptr, double* pair = nullptr,
-                                              float* qext = nullptr) {
+                                              double* pair = nullptr, float* qext = nullptr) {
     const int64_t b = pair ? unit >> 1 : unit >> 2;
     const int cls = pair ? (int)(unit & 1) << 1 : (int)(unit & 3);
     const int d = a.d, n = a.n;
@@ -379,8 +371,7 @@ __device__ __forceinline__ double decode_unit(const DecodeArgs& a, float* ws, in
     // representative E_{l,s} = f * X_L^{l_X} * Z_L^{l_Z}, factor weights
     uint64_t sw[kMaxSynWords];
     for (int w = 0; w < a.words; ++w) sw[w] = a.syn[b * a.words + w];
-    for (int qf = lane; qf < n; qf += 32) {
-        const int q = rotate ? n - 1 - qf : qf;       // (d-1-r)*d + (d-1-c) = n-1-q
+    for (int q = lane; q < n; q += 32) {
         int x = 0, z = 0;
         const uint64_t* mk = a.dmask + (size_t)q * 2 * a.words;
         for (int w = 0; w < a.words; ++w) {
@@ -401,7 +392,7 @@ __device__ __forceinline__ double decode_unit(const DecodeArgs& a, float* ws, in
         for (int uv = 0; uv < 4; ++uv) {
             const int xx = x ^ (uv & 1), zz = z ^ (uv >> 1);
             const int pidx = (!xx && !zz) ? 0 : (xx && !zz) ? 1 : (xx && zz) ? 2 : 3;
-            wts[4 * qf + uv] = row[pidx];
+            wts[4 * q + uv] = row[pidx];
         }
     }
     (void)cls;
@@ -577,37 +568,6 @@ __device__ __forceinline__ double decode_unit(const DecodeArgs& a, float* ws, in
     const int cend = pair ? d - 1 : d;
     for (int c = 0; c < cend && !zero && !bad; ++c) {
         sweep_column(c);
-        if (ckpt && c < d - 1 && !zero && !bad) {
-            const SiteStep* S = a.steps + (size_t)c * (d + 1);
-            // dense vector over corner column c+1 from the new MPS
-            const int full = 1 << (d + 1);
-            float* v = xbuf;
-            float* vn = xbuf + full;
-            if (lane == 0) v[0] = 1.f;
-            __syncwarp();
-            int nidx = 1;
-            for (int i = 0; i <= d; ++i) {
-                const SiteStep st = S[i];
-                const int Sl = st.Sl, Sr = st.S, pbi = st.pb;
-                const float* site = mps + st.offN;
-                for (int e = lane; e < nidx * 2 * Sr; e += 32) {
-                    const int s = e % Sr, rest = e / Sr, bb = rest / nidx, idx = rest - bb * nidx;
-                    float acc = 0.f;
-                    if (bb < pbi) {
-                        if (st.nkind == K_IDR) acc = v[idx * Sl + bb * Sr + s];
-                        else if (st.nkind == K_IDL) acc = (s / Sl == bb) ? v[idx * Sl + s % Sl] : 0.f;
-                        else
-                            for (int sl = 0; sl < Sl; ++sl) acc = fmaf(v[idx * Sl + sl], site[(sl * pbi + bb) * Sr + s], acc);
-                    }
-                    vn[e] = acc;
-                }
-                __syncwarp();
-                float* tmp = v; v = vn; vn = tmp;
-                nidx *= 2;
-            }
-            for (int e = lane; e < full; e += 32) ckpt[(size_t)c * full + e] = v[e];
-            __syncwarp();
-        }
     }
     auto contract = [&]() -> double {
     double logz;
@@ -696,7 +656,7 @@ decode_fp32_kernel(DecodeArgs a) {
         float* ws = reinterpret_cast<float*>(smem4) + (size_t)warp * a.per_warp;
         float* qx = a.qgws + (size_t)gw * a.q_per_warp;
         for (int64_t unit = gw; unit < 2 * a.B; unit += nw) {
-            decode_unit(a, ws, unit, lane, false, nullptr, nullptr, lz, qx);
+            decode_unit(a, ws, unit, lane, lz, qx);
             if (lane == 0) {
                 a.logP[(unit >> 1) * 4 + 2 * (unit & 1)] = lz[0];
                 a.logP[(unit >> 1) * 4 + 2 * (unit & 1) + 1] = lz[1];
@@ -709,7 +669,7 @@ decode_fp32_kernel(DecodeArgs a) {
         const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
         float* ws = a.gws + (size_t)gw * a.per_warp;
         for (int64_t unit = gw; unit < 2 * a.B; unit += nw) {
-            decode_unit(a, ws, unit, lane, false, nullptr, nullptr, lz);
+            decode_unit(a, ws, unit, lane, lz);
             if (lane == 0) {
                 a.logP[(unit >> 1) * 4 + 2 * (unit & 1)] = lz[0];
                 a.logP[(unit >> 1) * 4 + 2 * (unit & 1) + 1] = lz[1];
@@ -718,217 +678,12 @@ decode_fp32_kernel(DecodeArgs a) {
         }
     } else {
         if (gw >= 2 * a.B) return;
-        decode_unit(a, reinterpret_cast<float*>(smem4) + (size_t)warp * a.per_warp, gw, lane, false, nullptr, nullptr,
-                    lz);
+        decode_unit(a, reinterpret_cast<float*>(smem4) + (size_t)warp * a.per_warp, gw, lane, lz);
         if (lane == 0) {
             a.logP[(gw >> 1) * 4 + 2 * (gw & 1)] = lz[0];
             a.logP[(gw >> 1) * 4 + 2 * (gw & 1) + 1] = lz[1];
         }
     }
-}
-
-// ------------------------------------------------------------------ adjoint
-// Z is linear in every qubit factor, so dZ/dw_q is the environment of that
-// factor (Sec. 3.2.4: the gradient the differentiable estimation of Eq. 10
-// back-propagates through the contraction). For the factors of column c:
-//   Z = <R_{c+1}| T_c |L_c>,
-// L_c the left boundary state over corner column c (forward sweep), R_{c+1}
-// the right state over corner column c+1 (the forward sweep of the half-turn
-// image). T_c L is applied one factor at a time (states over the d+2 bits
-// b_0..b_r | spare = a_r | a_{r+1}..a_d, as in the column elimination), the
-// transposed steps carry R back, and each factor's environment is the
-// contraction of the forward state before it with the backward state after
-// it, bucketed by the factor's four variables. Returned per qubit:
-// dln Z / dw_q[u + 2v] = env / <R|T|L> (scale-free).
-// wts holds the factor weights in half-turn order (qubit q at n-1-q).
-__device__ void column_sandwich(int d, int c, const float* __restrict__ L, const float* __restrict__ R,
-                                const float* __restrict__ wts, float* __restrict__ G, float* __restrict__ F0,
-                                float* __restrict__ F1, float* __restrict__ out, int lane) {
-    const int n = d * d;
-    const int half = 1 << (d + 1), size = half << 1;
-    const int spare = half;
-    // transposed sweep: G_d[idx] = R[b] (both values of the last a_d), then
-    // G_r[old] = sum_{b_{r+1}} G_{r+1}[new(old, b_{r+1})] w_r(...)
-    float* Gd = G + (size_t)d * size;
-    for (int e = lane; e < size; e += 32) Gd[e] = R[e & (half - 1)];
-    __syncwarp();
-    for (int r = d - 1; r >= 0; --r) {
-        const float* wq = wts + 4 * (n - 1 - (r * d + c));
-        const int par = (r + c) & 1;
-        const float* Gn = G + (size_t)(r + 1) * size;
-        float* Go = G + (size_t)r * size;
-        const int bit1 = 1 << (r + 1);
-        for (int old = lane; old < size; old += 32) {
-            const int a = (old >> (d + 1)) & 1, ar1 = (old >> (r + 1)) & 1, br = (old >> r) & 1;
-            const int base = (old & ~bit1 & ~spare) | (ar1 << (d + 1));
-            float acc = 0.f;
-            for (int br1 = 0; br1 < 2; ++br1)
-                acc = fmaf(Gn[base | (br1 << (r + 1))], qweight(wq, par, a, ar1, br, br1), acc);
-            Go[old] = acc;
-        }
-        __syncwarp();
-    }
-    // forward sweep with the environment of each factor
-    for (int e = lane; e < size; e += 32) {
-        const int a0 = (e >> (d + 1)) & 1;
-        F0[e] = L[(e & ~1 & (half - 1)) | a0];
-    }
-    __syncwarp();
-    float zloc = 0.f;
-    for (int r = 0; r < d; ++r) {
-        const float* wq = wts + 4 * (n - 1 - (r * d + c));
-        const int par = (r + c) & 1;
-        const float* Gn = G + (size_t)(r + 1) * size;
-        const int bit1 = 1 << (r + 1);
-        float env[16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) env[k] = 0.f;
-        // the states in eight groups by the factor's bits (a_{r+1}, b_r,
-        // b_{r+1}), so that each group's environment entries are fixed
-        // registers: idx = low | b_r << r | b_{r+1} << (r+1) | mid << (r+2)
-        // | a_{r+1} << (d+1), and F0 holds a_{r+1} at bit r+1, a_r at d+1
-        (void)bit1;
-        const int nrest = size >> 3;
-#pragma unroll
-        for (int combo = 0; combo < 8; ++combo) {
-            const int ar1 = combo & 1, br = (combo >> 1) & 1, br1 = (combo >> 2) & 1;
-            const float w0 = qweight(wq, par, 0, ar1, br, br1), w1 = qweight(wq, par, 1, ar1, br, br1);
-            float e0 = 0.f, e1 = 0.f;
-            for (int rs = lane; rs < nrest; rs += 32) {
-                const int low = rs & ((1 << r) - 1), mid = rs >> r;
-                const int core = low | (br << r) | (mid << (r + 2));
-                const int idx = core | (br1 << (r + 1)) | (ar1 << (d + 1));
-                const int fb = core | (ar1 << (r + 1));
-                const float g = Gn[idx];
-                const float fa0 = F0[fb], fa1 = F0[fb | spare];
-                F1[idx] = fmaf(fa0, w0, fa1 * w1);
-                e0 = fmaf(fa0, g, e0);
-                e1 = fmaf(fa1, g, e1);
-            }
-            env[0 | (ar1 << 1) | (br << 2) | (br1 << 3)] += e0;
-            env[1 | (ar1 << 1) | (br << 2) | (br1 << 3)] += e1;
-        }
-        // bucket (a, a', b, b') -> (u, v) of this factor
-        float eu[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const float v = warp_sum(env[k]);
-            const int a = k & 1, ap = (k >> 1) & 1, b = (k >> 2) & 1, bp = (k >> 3) & 1;
-            int u, vv;
-            if (par == 0) { u = a ^ bp; vv = ap ^ b; }
-            else { u = ap ^ b; vv = a ^ bp; }
-            eu[u + 2 * vv] += v;
-        }
-        if (r == 0) {
-            // <R|T|L> from the first factor (Euler: sum_k env_k w_k)
-            zloc = eu[0] * wq[0] + eu[1] * wq[1] + eu[2] * wq[2] + eu[3] * wq[3];
-        }
-        if (lane < 4) out[4 * r + lane] = zloc > 0.f ? eu[lane] / zloc : 0.f;
-        __syncwarp();
-        float* t = F0; F0 = F1; F1 = t;
-    }
-}
-
-struct GradArgs {
-    const double* dlogP;       // [B][4] upstream gradient, or nullptr
-    double* logP;              // [B][4] output, or nullptr
-    double* dnoise;            // [n][4] accumulated d L / d p_{q,P}
-    float* gws;                // per-warp workspace
-    int64_t per_warp;          // floats per warp
-};
-
-// Persistent adjoint kernel: each warp loops over units, accumulates its
-// share of dL/dp in FP64 in its workspace and adds it once at the end.
-__global__ void __launch_bounds__(128) grad_kernel(DecodeArgs a, GradArgs g) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int d = a.d, n = a.n;
-    const int full = 1 << (d + 1), size = full << 1;
-    float* base = g.gws + (size_t)gw * g.per_warp;
-    float* ws = base;                                   // sweep workspace (a.per_warp floats)
-    float* ckL = ws + a.per_warp;                       // (d-1) x full
-    float* ckR = ckL + (size_t)(d - 1) * full;          // (d-1) x full
-    float* xbuf = ckR + (size_t)(d - 1) * full;         // 2 x full
-    float* G = xbuf + 2 * full;                         // (d+1) x size
-    float* F0 = G + (size_t)(d + 1) * size;             // size
-    float* F1 = F0 + size;                              // size
-    float* ones = F1 + size;                            // full
-    float* out = ones + full;                           // 4d
-    double* acc = reinterpret_cast<double*>(out + ((4 * d + 1) & ~1));   // n x 4
-    for (int e = lane; e < 4 * n; e += 32) acc[e] = 0.0;
-    __syncwarp();
-    for (int64_t unit = gw; unit < 4 * a.B; unit += nw) {
-        const int64_t b = unit >> 2;
-        const int cls = (int)(unit & 3);
-        const double lz = decode_unit(a, ws, unit, lane, false, ckL, xbuf);
-        if (g.logP && lane == 0) g.logP[unit] = lz;
-        const double up = g.dlogP ? g.dlogP[unit] : 0.0;
-        if (!(lz > -INFINITY) || up == 0.0) { __syncwarp(); continue; }
-        decode_unit(a, ws, unit, lane, true, ckR, xbuf);
-        // the rotated run left the weights of the half-turn image, where the
-        // original qubit q sits at n-1-q (read that way below)
-        const float* wts = ws + a.off_w;
-        // representatives (original frame) to map (u, v) -> P
-        uint64_t sw[kMaxSynWords];
-        for (int w = 0; w < a.words; ++w) sw[w] = a.syn[b * a.words + w];
-        for (int c = 0; c < d; ++c) {
-            const float* L;
-            const float* R;
-            if (c == 0) {
-                for (int e = lane; e < full; e += 32) {
-                    int ok = 1;
-                    for (int i = 0; i <= d; ++i) ok &= !((e >> i) & 1) || plaquette_is_check(d, i, 0);
-                    ones[e] = ok ? 1.f : 0.f;
-                }
-                __syncwarp();
-                L = ones;
-            } else {
-                L = ckL + (size_t)(c - 1) * full;
-            }
-            // R over corner column c+1: the image's state after d-1-c columns
-            // (bits reversed: image row i is row d-i)
-            const int cp = d - 1 - c;
-            float* Rb = xbuf;
-            for (int e = lane; e < full; e += 32) {
-                int rev = 0;
-                for (int i = 0; i <= d; ++i) rev |= ((e >> i) & 1) << (d - i);
-                float v;
-                if (cp == 0) {
-                    int ok = 1;
-                    for (int i = 0; i <= d; ++i) ok &= !((e >> i) & 1) || plaquette_is_check(d, i, d);
-                    v = ok ? 1.f : 0.f;
-                } else {
-                    v = ckR[(size_t)(cp - 1) * full + rev];
-                }
-                Rb[e] = v;
-            }
-            __syncwarp();
-            R = Rb;
-            column_sandwich(d, c, L, R, wts, G, F0, F1, out, lane);
-            // dL/dp_{q,P} += up * dlnZ/dw_q[uv] with P = E_q xor X^u Z^v
-            for (int r = lane; r < d; r += 32) {
-                const int q = r * d + c;
-                int x = 0, z = 0;
-                const uint64_t* mk = a.dmask + (size_t)q * 2 * a.words;
-                for (int w = 0; w < a.words; ++w) {
-                    x ^= __popcll(sw[w] & mk[w]) & 1;
-                    z ^= __popcll(sw[w] & mk[a.words + w]) & 1;
-                }
-                if ((cls & 1) && c == 0) x ^= 1;
-                if ((cls & 2) && r == 0) z ^= 1;
-                for (int uv = 0; uv < 4; ++uv) {
-                    const int xx = x ^ (uv & 1), zz = z ^ (uv >> 1);
-                    const int pidx = (!xx && !zz) ? 0 : (xx && !zz) ? 1 : (xx && zz) ? 2 : 3;
-                    acc[4 * q + pidx] += up * (double)out[4 * r + uv];
-                }
-            }
-            __syncwarp();
-        }
-    }
-    __syncwarp();
-    for (int e = lane; e < 4 * n; e += 32)
-        if (acc[e] != 0.0) atomicAdd(g.dnoise + e, acc[e]);
 }
 
 __global__ void noise_check_kernel(const float* __restrict__ noise, int mode, int64_t count, int* status) {
@@ -1271,7 +1026,8 @@ mld_status mld_decode_grad(const mld_code* Cc, const float* noise, const uint64_
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return MLD_ERR_CUDA;
-    if (mld::grad_dense_supported(d)) {
+    if (!mld::grad_dense_supported(d)) return MLD_ERR_UNSUPPORTED;
+    {
         // dense states on chip: one block per (syndrome, class) unit
         const int64_t blocks = mld::grad_dense_blocks(d, sms, B);
         if (blocks < 1) return MLD_ERR_CUDA;
@@ -1296,50 +1052,6 @@ mld_status mld_decode_grad(const mld_code* Cc, const float* noise, const uint64_
         return mld::launch_grad_dense(d, ga, blocks, reinterpret_cast<cudaStream_t>(stream)) ? MLD_OK
                                                                                               : MLD_ERR_CUDA;
     }
-    const int64_t full = (int64_t)1 << (d + 1), size = full << 1;
-    const int64_t per_warp = P.floats_per_warp + 2 * (d - 1) * full + 2 * full + (d + 1) * size + 2 * size + full +
-                             ((4 * d + 1) & ~1) + 8 * n;
-    const int W = 4;
-    int64_t nw = (int64_t)sms * 16;
-    const int64_t need = ((4 * B + W - 1) / W) * W;
-    if (nw > need) nw = need;
-    const size_t bytes = (size_t)nw * per_warp * sizeof(float);
-    if (bytes > C->gradws_bytes) {
-        cudaFree(C->d_gradws);
-        C->d_gradws = nullptr;
-        C->gradws_bytes = 0;
-        if (cudaMalloc(&C->d_gradws, bytes) != cudaSuccess) return MLD_ERR_NOMEM;
-        C->gradws_bytes = bytes;
-    }
-    mld::DecodeArgs a;
-    a.steps = pd->d_steps;
-    a.gws = nullptr;
-    a.dmask = C->d_dmask;
-    a.noise = noise;
-    a.syn = syn;
-    a.logP = nullptr;
-    a.status = C->d_status;
-    a.B = B;
-    a.d = d;
-    a.n = n;
-    a.words = C->words;
-    a.noise_mode = MLD_NOISE_TABLE;
-    a.off_w = P.off_w;
-    a.off_mps = P.off_mps;
-    a.off_buf0 = P.off_buf0;
-    a.off_buf1 = P.off_buf1;
-    a.off_q = P.off_q;
-    a.off_svd = P.off_svd;
-    a.per_warp = P.floats_per_warp;
-    for (int i = 0; i <= mld::kMaxD; ++i) a.init_sizes[i] = i <= d ? P.init_sizes[i] : 0;
-    mld::GradArgs g;
-    g.dlogP = dlogP;
-    g.logP = logP;
-    g.dnoise = dnoise;
-    g.gws = C->d_gradws;
-    g.per_warp = per_warp;
-    mld::grad_kernel<<<(unsigned)(nw / W), 32 * W, 0, reinterpret_cast<cudaStream_t>(stream)>>>(a, g);
-    return cudaGetLastError() == cudaSuccess ? MLD_OK : MLD_ERR_CUDA;
 }
 
 mld_status mld_decode_status(const mld_code* C) {

@@ -49,25 +49,32 @@ struct GradShape {
     static constexpr int SIZE = HALF << 1;          // states inside a column (one more bit)
     static constexpr int REST1 = SIZE >> 3;         // rests of a single step (eight entries each)
     static constexpr int REST2 = SIZE >> 4;         // rests of a pair step (sixteen entries each)
-    static constexpr int NT = REST2 >= 128 ? 128 : 32;
+    static constexpr int NT = REST2 >= 512 ? 512 : (REST2 >= 128 ? 128 : 32);
+    // d >= 11: one block fills an SM's shared memory, so L_c is read from the
+    // block's global slice, each step's environment sums are reduced at once,
+    // and the representative's bits are recomputed where they are needed
+    static constexpr bool BIG = D >= 11;
     static constexpr int NW = NT / 32;
     static constexpr int NG = (D + 1) / 2;          // stored G states: r = 0, 2, .., d-1
     // shared memory (floats)
     static constexpr int off_w = 0;                          // 4N factor weights (slot order Wp)
     static constexpr int off_g = (4 * N + 3) & ~3;           // NG states of SIZE
     static constexpr int off_l = off_g + NG * SIZE;           // HALF: L_c for the environment pass
-    static constexpr int off_ra = off_l + HALF;               // HALF: R_{c+1} (and staging)
+    static constexpr int off_ra = off_l + (BIG ? 0 : HALF);   // HALF: R_{c+1} (and staging)
     static constexpr int off_rb = off_ra + HALF;              // HALF: R_c being formed
-    static constexpr int off_red = off_rb + HALF;             // D x NW x 4 per-warp environment sums
-    static constexpr int off_env = off_red + D * NW * 4;      // D x 4 environments of a column
+    static constexpr int off_red = off_rb + HALF;             // per-warp environment sums:
+    static constexpr int RED = BIG ? NW * 8 : D * NW * 4;     //   of one step (BIG) or of the column
+    static constexpr int off_env = off_red + RED;             // D x 4 environments of a column
     static constexpr int off_misc = off_env + D * 4;          // 32: per-warp reductions
     static constexpr int off_rep = off_misc + 32;             // N ints: representative x + 2z
-    static constexpr int floats = off_rep + N;
+    static constexpr int floats = off_rep + (BIG ? 0 : N);
     static constexpr int lfloats = (D - 1) * HALF;            // global: L_1..L_{d-1}
     static constexpr int slice = lfloats + 8 * N;              // + the block's 4N double gradient sums
     // blocks per SM that shared memory allows (the register budget is held to it)
-    static constexpr int FIT = (227 * 1024) / (floats * 4 + 1024);
+    static constexpr int FIT0 = (227 * 1024) / (floats * 4 + 1024);
+    static constexpr int FIT = FIT0 < 1 ? 1 : FIT0;   // one block of up to 227 KB always fits
     static constexpr int MINB = FIT < 16 ? FIT : 16;
+    static_assert(floats * 4 <= 227 * 1024, "a block's shared memory is at most 227 KB");
 };
 
 // G state slot of the state before factor r (r even, or r = d).
@@ -321,13 +328,13 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
     float* sm = reinterpret_cast<float*>(smem4);
     float* wts = sm + S::off_w;
     float* G = sm + S::off_g;              // G + gslot(r) * SIZE: the state before factor r
-    float* Lb = sm + S::off_l;
+    float* Lb = sm + S::off_l;             // (d <= 9 only)
     float* Rcur = sm + S::off_ra;
     float* Rnxt = sm + S::off_rb;
     float* red = sm + S::off_red;
     float* env = sm + S::off_env;
     float* misc = sm + S::off_misc;
-    int* rep = reinterpret_cast<int*>(sm + S::off_rep);
+    int* rep = reinterpret_cast<int*>(sm + S::off_rep);   // (d <= 9 only)
     float* Lg = g.lws + (size_t)blockIdx.x * S::slice;
     double* acc = reinterpret_cast<double*>(Lg + S::lfloats);   // this block's dL/dp, summed in unit order
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -361,7 +368,7 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
                 const int xx = x ^ (uv & 1), zz = z ^ (uv >> 1);
                 wts[4 * q + j] = row[xx ? (zz ? 2 : 1) : (zz ? 3 : 0)];
             }
-            rep[q] = x + 2 * z;
+            if constexpr (!S::BIG) rep[q] = x + 2 * z;
         }
         {
             const int pm0 = present_rows<D>(0);
@@ -440,7 +447,7 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
             for (int bi = tid; bi < HALF; bi += NT) Rcur[bi] = (bi & ~pmd) == 0 ? 1.f : 0.f;   // R_d
         }
         for (int c = D - 1; c >= 0; --c) {
-            {
+            if constexpr (!S::BIG) {
                 const int pm0 = present_rows<D>(0);
                 for (int bi = tid; bi < HALF; bi += NT)
                     Lb[bi] = c == 0 ? ((bi & ~pm0) == 0 ? 1.f : 0.f) : Lg[(c - 1) * HALF + bi];
@@ -513,7 +520,11 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
 #pragma unroll
                         for (int m = 0; m < 16; ++m) {
                             const int lg = core | (m & 7) | ((m >> 3) << (D + 1));
-                            X[m] = Lb[left_index<D>(lg)];
+                            const int li = left_index<D>(lg);
+                            if constexpr (S::BIG)
+                                X[m] = c == 0 ? ((li & ~present_rows<D>(0)) == 0 ? 1.f : 0.f) : Lg[(c - 1) * HALF + li];
+                            else
+                                X[m] = Lb[li];
                             Gz[m] = Gn[o2[m]];
                         }
                     } else {
@@ -547,23 +558,43 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
                 const float tot = reduce_scatter8(e, lane);
                 if ((lane & 3) == 0) {
                     const int slot = lane >> 2;
-                    red[((r + (slot >> 2)) * NW + warp) * 4 + (slot & 3)] = tot;
+                    if constexpr (S::BIG) red[warp * 8 + slot] = tot;
+                    else red[((r + (slot >> 2)) * NW + warp) * 4 + (slot & 3)] = tot;
                 }
                 __syncthreads();
+                if constexpr (S::BIG) {
+                    if (tid < 8) {
+                        float sum = 0.f;
+                        for (int w = 0; w < NW; ++w) sum += red[w * 8 + tid];
+                        env[(r + (tid >> 2)) * 4 + (tid & 3)] = sum;
+                    }
+                    __syncthreads();
+                }
                 Fa = Fb;
             }
             {
                 float e[4] = {0.f, 0.f, 0.f, 0.f};
                 for (int rs = tid; rs < S::REST1; rs += NT) single_environment<D, true>(Fa, Rcur, D - 1, rs, e);
                 const float tot = reduce_scatter4(e, lane);
-                if ((lane & 7) == 0) red[((D - 1) * NW + warp) * 4 + (lane >> 3)] = tot;
+                if ((lane & 7) == 0) {
+                    if constexpr (S::BIG) red[warp * 8 + (lane >> 3)] = tot;
+                    else red[((D - 1) * NW + warp) * 4 + (lane >> 3)] = tot;
+                }
                 __syncthreads();
             }
-            for (int t = tid; t < D * 4; t += NT) {
-                float s = 0.f;
+            if constexpr (S::BIG) {
+                if (tid < 4) {
+                    float sum = 0.f;
+                    for (int w = 0; w < NW; ++w) sum += red[w * 8 + tid];
+                    env[(D - 1) * 4 + tid] = sum;
+                }
+            } else {
+                for (int t = tid; t < D * 4; t += NT) {
+                    float s = 0.f;
 #pragma unroll
-                for (int w = 0; w < NW; ++w) s += red[((t >> 2) * NW + w) * 4 + (t & 3)];
-                env[t] = s;
+                    for (int w = 0; w < NW; ++w) s += red[((t >> 2) * NW + w) * 4 + (t & 3)];
+                    env[t] = s;
+                }
             }
             __syncthreads();
             // dZ/dp_{q,P} = env / <R|T|L>, with <R|T|L> = sum_j env_j Wp_j of factor 0
@@ -577,7 +608,23 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
                 const bool par = ((r + c) & 1) != 0;
                 const float eu = env[4 * r + (par ? ((uv & 1) << 1) | (uv >> 1) : uv)];
                 if (zc > 0.f) {
-                    const int q = r * D + c, xx = (rep[q] & 1) ^ (uv & 1), zz = (rep[q] >> 1) ^ (uv >> 1);
+                    const int q = r * D + c;
+                    int rx, rz;
+                    if constexpr (S::BIG) {
+                        rx = 0; rz = 0;
+                        const uint64_t* mk = g.dmask + (size_t)q * 2 * g.words;
+                        for (int w = 0; w < g.words; ++w) {
+                            const uint64_t sw = g.syn[b * g.words + w];
+                            rx ^= __popcll(sw & mk[w]) & 1;
+                            rz ^= __popcll(sw & mk[g.words + w]) & 1;
+                        }
+                        if ((cls & 1) && c == 0) rx ^= 1;
+                        if ((cls & 2) && r == 0) rz ^= 1;
+                    } else {
+                        rx = rep[q] & 1;
+                        rz = rep[q] >> 1;
+                    }
+                    const int xx = rx ^ (uv & 1), zz = rz ^ (uv >> 1);
                     acc[4 * q + (xx ? (zz ? 2 : 1) : (zz ? 3 : 0))] += up * (double)(eu / zc);
                 }
             }
@@ -638,7 +685,7 @@ bool launch_d(const GradDenseArgs& a, int64_t blocks, cudaStream_t s) {
 
 }  // namespace
 
-bool grad_dense_supported(int d) { return d == 3 || d == 5 || d == 7 || d == 9; }
+bool grad_dense_supported(int d) { return d == 3 || d == 5 || d == 7 || d == 9 || d == 11; }
 
 int64_t grad_dense_blocks(int d, int sms, int64_t B) {
     switch (d) {
@@ -646,6 +693,7 @@ int64_t grad_dense_blocks(int d, int sms, int64_t B) {
         case 5: return blocks_d<5>(sms, B);
         case 7: return blocks_d<7>(sms, B);
         case 9: return blocks_d<9>(sms, B);
+        case 11: return blocks_d<11>(sms, B);
     }
     return 0;
 }
@@ -656,6 +704,7 @@ int64_t grad_dense_workspace_floats(int d) {
         case 5: return GradShape<5>::slice;
         case 7: return GradShape<7>::slice;
         case 9: return GradShape<9>::slice;
+        case 11: return GradShape<11>::slice;
     }
     return 0;
 }
@@ -666,6 +715,7 @@ bool launch_grad_dense(int d, const GradDenseArgs& a, int64_t blocks, cudaStream
         case 5: return launch_d<5>(a, blocks, s);
         case 7: return launch_d<7>(a, blocks, s);
         case 9: return launch_d<9>(a, blocks, s);
+        case 11: return launch_d<11>(a, blocks, s);
     }
     return false;
 }
