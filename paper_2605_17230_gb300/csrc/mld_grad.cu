@@ -1,10 +1,10 @@
-// Dense adjoint of the untruncated sweep, d = 3..9: d ln Z_l / d p_{q,P}.
+// Dense adjoint of the untruncated sweep, d = 3..11: d ln Z_l / d p_{q,P}.
 // (Each block sums its units' gradients in a fixed order and a second
 // kernel adds the blocks' sums in block order: reruns are bit-identical.)
 //
 // Z is linear in every qubit factor, so dZ/dw_q is the environment of that
 // factor (Sec. 3.2.4: the contraction is differentiable in the local error
-// probabilities, which the estimation of Eq. 10 back-propagates). For d <= 9
+// probabilities, which the estimation of Eq. 10 back-propagates). For d <= 11
 // the exact boundary state over one corner column has at most 2^(d+1)
 // entries (one plaquette variable per row, absent plaquettes pinned to 0), so
 // the states are kept dense on chip. One thread block owns one (syndrome,
