@@ -60,3 +60,48 @@ def test_invalid_distance_rejected():
     for d in (1, 2, 4, 27):
         with pytest.raises(mld.MldError):
             mld.Code(d)
+
+
+def test_host_side_argument_checks():
+    """Errors the host can see are returned before anything touches a
+    device (so they run here without a GPU): bad mechanisms, sizes, chi,
+    precision, noise mode, missing or misaligned pointers, distances beyond a
+    path's range. B = 0 with valid arguments is a no-op."""
+    import ctypes
+    lib = mld.load()
+    P = ctypes.c_void_p
+    OK, INVALID, UNSUPPORTED = 0, 1, 2
+    c5, c11, c13 = mld.Code(5), mld.Code(11), mld.Code(13)
+    fake = P(4096)            # aligned, never dereferenced on these paths
+
+    def dem(code, q, c, p, n=None, B=0):
+        q = np.ascontiguousarray(q, np.int32)
+        c = np.ascontiguousarray(c, np.int32)
+        p = np.ascontiguousarray(p, np.float64)
+        f = lambda a: a.ctypes.data_as(P)
+        return lib.mld_decode_dem(P(code.handle), f(q), f(c), f(p), len(p) if n is None else n, fake, B, fake,
+                                  None, None)
+
+    assert dem(c5, [0, 24], [1, 3], [0.1, 1.0]) == OK
+    assert dem(c5, [], [], []) == OK
+    for q, c, p in (([25], [1], [0.1]), ([-1], [1], [0.1]), ([0], [0], [0.1]), ([0], [4], [0.1]),
+                    ([0], [1], [-0.1]), ([0], [1], [1.5]), ([0], [1], [np.nan])):
+        assert dem(c5, q, c, p) == INVALID, (q, c, p)
+    assert dem(c5, [0], [1], [0.1], n=-1) == INVALID
+    assert dem(c11, [0], [1], [0.1]) == UNSUPPORTED
+    # mld_decode(code, noise, mode, syn, B, chi, precision, logP, argmax, stream)
+    dec = lambda *a: lib.mld_decode(*a)
+    assert dec(P(c5.handle), fake, 0, fake, 0, 8, 0, fake, None, None) == OK
+    assert dec(P(c5.handle), fake, 0, fake, -1, 8, 0, fake, None, None) == INVALID
+    assert dec(P(c5.handle), fake, 0, fake, 4, 0, 0, fake, None, None) == INVALID        # chi < 1
+    assert dec(P(c5.handle), fake, 0, fake, 4, 8, 7, fake, None, None) == INVALID        # precision
+    assert dec(P(c5.handle), fake, 5, fake, 4, 8, 0, fake, None, None) == INVALID        # noise mode
+    assert dec(P(c5.handle), None, 0, fake, 4, 8, 0, fake, None, None) == INVALID        # no noise
+    assert dec(P(c5.handle), P(4100), 0, fake, 4, 8, 0, fake, None, None) == INVALID     # misaligned table
+    # mld_decode_grad(code, noise, syn, B, chi, dlogP, logP, dnoise, stream)
+    grad = lambda *a: lib.mld_decode_grad(*a)
+    assert grad(P(c5.handle), fake, fake, 0, 8, None, None, fake, None) == OK
+    assert grad(P(c5.handle), fake, fake, -1, 8, None, None, fake, None) == INVALID
+    assert grad(P(c5.handle), fake, fake, 4, 0, None, None, fake, None) == INVALID
+    assert grad(P(c5.handle), fake, fake, 4, 8, None, None, None, None) == INVALID       # no dnoise
+    assert grad(P(c13.handle), fake, fake, 4, 64, None, None, fake, None) == UNSUPPORTED
