@@ -400,3 +400,127 @@ def test_mechanism_sampler_matches_composed_table():
         f = np.bincount(code_to_row[E[:, qq]], minlength=4) / B
         sig = np.sqrt(tab[qq] * (1 - tab[qq]) / B)
         assert (np.abs(f - tab[qq]) <= 5 * sig + 1e-12).all(), (qq, f, tab[qq])
+
+
+# --- the boundary-MPS mode at truncated chi, against dense cut truncations ---
+
+def _dense_column_transfer(d, psi, noise, E, c):
+    """psi'(beta) = sum_alpha psi(alpha) prod_r w_r(alpha_r, alpha_r+1, beta_r, beta_r+1)
+    over corner columns c (alpha) and c+1 (beta), every position binary (an
+    absent plaquette's variable is pinned to 0 by zero entries). The qubit
+    factor of (r, c) is p_q[E_q xor X^u Z^v], u (v) the XOR of the variables of
+    its X-type (Z-type) corner plaquettes (Eq. 7, generator picture). Written
+    here from the layout of synth, not from the oracle."""
+    L = d + 1
+    idx = np.arange(1 << L)
+    bits = (idx[:, None] >> (L - 1 - np.arange(L))[None, :]) & 1      # position 0 = most significant
+    a = bits[None, :, :]                                               # alpha [1, S, L]
+    b = bits[:, None, :]                                               # beta  [S, 1, L]
+    code_of = np.array([[0, 3], [1, 2]])                              # noise column of (x, z)
+    T = np.ones((1 << L, 1 << L))
+    for r in range(d):
+        q = r * d + c
+        u = np.zeros_like(T, dtype=np.int64)
+        v = np.zeros_like(T, dtype=np.int64)
+        for (i, j), var in (((r, c), a[..., r]), ((r + 1, c), a[..., r + 1]),
+                            ((r, c + 1), b[..., r]), ((r + 1, c + 1), b[..., r + 1])):
+            if not synth._present(d, i, j):
+                continue
+            if (i + j) % 2 == 0:
+                u = u ^ var
+            else:
+                v = v ^ var
+        x = (int(E[q]) & 1) ^ u
+        z = ((int(E[q]) >> 1) & 1) ^ v
+        T *= noise[q][code_of[x, z]]
+    pres_b = np.array([synth._present(d, i, c + 1) for i in range(L)])
+    keep = np.all(bits[:, ~pres_b] == 0, axis=1)                      # beta of absent positions = 0
+    return (T @ psi) * keep
+
+
+def _dense_truncated_logz(d, noise, E, chi, gaps):
+    """ln Z of the boundary-MPS rule computed on the dense state: after each
+    column, cut by cut from the last bond to the first, the best rank-chi
+    approximation (Eckart-Young, numpy SVD) of the full 2^(d+1) vector
+    matricised at that cut. The right-to-left SVD sweep of a left-canonical
+    MPS performs exactly this sequence of projections."""
+    L = d + 1
+    idx = np.arange(1 << L)
+    bits = (idx[:, None] >> (L - 1 - np.arange(L))[None, :]) & 1
+    pres = np.array([synth._present(d, i, 0) for i in range(L)])
+    psi = np.all(bits[:, ~pres] == 0, axis=1).astype(np.float64)
+    log_scale = 0.0
+    for c in range(d):
+        psi = _dense_column_transfer(d, psi, noise, E, c)
+        for k in range(L - 2, -1, -1):                                # cut between positions k, k+1
+            M = psi.reshape(1 << (k + 1), 1 << (L - 1 - k))
+            U, S, Vh = np.linalg.svd(M, full_matrices=False)
+            if chi < len(S) and S[chi] > 1e-12 * S[0]:
+                gaps.append((S[chi - 1] - S[chi]) / S[chi - 1])
+            kk = min(chi, len(S))
+            psi = ((U[:, :kk] * S[:kk]) @ Vh[:kk]).reshape(-1)
+        m = np.abs(psi).max()
+        psi = psi / m
+        log_scale += math.log(m)
+    return math.log(psi.sum()) + log_scale
+
+
+def _posterior(x):
+    return np.exp(x - np.logaddexp.reduce(x, axis=1, keepdims=True))
+
+
+def _mps_and_dense(d, chi, seed):
+    n = d * d
+    noise = synth.lognormal_biased(n, seed=seed, median=0.15)
+    syn = synth.syndromes_of(d, synth.sample_errors(d, noise, 2, seed=41))
+    reps = oracle.representatives(d, syn)
+    gaps = []
+    ref = np.array([[_dense_truncated_logz(d, noise, reps[b, l], chi, gaps) for l in range(4)]
+                    for b in range(len(syn))])
+    got = np.array([[omps.coset_logz_mps(d, noise, reps[b, l], chi) for l in range(4)]
+                    for b in range(len(syn))])
+    return ref, got, gaps
+
+
+@pytest.mark.parametrize("d,chi", [(5, 2), (5, 3), (7, 4), (7, 6)])
+def test_mps_mode_truncation_equals_dense_cut_truncations(d, chi):
+    """At truncated chi the boundary-MPS mode (left QR sweep, then right-to-left
+    SVD keeping min(chi, #values), Sec. 3.2.1) equals, column by column, the
+    dense transfer followed by the optimal rank-chi truncation of the dense
+    state at every cut from the last to the first. Per-qubit noise keeps the
+    singular values at each cut apart (relative gap at the cut above 1e-3),
+    so the truncation is unique; rates near 0.15 make the discarded weight
+    matter. Both sides round in FP64 relative to the largest coset, so the
+    bar is 1e-10 on the leading coset's ln Z and on the posterior Pr(l|s)."""
+    ref, got, gaps = _mps_and_dense(d, chi, 40 + d)
+    assert gaps and min(gaps) > 1e-3                          # no tie at any cut
+    lead = np.argmax(ref, axis=1)
+    rows = np.arange(len(ref))
+    assert np.abs(got[rows, lead] - ref[rows, lead]).max() < 1e-10
+    assert np.abs(_posterior(got) - _posterior(ref)).max() < 1e-10
+
+
+def test_dense_cut_pin_detects_a_missing_canonical_sweep(monkeypatch):
+    """The pin above has the power to catch a plausible mistake: truncating the
+    applied MPS by right-to-left SVDs without first bringing it to
+    left-canonical form (a sub-optimal truncation that still converges in
+    chi) moves the leading ln Z and the posterior far beyond the pin's 1e-10
+    (by 1e-3 to 1e-1 on these cases)."""
+
+    def compress_without_qr(mps, chi_):
+        mps = [t.copy() for t in mps]
+        for i in range(len(mps) - 1, 0, -1):
+            l, p, r = mps[i].shape
+            U, S, Vh = np.linalg.svd(mps[i].reshape(l, p * r), full_matrices=False)
+            k = min(chi_, S.shape[0])
+            mps[i] = Vh[:k].reshape(k, p, r)
+            mps[i - 1] = np.einsum("lpa,ab->lpb", mps[i - 1], U[:, :k] * S[:k])
+        return mps
+
+    monkeypatch.setattr(omps, "compress", compress_without_qr)
+    for d, chi in [(5, 2), (7, 4)]:
+        ref, got, _ = _mps_and_dense(d, chi, 40 + d)
+        lead = np.argmax(ref, axis=1)
+        rows = np.arange(len(ref))
+        assert max(np.abs(got[rows, lead] - ref[rows, lead]).max(),
+                   np.abs(_posterior(got) - _posterior(ref)).max()) > 1e-4
