@@ -2,10 +2,16 @@
 
 Workload (one "step"): decode 65,536 seeded syndromes of the d=9 rotated code
 under depolarizing p=0.10 at bond dimension chi=32 (4 coset log-probabilities
-each, plus the argmax): the whole hot path (pure error, column MPO.MPS
-products, QR/SVD compression, power-of-two renormalisation, final contraction,
-argmax) in one mld_decode call on inputs resident in HBM. Synthetic inputs:
-errors drawn from the counter generator in synth/, syndromes extracted.
+each, plus the argmax) in one mld_decode call on inputs resident in HBM. At
+this point chi is at or above the exact bond 2^floor(9/2) = 16, so no
+singular value is discarded: the step is the pure error, the column MPO.MPS
+products, power-of-two renormalisation, the final contraction and the argmax
+(no QR or SVD runs). Synthetic inputs: errors drawn from the counter
+generator in synth/, syndromes extracted.
+
+Other workloads (--workload): mixed (the d=3..13 graph batch), large (d=17
+and 25 at truncating chi), ler (logical-error rates of the d/p grid against
+the oracle), grad, dmle, dem.
 
 Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle
 on the host cores instead (a bounded sample per step).
@@ -31,13 +37,12 @@ import synth  # noqa: E402
 D, CHI, P, B = 9, 32, 0.10, 65536
 SEED = synth.config_seed(1, D, P)
 L2_FLUSH_BYTES = 256 << 20
-SM_COUNT_NOMINAL = 152
-FP32_LANES_PER_SM = 128
 METRIC = "syndromes/s at d=9 χ=32 (4 cosets), mixed-precision vs FP32, |ΔlogP|≤1e-3"
+TF32_PER_BF16 = 1.1 / 2.25          # nominal dense TF32 / BF16 tensor rates of GB300
 
 # DRAM bytes per syndrome of the decode kernel (dram__bytes_read.sum + write.sum of one ncu
-# capture of 8,192 syndromes, profiles/decode_exact_d9_chi32_full.md), valid only for the kernel
-# sources they were taken on: any change to them makes the traffic unknown (null).
+# capture of 8,192 syndromes of the headline kernel), valid only for the kernel sources they
+# were taken on: any change to them makes the traffic unknown (null).
 TRAFFIC_SOURCES_SHA = "3d9a42386b4f2832"
 TRAFFIC_BYTES_PER_SYNDROME = {0: (282.880e3 + 0.512e3) / 8192, 2: (284.672e3 + 3.328e3) / 8192}
 
@@ -55,6 +60,26 @@ def kernel_sources_sha():
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def _measured_peaks():
+    """The driver-written measured peaks of this machine's GPUs, if present."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def wilson_interval(k, n, z=1.959963984540054):
+    """Wilson score interval of a binomial proportion k/n (95% by default)."""
+    if n == 0:
+        return (0.0, 1.0)
+    ph = k / n
+    den = 1.0 + z * z / n
+    c = (ph + z * z / (2 * n)) / den
+    h = z * ((ph * (1 - ph) / n + z * z / (4 * n * n)) ** 0.5) / den
+    return (max(0.0, c - h), min(1.0, c + h))
 
 
 def _env_int(k, dflt):
@@ -135,17 +160,31 @@ class Clocks:
 
 def cpu_baseline(sample=B):
     """The FP64 oracle (exact dense contraction, OpenMP over syndromes) on
-    the host cores, on a bounded sample of the same workload."""
+    the host cores, on a bounded sample of the same workload; the same on one
+    core, and the oracle's FP64 boundary-MPS mode (the plain method of Sec.
+    3.2.1 in numpy, at the same chi) on a few syndromes."""
     import oracle
+    import oracle.mps as omps
     noise, syn = workload(sample, 0)
     oracle.decode(D, noise, syn[:64])                  # warm-up
     cores = os.cpu_count() or 1
     t = time.perf_counter()
     oracle.decode(D, noise, syn, threads=cores)
     dt = time.perf_counter() - t
+    one = min(sample, 2048)
+    t = time.perf_counter()
+    oracle.decode(D, noise, syn[:one], threads=1)
+    dt1 = time.perf_counter() - t
+    nm = 4
+    t = time.perf_counter()
+    omps.decode_mps(D, noise.astype(np.float64), syn[:nm], CHI, xl_column=D - 1)
+    dtm = time.perf_counter() - t
     return {"value": sample / dt, "unit": "syndromes/s", "cores": cores, "kind": "oracle",
             "sample": f"{sample} of the {B} d=9 p=0.10 syndromes (rank 0's batch), exact FP64 dense "
-                      f"contraction, {dt:.1f} s wall on {cores} threads"}
+                      f"contraction, {dt:.1f} s wall on {cores} threads",
+            "one_core_value": one / dt1, "one_core_sample": f"first {one} syndromes, 1 thread",
+            "mps_mode_value": nm / dtm,
+            "mps_mode_sample": f"first {nm} syndromes, FP64 boundary MPS at chi={CHI} (numpy QR/SVD), 1 process"}
 
 
 def run_reference(args, rank, world):
@@ -239,64 +278,126 @@ def run_mixed(args):
     print(json.dumps(line), flush=True)
 
 
-# Truncating points (chi below the exact bond 2^floor(d/2)): (d, chi, syndromes per point).
-# The large-d points decode one wave of resident warps each (the kernel keeps one
-# (syndrome, l_Z) per warp in a global-memory workspace: 2,432 warps, 1,216 syndromes),
-# a bounded sample of the 16,384-syndrome workload.
-LARGE_POINTS = [(9, 8, 65536), (11, 16, 16384), (17, 32, 1216), (17, 64, 1216), (25, 32, 1216)]
-LARGE_POINTS_ALL = LARGE_POINTS + [(17, 128, 952), (25, 64, 1048), (25, 128, 308)]
+def _hist_summary(h):
+    tot = int(h.sum())
+    if tot == 0:
+        return None
+    ks = np.arange(len(h))
+    cdf = np.cumsum(h) / tot
+    return {"cuts": tot, "mean": float((h * ks).sum() / tot), "p99": int(np.searchsorted(cdf, 0.99)),
+            "max": int(ks[h > 0].max()), "last_bin_is_64_or_more": True}
+
+
+def _posterior(x):
+    return np.exp(x - np.logaddexp.reduce(x, axis=1, keepdims=True))
 
 
 def run_large(args):
-    """Truncated chi: d=9 chi=8 and d=11 chi=16 (the truncating points of the d/p grid), and
-    d=17, 25 at chi 32..128 under depolarizing p=0.12 and biased noise (eta=100, p=0.12).
-    Reports syndromes/s per point and, where the untruncated kernel runs (d <= 13), the error of
-    the leading coset's ln Z and of the posterior Pr(l|s) on a sample against the same syndromes
-    decoded at the exact bond dimension 2^floor(d/2) (whose parity with the FP64 oracle the test
-    suite checks)."""
+    """The scale workload: rotated d=17 and 25, depolarizing p=0.12 and biased eta=100 (p=0.12),
+    16,384 syndromes per point (seed config_seed(5, d, 0.12)), chi = 32, 64, 128. Every point reports
+    syndromes/s, the executed flops rate, the kept-bond histogram of the rank-adaptive truncation,
+    the logical-error rate with its 95% Wilson interval, and the largest change of the leading
+    coset's ln Z and of the posterior against the chi=128 run of the same syndromes."""
     import torch
     import paper_2605_17230_gb300 as mld
-    pts = LARGE_POINTS_ALL if args.large_all else LARGE_POINTS
+    Bl = args.large_batch
+    chis = (32, 64, 128)
     out = []
-    for d, chi, B in pts:
+    for d in (17, 25):
         code = mld.Code(d)
         n = d * d
         for name, noise in (("depolarizing p=0.12", synth.depolarizing(n, 0.12)),
                             ("biased eta=100 p=0.12", synth.biased(n, 0.12, 100.0))):
             noise = noise.astype(np.float32)
-            E = synth.sample_errors(d, noise, B, seed=synth.config_seed(5, d, 0.12))
+            E = synth.sample_errors(d, noise, Bl, seed=synth.config_seed(5, d, 0.12))
+            true = synth.true_class(d, E)
+            nz = torch.tensor(noise, device="cuda")
+            sy = torch.tensor(synth.syndromes_of(d, E).view(np.int64), device="cuda")
+            res = {}
+            for chi in chis[::-1]:
+                code.decode(nz, sy[:256], chi)                     # warm-up: workspaces
+                torch.cuda.synchronize()
+                code.executed_flops()
+                code.bond_histogram()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                lp, am = code.decode(nz, sy, chi)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                st = code.status()
+                if st != 0:
+                    raise RuntimeError("device status: " + mld.mld_status_string(st))
+                res[chi] = (lp.cpu().numpy(), am.cpu().numpy(), ms, code.executed_flops(), code.bond_histogram())
+            ref = res[128][0]
+            lead = np.argmax(ref, axis=1)
+            rows = np.arange(Bl)
+            for chi in chis:
+                lp, am, ms, fl, h = res[chi]
+                k = int((am != true).sum())
+                rec = {"d": d, "chi": chi, "noise": name, "syndromes": Bl, "ms": ms,
+                       "syndromes_per_s": Bl / (ms / 1e3), "executed_tflops": fl / ms / 1e9,
+                       "bonds": _hist_summary(h), "ler": k / Bl, "ler_ci95": wilson_interval(k, Bl),
+                       "max_abs_dlogP_leading_vs_chi128": float(np.abs(lp[rows, lead] - ref[rows, lead]).max()),
+                       "max_abs_dposterior_vs_chi128": float(np.abs(_posterior(lp) - _posterior(ref)).max()),
+                       "argmax_equals_chi128": float(np.mean(am == res[128][1]))}
+                out.append(rec)
+                print(json.dumps(rec), flush=True)
+        code.close()
+    print(json.dumps({"metric": "syndromes/s at truncating chi (rank-adaptive sweep)", "workload": "large",
+                      "points": out, "data": "synthetic", "dtype": "f32",
+                      "cutoff": "singular values <= 1e-7 sigma_1 discarded (default)"}), flush=True)
+
+
+def run_ler(args):
+    """Logical-error rates of the d/p grid (d = 5, 7, 9; depolarizing p = 0.05, 0.10, 0.15, 0.19;
+    65,536 syndromes each, seed config_seed(1, d, p)): the GPU decoder's LER at every distinct chi of
+    {8, 16, 32, exact} (chi >= 2^floor(d/2) is exact, so d = 5, 7 have the exact point only) and the
+    FP64 oracle's exact-MLD LER on the same syndromes, each with a 95% Wilson interval, and the
+    decisions that differ from the oracle where its two best cosets are more than 1e-4 apart in
+    ln Z (must be 0 at exact chi). The paper's optimal threshold of 18.9% (Sec. 2.2, Table 1) is the
+    context: below it the LER falls with d, near it the curves meet."""
+    import torch
+    import oracle
+    import paper_2605_17230_gb300 as mld
+    Bq = args.ler_batch
+    table = []
+    for d in (5, 7, 9):
+        code = mld.Code(d)
+        n = d * d
+        exact = 1 << (d // 2)
+        chis = sorted({min(c, exact) for c in (8, 16, 32, exact)})
+        for p in (0.05, 0.10, 0.15, 0.19):
+            noise = synth.depolarizing(n, p).astype(np.float32)
+            E = synth.sample_errors(d, noise, Bq, seed=synth.config_seed(1, d, p))
             syn = synth.syndromes_of(d, E)
+            true = synth.true_class(d, E)
+            ref, am_ref = oracle.decode(d, noise, syn, threads=os.cpu_count() or 1)
+            top = np.sort(ref, axis=1)
+            clear = top[:, -1] - top[:, -2] > 1e-4
+            k_ref = int((am_ref != true).sum())
             nz = torch.tensor(noise, device="cuda")
             sy = torch.tensor(syn.view(np.int64), device="cuda")
-            code.decode(nz, sy, chi, mld.MLD_FP32)          # warm-up: plan upload, workspace
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            lp, am = code.decode(nz, sy, chi, mld.MLD_FP32)
-            e1.record()
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1)
-            if code.status() != 0:
-                raise RuntimeError("device status: " + mld.mld_status_string(code.status()))
-            lp, am = lp.cpu().numpy(), am.cpu().numpy()
-            rec = {"d": d, "chi": chi, "noise": name, "syndromes": B, "ms": ms,
-                   "syndromes_per_s": B / (ms / 1e3),
-                   "argmax_equals_true_class": float(np.mean(am == synth.true_class(d, E)))}
-            if d <= 13:
-                k = 1024
-                ref_t, _ = code.decode(nz, sy[:k], 1 << (d // 2), mld.MLD_FP32)
-                ref = ref_t.cpu().numpy()
-                lead = np.argmax(ref, axis=1)
-                post = lambda x: np.exp(x - np.logaddexp.reduce(x, axis=1, keepdims=True))
-                rec.update({"exact_chi_sample": k,
-                            "max_abs_dlogP_leading_coset": float(np.abs(lp[np.arange(k), lead] -
-                                                                       ref[np.arange(k), lead]).max()),
-                            "max_abs_dposterior": float(np.abs(post(lp[:k]) - post(ref)).max()),
-                            "argmax_equals_exact_chi": float(np.mean(am[:k] == lead))})
-            out.append(rec)
-            print(json.dumps(rec), flush=True)
-    print(json.dumps({"metric": "syndromes/s at truncating chi", "workload": "large", "points": out,
-                      "data": "synthetic", "dtype": "f32"}), flush=True)
+            for chi in chis:
+                lp, am = code.decode(nz, sy, chi)
+                torch.cuda.synchronize()
+                am = am.cpu().numpy()
+                k = int((am != true).sum())
+                rec = {"d": d, "p": p, "chi": chi, "exact": chi >= exact, "syndromes": Bq,
+                       "ler_gpu": k / Bq, "ler_gpu_ci95": wilson_interval(k, Bq),
+                       "ler_oracle_exact": k_ref / Bq, "ler_oracle_ci95": wilson_interval(k_ref, Bq),
+                       "non_tie_decisions_differing_from_oracle": int((am[clear] != am_ref[clear]).sum()),
+                       "ties": int((~clear).sum())}
+                table.append(rec)
+                print(json.dumps(rec), flush=True)
+        code.close()
+    exact_rows = {(r["d"], r["p"]): r["ler_oracle_exact"] for r in table}
+    ordering = {f"p={p}": [exact_rows[(d, p)] for d in (5, 7, 9)] for p in (0.05, 0.10, 0.15, 0.19)}
+    print(json.dumps({"metric": "logical-error rates, GPU vs FP64 oracle (exact MLD)", "workload": "ler",
+                      "table": table, "oracle_ler_by_d_5_7_9": ordering,
+                      "tolerance": "decisions equal to the oracle's wherever its top two cosets differ by "
+                                   "more than 1e-4 in ln Z; 0 mismatches required at exact chi",
+                      "data": "synthetic"}), flush=True)
 
 
 def run_grad(args):
@@ -427,14 +528,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=B, help="syndromes per GPU per step (default: the "
                     "65536 of the workload; smaller values only for profiling captures)")
-    ap.add_argument("--workload", default="metric", choices=["metric", "mixed", "grad", "large", "dmle", "dem"],
+    ap.add_argument("--workload", default="metric",
+                    choices=["metric", "mixed", "grad", "large", "ler", "dmle", "dem"],
                     help="metric: the headline d=9 line (default); mixed: the 1,048,576-syndrome mixed-d "
                          "graph batch; grad: the adjoint on the d=7 workload; dmle: full-batch noise "
                          "estimation from 1,048,576 unlabelled d=9 syndromes; dem: detector-picture decode of "
-                         "a d=9 X/Y/Z mechanism model; large: truncating chi "
-                         "(d=9 chi=8, d=11 chi=16, and samples of d=17, 25 at chi 32..128)")
-    ap.add_argument("--large-all", action="store_true", help="with --workload large: also the slow "
-                    "points (d=17 chi=128, d=25 chi=64 and 128)")
+                         "a d=9 X/Y/Z mechanism model; large: d=17, 25 at chi 32..128 (truncating); "
+                         "ler: logical-error rates of the d/p grid against the oracle")
+    ap.add_argument("--large-batch", type=int, default=16384)
+    ap.add_argument("--ler-batch", type=int, default=65536)
     ap.add_argument("--mixed-total", type=int, default=1 << 20)
     args = ap.parse_args()
     rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)
@@ -451,6 +553,8 @@ def main():
         return run_dem(args) if rank == 0 else None
     if args.workload == "large":
         return run_large(args) if rank == 0 else None
+    if args.workload == "ler":
+        return run_ler(args) if rank == 0 else None
 
     import torch
     import paper_2605_17230_gb300 as mld
@@ -545,10 +649,15 @@ def main():
 
     # roofline of the dominant kernel (the fused decode kernel): counted flops
     # of the executed schedule / its CUDA-event time (the argmax kernel is
-    # < 1% of the step and is included in the timing)
+    # < 1% of the step and is included in the timing), against the FP32 FMA
+    # rate measured on this GPU by an FFMA microbenchmark (outside the timed
+    # region); the tensor fraction sets the same flops against the dense TF32
+    # rate (the measured BF16 cuBLAS peak scaled by the nominal TF32/BF16 ratio)
     flops_per_syn = code.flops(CHI, prec_mixed)
     achieved = Bn * flops_per_syn / (statistics.median(ms) / 1e3) / 1e12
-    peak = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    peak, sms = mld.mld_measure_fp32_peak(2.0)
+    peaks = _measured_peaks()
+    bf16 = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
     traffic = (TRAFFIC_BYTES_PER_SYNDROME[prec_mixed] * Bn
                if kernel_sources_sha() == TRAFFIC_SOURCES_SHA and prec_mixed in TRAFFIC_BYTES_PER_SYNDROME
                else None)
@@ -567,10 +676,12 @@ def main():
         "mixed_vs_fp32_max_abs_dlogP": dlogp,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "note": "FP32 FFMA pipe: 152 SMs x 128 lanes x 2 flop x 2070 MHz; achieved = counted "
-                             "flops of the executed sweep schedule / kernel time; traffic = DRAM bytes per "
-                             "launch (ncu capture of 8,192 syndromes scaled by the syndrome count; null "
-                             "when the kernel sources differ from the captured ones)"},
+                     "peak_source": f"measured: FFMA microbenchmark on {sms} SMs (mld_measure_fp32_peak, 2 s)",
+                     "tensor_frac": (achieved / (bf16 * TF32_PER_BF16)) if bf16 else None,
+                     "tensor_peak_source": "measured BF16 cuBLAS peak (sustained) x nominal TF32/BF16 1.1/2.25",
+                     "note": "achieved = counted flops of the executed sweep schedule / kernel time; traffic = "
+                             "DRAM bytes per launch (ncu capture of 8,192 syndromes scaled by the syndrome "
+                             "count; null when the kernel sources differ from the captured ones)"},
         "e2e": {"value": e2e_val, "unit": "syndromes/s", "h2d_bytes_per_step": int(h_noise.numel() * 4 +
                                                                                      h_syn.numel() * 8),
                 "d2h_bytes_per_step": int(h_lp.numel() * 8 + h_am.numel())},

@@ -226,6 +226,30 @@ mld_status mld_decode_grad(const mld_code* code, const float* noise, const uint6
  * MLD_ERR_NUMERIC or MLD_ERR_TIMEOUT, in that order of precedence. */
 mld_status mld_decode_status(const mld_code* code);
 
+/* Relative cutoff of the truncating SVDs (Sec. 3.2.1 discards the smallest
+ * singular values; this sets which of them count as resolved). At every cut
+ * of a truncating chi the compression keeps the k largest singular values,
+ * k = min(chi, #{sigma_j > rel * sigma_1}). Default 1e-7: values below it lie
+ * under the FP32 resolution of the bond matrix, and dropping them lets the
+ * kernel run on the numerical rank of each cut (6..27 at p = 0.12, d = 17
+ * and 25) instead of chi. rel = 0 keeps min(chi, number of values) exactly.
+ * Applies to later decodes of this code object. MLD_ERR_INVALID_ARG unless
+ * 0 <= rel < 1. Host only. */
+mld_status mld_code_set_svd_cutoff(mld_code* code, double rel);
+
+/* Floating-point operations executed by the truncating sweeps of this code
+ * since the last call (apply, QR, Q applications and every Jacobi pair
+ * evaluation and rotation actually performed, counted on the device), then
+ * reset to zero. The caller synchronises the decode streams first. Untruncated
+ * decodes are not counted here (see mld_decode_flops). */
+mld_status mld_decode_executed_flops(const mld_code* code, double* flops);
+
+/* Histogram of the bonds kept at the truncating cuts of this code's decodes
+ * since the last call: hist[k] (k = 1..63) counts cuts that kept k singular
+ * values, hist[64] those that kept 64 or more (rank-adaptive kernel only);
+ * then reset. The caller synchronises the decode streams first. */
+mld_status mld_decode_bond_histogram(const mld_code* code, int64_t* hist /* [65] */);
+
 /* Counted floating-point operations per syndrome (all four classes) of the
  * sweep schedule that mld_decode runs for this code, chi and precision: the
  * MPO.MPS products, the QR and Q applications of truncating columns and the
@@ -261,6 +285,13 @@ mld_status mld_decode_flops(const mld_code* code, int chi, int precision, double
 mld_status mld_decode_dem(const mld_code* code, const int32_t* mech_qubit, const int32_t* mech_pauli,
                           const double* mech_p, int32_t n_mech, const uint64_t* syndromes, int64_t B,
                           double* logP, uint8_t* argmax, void* stream);
+
+/* Measurement helper (not part of the method): times a kernel of independent
+ * FP32 FMA chains on every SM of the current device for about `seconds` and
+ * returns the sustained rate in TFLOP/s (2 flops per FMA) and the SM count,
+ * the denominator of the FP32 sweep kernels' roofline. Synchronous; allocates
+ * a small buffer. */
+mld_status mld_measure_fp32_peak(double seconds, double* tflops, int* sm_count);
 
 /* Number of kernel launches one mld_decode call with an argmax output makes
  * (the noise check, the sweep, the argmax; for accounting). */

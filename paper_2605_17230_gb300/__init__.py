@@ -34,7 +34,8 @@ EXPORTED_SYMBOLS = ["mld_code_create_rotated", "mld_code_destroy", "mld_code_inf
                     "mld_decode", "mld_decode_host", "mld_decode_status", "mld_decode_launches",
                     "mld_decode_flops", "mld_decode_noalloc", "mld_decode_batch", "mld_graph_create",
                     "mld_graph_launch", "mld_graph_destroy", "mld_autotune", "mld_decode_grad",
-                    "mld_decode_dem", "mld_status_string"]
+                    "mld_decode_dem", "mld_status_string", "mld_code_set_svd_cutoff",
+                    "mld_decode_executed_flops", "mld_decode_bond_histogram", "mld_measure_fp32_peak"]
 
 _lib = None
 
@@ -102,6 +103,14 @@ def load(build_if_missing: bool = True):
     lib.mld_decode_grad.restype = I
     lib.mld_decode_dem.argtypes = [P, P, P, P, I, P, L, P, P, P]
     lib.mld_decode_dem.restype = I
+    lib.mld_code_set_svd_cutoff.argtypes = [P, ctypes.c_double]
+    lib.mld_code_set_svd_cutoff.restype = I
+    lib.mld_decode_executed_flops.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+    lib.mld_decode_executed_flops.restype = I
+    lib.mld_decode_bond_histogram.argtypes = [P, P]
+    lib.mld_decode_bond_histogram.restype = I
+    lib.mld_measure_fp32_peak.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]
+    lib.mld_measure_fp32_peak.restype = I
     lib.mld_decode_launches.argtypes = []
     lib.mld_decode_launches.restype = I
     lib.mld_status_string.argtypes = [I]
@@ -163,6 +172,13 @@ def mld_decode_host(code, noise, noise_mode, syndromes, B, chi, precision, logP,
 
 def mld_decode_status(code) -> int:
     return load().mld_decode_status(ctypes.c_void_p(code))
+
+
+def mld_measure_fp32_peak(seconds=1.0):
+    """Sustained FP32 FMA rate of the current GPU (TFLOP/s) and its SM count."""
+    t, n = ctypes.c_double(), ctypes.c_int()
+    _check(load().mld_measure_fp32_peak(float(seconds), ctypes.byref(t), ctypes.byref(n)), "mld_measure_fp32_peak")
+    return t.value, n.value
 
 
 def mld_decode_launches() -> int:
@@ -253,8 +269,28 @@ class Code:
                "mld_decode_flops")
         return v.value
 
+    def bond_histogram(self):
+        """Kept bonds of truncating cuts since the last call: int64 [65]
+        (index k; the last bin counts k >= 64); resets the device histogram."""
+        h = np.zeros(65, np.int64)
+        _check(load().mld_decode_bond_histogram(ctypes.c_void_p(self.handle), h.ctypes.data_as(ctypes.c_void_p)),
+               "mld_decode_bond_histogram")
+        return h
+
     def status(self) -> int:
         return mld_decode_status(self.handle)
+
+    def set_svd_cutoff(self, rel: float):
+        """Relative singular-value cutoff of truncating chi (mld_code_set_svd_cutoff)."""
+        _check(load().mld_code_set_svd_cutoff(ctypes.c_void_p(self.handle), float(rel)), "mld_code_set_svd_cutoff")
+
+    def executed_flops(self) -> float:
+        """Flops executed by truncating sweeps since the last call (the
+        caller synchronises first); resets the device counter."""
+        v = ctypes.c_double()
+        _check(load().mld_decode_executed_flops(ctypes.c_void_p(self.handle), ctypes.byref(v)),
+               "mld_decode_executed_flops")
+        return v.value
 
 
 def make_jobs(items):

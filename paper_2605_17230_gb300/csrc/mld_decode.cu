@@ -18,6 +18,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -27,6 +28,7 @@
 #include "mld_dem.h"
 #include "mld_grad.h"
 #include "mld_internal.h"
+#include "mld_trunc.h"
 
 extern "C" mld_status mld_code_build_host(int d, mld_code** out);
 
@@ -51,6 +53,9 @@ struct DecodeArgs {
     int init_sizes[kMaxD + 1];
     float* qgws = nullptr;     // split mode: the kept tall blocks of each resident warp in global memory
     int64_t q_per_warp = 0;    // floats per warp of qgws
+    float cutoff = 0.f;        // singular values <= cutoff * sigma_1 of a bond matrix are discarded
+    const int64_t* ulist = nullptr;   // global mode: decode only these units (count at *ucount)
+    const int* ucount = nullptr;
 };
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -531,33 +536,38 @@ __device__ __forceinline__ double decode_unit(const DecodeArgs& a, float* ws, in
                     sig[k] = sqrtf(s2);
                 }
                 __syncwarp();
+                // the relative cutoff: values at or below cutoff * sigma_1 are
+                // discarded (their site rows and carry columns written as zero)
+                float smax = 0.f;
+                for (int k = lane; k < nv; k += 32) smax = fmaxf(smax, sig[k]);
+                const float sfloor = a.cutoff * warp_max(smax);
                 for (int k = lane; k < nv; k += 32) {
                     int rank = 0;
                     const float sk = sig[k];
                     for (int j = 0; j < nv; ++j) rank += (sig[j] > sk) || (sig[j] == sk && j < k);
-                    if (rank < Sl) perm[rank] = k;
+                    if (rank < Sl) perm[rank] = sk > sfloor ? k : -1;
                 }
                 __syncwarp();
                 if (tallT) {
                     // T = X V^T: site = V[:, top]^T (Sl x cols), carry = X[:, top]
                     for (int e = lane; e < Sl * cols; e += 32) {
                         const int s = e / cols, cc = e - s * cols;
-                        site[e] = acc[cc * nv + perm[s]];
+                        site[e] = perm[s] >= 0 ? acc[cc * nv + perm[s]] : 0.f;
                     }
                     for (int e = lane; e < rows * Sl; e += 32) {
                         const int r = e / Sl, s = e - r * Sl;
-                        g[e] = X[r * nv + perm[s]];
+                        g[e] = perm[s] >= 0 ? X[r * nv + perm[s]] : 0.f;
                     }
                 } else {
                     // T = U X^T: site = X[:, top]^T / sigma, carry = U[:, top] sigma
                     for (int e = lane; e < Sl * cols; e += 32) {
                         const int s = e / cols, cc = e - s * cols;
-                        const float sg = sig[perm[s]];
+                        const float sg = perm[s] >= 0 ? sig[perm[s]] : 0.f;
                         site[e] = sg > 0.f ? X[cc * nv + perm[s]] / sg : 0.f;
                     }
                     for (int e = lane; e < rows * Sl; e += 32) {
                         const int r = e / Sl, s = e - r * Sl;
-                        t[e] = acc[r * nv + perm[s]] * sig[perm[s]];
+                        t[e] = perm[s] >= 0 ? acc[r * nv + perm[s]] * sig[perm[s]] : 0.f;
                     }
                     float* tmp = g; g = t; t = tmp;
                 }
@@ -668,7 +678,9 @@ decode_fp32_kernel(DecodeArgs a) {
     if constexpr (GLOBAL) {
         const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
         float* ws = a.gws + (size_t)gw * a.per_warp;
-        for (int64_t unit = gw; unit < 2 * a.B; unit += nw) {
+        const int64_t nunits = a.ulist ? (int64_t)*a.ucount : 2 * a.B;
+        for (int64_t idx = gw; idx < nunits; idx += nw) {
+            const int64_t unit = a.ulist ? a.ulist[idx] : idx;
             decode_unit(a, ws, unit, lane, lz);
             if (lane == 0) {
                 a.logP[(unit >> 1) * 4 + 2 * (unit & 1)] = lz[0];
@@ -776,6 +788,141 @@ mld_status ensure_code_device(mld_code* C) {
 }
 }  // namespace mld
 
+namespace {
+
+// Grow a device buffer owned by the code object to at least `bytes`.
+template <typename T>
+mld_status grow(T** buf, size_t* have, size_t bytes) {
+    if (bytes <= *have) return MLD_OK;
+    cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+    if (cudaMalloc(reinterpret_cast<void**>(buf), bytes) != cudaSuccess) return MLD_ERR_NOMEM;
+    *have = bytes;
+    return MLD_OK;
+}
+
+// Truncating chi: the rank-adaptive kernel (one warp per unit) over all units
+// with small slice capacities on every resident warp; the units it hands
+// back go to a second pass of the same kernel with large capacities on one
+// block of warps per 4 SMs, and what that hands back (bonds above 128) to the
+// fixed-shape kernel in global-workspace mode. Later passes read their unit
+// count on the device and exit at once when it is zero. Control block
+// (bytes): [0] queue head of pass 1, [8] of pass 2, [16] overflow count of
+// pass 1, [20] of pass 2, [24] executed flops (f64, accumulated), [32] bond
+// histogram (65 x u64, accumulated).
+constexpr size_t kTctlBytes = 1024;
+constexpr int kTruncArena = 3072;        // on-chip work arena per unit (floats)
+
+mld_status decode_truncated(mld_code* C, const mld::Plan& P, const mld::SiteStep* d_steps, const float* noise,
+                            int noise_mode, const uint64_t* syn, int64_t B, int chi, double* logP,
+                            cudaStream_t s) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return MLD_ERR_CUDA;
+    const int64_t units = 2 * B;
+    const int bps = mld::trunc_blocks_per_sm(kTruncArena);
+    if (bps < 1) return MLD_ERR_CUDA;
+    const int upb = mld::trunc_units_per_block();
+    int64_t blocks1 = (int64_t)bps * sms;
+    if (blocks1 > (units + upb - 1) / upb) blocks1 = (units + upb - 1) / upb;
+    const bool pass2 = chi > mld::kTruncSmall.max_bond;   // otherwise only carry rows can overflow
+    int64_t blocks2 = (sms + 3) / 4;
+    const size_t ws1 = (size_t)blocks1 * upb * mld::kTruncSmall.slice();
+    const size_t ws2 = (size_t)blocks2 * upb * mld::kTruncLarge.slice();
+    mld_status st = grow(&C->d_tws, &C->tws_bytes, std::max(ws1, ws2) * sizeof(float));
+    if (st != MLD_OK) return st;
+    if (!C->d_tctl) {
+        if (cudaMalloc(&C->d_tctl, kTctlBytes) != cudaSuccess) return MLD_ERR_NOMEM;
+        if (cudaMemset(C->d_tctl, 0, kTctlBytes) != cudaSuccess) return MLD_ERR_CUDA;
+    }
+    if (2 * units > C->ovf_cap) {
+        cudaFree(C->d_ovf);
+        C->d_ovf = nullptr;
+        C->ovf_cap = 0;
+        if (cudaMalloc(&C->d_ovf, (size_t)2 * units * sizeof(int64_t)) != cudaSuccess) return MLD_ERR_NOMEM;
+        C->ovf_cap = 2 * units;
+    }
+    char* ctl = static_cast<char*>(C->d_tctl);
+    // queue heads and overflow counts start at zero (flops and histogram accumulate)
+    if (cudaMemsetAsync(ctl, 0, 24, s) != cudaSuccess) return MLD_ERR_CUDA;
+    mld::TruncArgs ta;
+    ta.dmask = C->d_dmask;
+    ta.noise = noise;
+    ta.syn = syn;
+    ta.logP = logP;
+    ta.status = C->d_status;
+    ta.B = B;
+    ta.d = C->d;
+    ta.n = C->n;
+    ta.words = C->words;
+    ta.noise_mode = noise_mode;
+    ta.chi = chi;
+    ta.cutoff = C->svd_cutoff;
+    ta.arena = kTruncArena;
+    ta.caps = mld::kTruncSmall;
+    ta.ws = C->d_tws;
+    ta.next_unit = reinterpret_cast<unsigned long long*>(ctl);
+    ta.in_list = nullptr;
+    ta.in_count = nullptr;
+    ta.ovf_list = C->d_ovf;
+    ta.ovf_count = reinterpret_cast<int*>(ctl + 16);
+    ta.flops = reinterpret_cast<double*>(ctl + 24);
+    ta.bond_hist = reinterpret_cast<unsigned long long*>(ctl + 32);
+    if (!mld::launch_trunc(ta, (int)blocks1, s)) return MLD_ERR_CUDA;
+    const int64_t* last_list = C->d_ovf;
+    const int* last_count = reinterpret_cast<const int*>(ctl + 16);
+    if (pass2) {
+        ta.caps = mld::kTruncLarge;
+        ta.next_unit = reinterpret_cast<unsigned long long*>(ctl + 8);
+        ta.in_list = C->d_ovf;
+        ta.in_count = reinterpret_cast<const int*>(ctl + 16);
+        ta.ovf_list = C->d_ovf + units;
+        ta.ovf_count = reinterpret_cast<int*>(ctl + 20);
+        if (!mld::launch_trunc(ta, (int)blocks2, s)) return MLD_ERR_CUDA;
+        last_list = C->d_ovf + units;
+        last_count = reinterpret_cast<const int*>(ctl + 20);
+    }
+    // the fixed-shape kernel over what is left (persistent warps, global
+    // workspaces of at most 1 GiB in all)
+    mld::DecodeArgs a;
+    a.steps = d_steps;
+    a.dmask = C->d_dmask;
+    a.noise = noise;
+    a.syn = syn;
+    a.logP = logP;
+    a.status = C->d_status;
+    a.B = B;
+    a.d = C->d;
+    a.n = C->n;
+    a.words = C->words;
+    a.noise_mode = noise_mode;
+    a.off_w = P.off_w;
+    a.off_mps = P.off_mps;
+    a.off_buf0 = P.off_buf0;
+    a.off_buf1 = P.off_buf1;
+    a.off_q = P.off_q;
+    a.off_svd = P.off_svd;
+    a.per_warp = P.floats_per_warp;
+    for (int i = 0; i <= mld::kMaxD; ++i) a.init_sizes[i] = i <= C->d ? P.init_sizes[i] : 0;
+    a.cutoff = C->svd_cutoff;
+    a.ulist = last_list;
+    a.ucount = last_count;
+    const size_t pw = (size_t)P.floats_per_warp * sizeof(float);
+    const int W = 4;
+    int64_t nw = (int64_t)sms * 16;
+    while (nw > W && (size_t)nw * pw > ((size_t)1 << 30)) nw /= 2;
+    nw = (nw / W) * W;
+    st = grow(&C->d_gws, &C->gws_bytes, (size_t)nw * pw);
+    if (st != MLD_OK) return st;
+    a.gws = C->d_gws;
+    mld::decode_fp32_kernel<true><<<(unsigned)(nw / W), 32 * W, 0, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? MLD_OK : MLD_ERR_CUDA;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* mld_status_string(mld_status s) {
@@ -804,6 +951,9 @@ void mld_code_destroy(mld_code* C) {
         cudaFree(C->h_stage_dev);
         cudaFree(C->d_gws);
         cudaFree(C->d_gradws);
+        cudaFree(C->d_tws);
+        cudaFree(C->d_tctl);
+        cudaFree(C->d_ovf);
     }
     delete C;
 }
@@ -889,6 +1039,18 @@ mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, co
     // the mixed-precision path exists for the untruncated specialised kernel
     // (TF32 tensor-core products); BF16 and truncating chi run FP32 only
     if (precision == MLD_MIXED_BF16 || (precision == MLD_MIXED_TF32 && !exact)) return MLD_ERR_UNSUPPORTED;
+    if (P.svd_sites != 0) {
+        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+        if (!mld::launch_noise_check(noise, noise_mode, noise_mode == MLD_NOISE_TABLE ? C->n : B, C->d_status, s))
+            return MLD_ERR_CUDA;
+        const mld_status ts = decode_truncated(C, P, pd->d_steps, noise, noise_mode, syn, B, chi, logP, s);
+        if (ts != MLD_OK) return ts;
+        if (argmax) {
+            mld::argmax_kernel<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(logP, argmax, B);
+            if (cudaGetLastError() != cudaSuccess) return MLD_ERR_CUDA;
+        }
+        return MLD_OK;
+    }
     const size_t pw = (size_t)(exact ? mld::exact_floats_per_warp(C->d) : P.floats_per_warp) * sizeof(float);
     const int64_t units = 2 * B;                       // (syndrome, l_Z) pairs, both kernels
     int W = 1;
@@ -1052,6 +1214,34 @@ mld_status mld_decode_grad(const mld_code* Cc, const float* noise, const uint64_
         return mld::launch_grad_dense(d, ga, blocks, reinterpret_cast<cudaStream_t>(stream)) ? MLD_OK
                                                                                               : MLD_ERR_CUDA;
     }
+}
+
+mld_status mld_code_set_svd_cutoff(mld_code* C, double rel) {
+    if (!C || !(rel >= 0.0) || !(rel < 1.0)) return MLD_ERR_INVALID_ARG;
+    C->svd_cutoff = (float)rel;
+    return MLD_OK;
+}
+
+mld_status mld_decode_executed_flops(const mld_code* Cc, double* out) {
+    mld_code* C = const_cast<mld_code*>(Cc);
+    if (!C || !out) return MLD_ERR_INVALID_ARG;
+    *out = 0.0;
+    if (!C->d_tctl) return MLD_OK;
+    char* ctl = static_cast<char*>(C->d_tctl);
+    if (cudaMemcpy(out, ctl + 24, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return MLD_ERR_CUDA;
+    if (cudaMemset(ctl + 24, 0, sizeof(double)) != cudaSuccess) return MLD_ERR_CUDA;
+    return MLD_OK;
+}
+
+mld_status mld_decode_bond_histogram(const mld_code* Cc, int64_t* hist) {
+    mld_code* C = const_cast<mld_code*>(Cc);
+    if (!C || !hist) return MLD_ERR_INVALID_ARG;
+    for (int k = 0; k <= 64; ++k) hist[k] = 0;
+    if (!C->d_tctl) return MLD_OK;
+    char* ctl = static_cast<char*>(C->d_tctl);
+    if (cudaMemcpy(hist, ctl + 32, 65 * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess) return MLD_ERR_CUDA;
+    if (cudaMemset(ctl + 32, 0, 65 * sizeof(int64_t)) != cudaSuccess) return MLD_ERR_CUDA;
+    return MLD_OK;
 }
 
 mld_status mld_decode_status(const mld_code* C) {

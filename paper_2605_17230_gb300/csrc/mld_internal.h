@@ -36,4 +36,13 @@ struct mld_code {
     // workspace of the adjoint kernel
     float* d_gradws = nullptr;
     size_t gradws_bytes = 0;
+    // rank-adaptive truncated sweep: per-block slices, the unit queue and
+    // overflow list, the executed-flop counter, and the relative cutoff on
+    // singular values (sigma_k <= svd_cutoff * sigma_1 is discarded)
+    float* d_tws = nullptr;
+    size_t tws_bytes = 0;
+    void* d_tctl = nullptr;              // [0] u64 queue head, [8] int overflow count, [16] f64 flops
+    int64_t* d_ovf = nullptr;
+    int64_t ovf_cap = 0;
+    float svd_cutoff = 1e-7f;
 };

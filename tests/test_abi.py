@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "mld.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(mld_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(mld_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declares_what_binding_exports():
@@ -105,3 +105,14 @@ def test_host_side_argument_checks():
     assert grad(P(c5.handle), fake, fake, 4, 0, None, None, fake, None) == INVALID
     assert grad(P(c5.handle), fake, fake, 4, 8, None, None, None, None) == INVALID       # no dnoise
     assert grad(P(c13.handle), fake, fake, 4, 64, None, None, fake, None) == UNSUPPORTED
+
+
+def test_wilson_interval_matches_scipy():
+    """The LER intervals the bench reports: Wilson score intervals, checked
+    against scipy's binomial test at several counts (including 0 and n)."""
+    stats = pytest.importorskip("scipy.stats")
+    import bench
+    for k, n in [(0, 100), (3, 100), (50, 100), (100, 100), (17, 65536), (6000, 65536)]:
+        lo, hi = bench.wilson_interval(k, n)
+        ref = stats.binomtest(k, n).proportion_ci(confidence_level=0.95, method="wilson")
+        assert abs(lo - ref.low) < 1e-9 and abs(hi - ref.high) < 1e-9

@@ -307,17 +307,6 @@ def test_d13_exact_global_workspace(mld, prec):
     check_argmax(am, ref)
 
 
-def test_d13_truncated_global_workspace_vs_fp64_mps(mld):
-    d, n, chi = 13, 169, 32
-    noise = synth.depolarizing(n, 0.10).astype(np.float32)
-    E = synth.sample_errors(d, noise, 2, seed=17)
-    syn = synth.syndromes_of(d, E)
-    ref = omps.decode_mps(d, noise.astype(np.float64), syn, chi, xl_column=d - 1)
-    lp, _ = gpu_decode(mld, d, noise, syn, chi)
-    best = np.argmax(ref, axis=1)
-    np.testing.assert_allclose(lp[np.arange(len(ref)), best], ref[np.arange(len(ref)), best], rtol=0, atol=1e-4)
-
-
 def test_d17_truncated_close_to_exact(mld):
     """d=17 at chi=16 (truncating, global workspace): the boundary-MPS value
     is an approximation of the exact contraction (Sec. 3.2.1: small chi
