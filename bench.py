@@ -279,13 +279,18 @@ def run_mixed(args):
 
 
 def _hist_summary(h):
-    tot = int(h.sum())
+    """Kept-bond statistics from mld_decode_bond_histogram (bin 0: steps that
+    ran in the global spill arena)."""
+    b = h.copy()
+    spilled = int(b[0])
+    b[0] = 0
+    tot = int(b.sum())
     if tot == 0:
         return None
-    ks = np.arange(len(h))
-    cdf = np.cumsum(h) / tot
-    return {"cuts": tot, "mean": float((h * ks).sum() / tot), "p99": int(np.searchsorted(cdf, 0.99)),
-            "max": int(ks[h > 0].max()), "last_bin_is_64_or_more": True}
+    ks = np.arange(len(b))
+    cdf = np.cumsum(b) / tot
+    return {"cuts": tot, "mean": float((b * ks).sum() / tot), "p99": int(np.searchsorted(cdf, 0.99)),
+            "max": int(ks[b > 0].max()), "steps_in_spill_arena": spilled}
 
 
 def _posterior(x):

@@ -246,8 +246,10 @@ mld_status mld_decode_executed_flops(const mld_code* code, double* flops);
 
 /* Histogram of the bonds kept at the truncating cuts of this code's decodes
  * since the last call: hist[k] (k = 1..63) counts cuts that kept k singular
- * values, hist[64] those that kept 64 or more (rank-adaptive kernel only);
- * then reset. The caller synchronises the decode streams first. */
+ * values, hist[64] those that kept 64 or more; hist[0] counts site steps
+ * whose buffers did not fit the on-chip arena and ran in the global spill
+ * arena (rank-adaptive kernel only); then reset. The caller synchronises the
+ * decode streams first. */
 mld_status mld_decode_bond_histogram(const mld_code* code, int64_t* hist /* [65] */);
 
 /* Counted floating-point operations per syndrome (all four classes) of the

@@ -100,6 +100,7 @@ __device__ __noinline__ int qrcp(float* M, int K, int ld, int N, float* tau, int
     for (int c = lane; c < N; c += 32) {
         const float* col = M + c * ld;
         float s = 0.f;
+#pragma unroll 2
         for (int r = 0; r < K; ++r) s = fmaf(col[r], col[r], s);
         nrm[c] = sqrtf(s);
         piv[c] = c;
@@ -164,12 +165,15 @@ __device__ __noinline__ int qrcp(float* M, int K, int ld, int N, float* tau, int
             float* col = M + cc * ld;
             if (tj != 0.f) {
                 float w = col[j];
+#pragma unroll 2
                 for (int rr = j + 1; rr < K; ++rr) w = fmaf(vj[rr], col[rr], w);
                 w *= tj;
                 col[j] -= w;
+#pragma unroll 2
                 for (int rr = j + 1; rr < K; ++rr) col[rr] = fmaf(-vj[rr], w, col[rr]);
             }
             float s = 0.f;
+#pragma unroll 2
             for (int rr = j + 1; rr < K; ++rr) s = fmaf(col[rr], col[rr], s);
             nrm[cc] = sqrtf(s);
         }
@@ -198,9 +202,11 @@ __device__ __noinline__ void apply_q(const float* V0, const float* tau0, int nr0
             if (tj == 0.f) continue;
             const float* v = Vs + j * ldv;
             float w = y[j];
+#pragma unroll 2
             for (int r = j + 1; r < K; ++r) w = fmaf(v[r], y[r], w);
             w *= tj;
             y[j] -= w;
+#pragma unroll 2
             for (int r = j + 1; r < K; ++r) y[r] = fmaf(-v[r], w, y[r]);
         }
     }
@@ -358,8 +364,11 @@ struct Unit {
         if (need > cap || (cbase != arena && csize + out + work <= a.arena)) {
             need = csize + out + work;
             if (need <= a.arena) { base = arena; cap = a.arena; }
-            else if (need <= a.caps.spill) { base = spill; cap = (int)a.caps.spill; }
-            else { ovf = true; return false; }
+            else if (need <= a.caps.spill) {
+                base = spill;
+                cap = (int)a.caps.spill;
+                if (lane == 0) atomicAdd(a.bond_hist, 1ULL);   // bin 0: steps run in the spill arena
+            } else { ovf = true; return false; }
             if (base != cbase) {
                 for (int e = lane; e < csize; e += 32) base[e] = cptr[e];
             } else {                           // same arena, carry moved to its bottom
@@ -492,6 +501,7 @@ struct Unit {
                         for (int al = 0; al < pam; ++al) {
                             const float* crow = C + (al * Dl) * ldC + kap;
                             float x = 0.f;
+#pragma unroll 2
                             for (int l = 0; l < Dl; ++l) x = fmaf(crow[l * ldC], A[l * ncolA + cA], x);
                             float w = 1.f;
                             if (i > 0) {
