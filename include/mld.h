@@ -54,8 +54,10 @@ typedef enum {
 } mld_status;
 
 typedef enum {
-    MLD_FP32 = 0,              /* FP32 storage and arithmetic (FP64 only in the
-                                  Jacobi rotation parameters and the log-norm) */
+    MLD_FP32 = 0,              /* FP32 storage and arithmetic, FP32 Jacobi
+                                  rotations; FP64 only where ln Z is formed
+                                  from the mantissa and the power-of-two
+                                  exponent */
     MLD_MIXED_BF16 = 1,        /* reserved: MLD_ERR_UNSUPPORTED (BF16 operands
                                   miss |d ln Z| <= 1e-3 on the leading coset) */
     MLD_MIXED_TF32 = 2         /* data-site MPO.MPS products on the tensor
@@ -145,22 +147,25 @@ mld_status mld_decode_host(const mld_code* code, const float* noise, int noise_m
  * is already reserved by another framework's caching allocator). The paper
  * has no counterpart: this is a deployment variant of the untruncated sweep.
  *   Scope: precision MLD_FP32, chi at or above the exact bond of every cut
- *   (no truncation), and the distances with a compile-time specialised kernel
- *   (3 <= d <= 11); anything else returns MLD_ERR_UNSUPPORTED.
+ *   (no truncation), and 3 <= d <= 11; anything else returns
+ *   MLD_ERR_UNSUPPORTED.
  *   Scratch: the status word and the code's destabiliser tables live in one
  *   16 KiB file-scope __device__ array that every GPU loading the library
  *   holds until the process exits; a code whose tables do not fit returns
- *   MLD_ERR_UNSUPPORTED. Each call resets the status word and rewrites the
- *   tables (asynchronous copies on `stream`); the array keeps the last call's
- *   contents, so calls that overlap on the GPU (other streams, other threads)
- *   race and must be serialised by the caller.
+ *   MLD_ERR_UNSUPPORTED. Each call resets the status word; the tables are
+ *   copied (asynchronously on `stream`, from pageable host memory) only when
+ *   the array holds another code's tables. The array keeps the last call's
+ *   contents, so calls that overlap on the GPU (other streams, other
+ *   threads) race and must be serialised by the caller.
  *   Set-up: the first call on a device looks up the array's device address
  *   (the device must be current); make that first call before any stream
  *   capture.
  *   Arguments as mld_decode. check_status != 0 synchronises the stream and
  *   returns the device status (MLD_OK, MLD_ERR_INVALID_ARG for invalid noise
- *   values as in mld_decode, or MLD_ERR_NUMERIC); 0 returns as soon as the
- *   work is enqueued. */
+ *   values as in mld_decode, MLD_ERR_NUMERIC or MLD_ERR_TIMEOUT); 0 returns as
+ *   soon as the work is enqueued, and the device status of that call cannot
+ *   be read afterwards (mld_decode_status reads another word, and the next
+ *   call clears this one). */
 mld_status mld_decode_noalloc(const mld_code* code, const float* noise, int noise_mode,
                               const uint64_t* syndromes, int64_t B, int chi, int precision,
                               double* logP, uint8_t* argmax, void* stream, int check_status);
@@ -198,7 +203,10 @@ void mld_graph_destroy(mld_graph* graph);
 
 /* Time the candidate CTA shapes (warps per block) of this code, chi and
  * precision on a synthetic batch of the given size and keep the fastest for
- * later decodes of this code object (per chi and precision). Synchronous. */
+ * later decodes of this code object (per chi and precision). For a
+ * truncating chi the rank-adaptive sweep (4 units per block) is a candidate
+ * beside the fixed-shape sweep's shapes, and the faster kernel is kept for
+ * that chi (unless mld_code_set_truncation_kernel forces one). Synchronous. */
 mld_status mld_autotune(const mld_code* code, int chi, int precision, int64_t sample_B, int* chosen_warps);
 
 /* Adjoint of the sweep: derivatives of ln Z_l(s) with respect to the noise
@@ -236,6 +244,16 @@ mld_status mld_decode_status(const mld_code* code);
  * Applies to later decodes of this code object. MLD_ERR_INVALID_ARG unless
  * 0 <= rel < 1. Host only. */
 mld_status mld_code_set_svd_cutoff(mld_code* code, double rel);
+
+/* Which kernel decodes a truncating chi for this code: 0 (default) per chi,
+ * mld_autotune's choice if it timed this chi, else the fixed-shape sweep when
+ * its whole per-warp state fits 24 KB of shared memory (small d and chi) and
+ * the rank-adaptive sweep otherwise; 1 always the rank-adaptive sweep (one
+ * warp per (syndrome, l_Z), runtime bonds, pivoted QR, Jacobi on R^T); 2
+ * always the fixed-shape sweep (one warp per unit, every bond at its
+ * chi-capped size, values below the cutoff written as zero). Both apply the
+ * same truncation rule. MLD_ERR_INVALID_ARG for other values. Host only. */
+mld_status mld_code_set_truncation_kernel(mld_code* code, int which);
 
 /* Floating-point operations executed by the truncating sweeps of this code
  * since the last call (apply, QR, Q applications and every Jacobi pair

@@ -35,7 +35,8 @@ EXPORTED_SYMBOLS = ["mld_code_create_rotated", "mld_code_destroy", "mld_code_inf
                     "mld_decode_flops", "mld_decode_noalloc", "mld_decode_batch", "mld_graph_create",
                     "mld_graph_launch", "mld_graph_destroy", "mld_autotune", "mld_decode_grad",
                     "mld_decode_dem", "mld_status_string", "mld_code_set_svd_cutoff",
-                    "mld_decode_executed_flops", "mld_decode_bond_histogram", "mld_measure_fp32_peak"]
+                    "mld_decode_executed_flops", "mld_decode_bond_histogram", "mld_measure_fp32_peak",
+                    "mld_code_set_truncation_kernel"]
 
 _lib = None
 
@@ -109,6 +110,8 @@ def load(build_if_missing: bool = True):
     lib.mld_decode_executed_flops.restype = I
     lib.mld_decode_bond_histogram.argtypes = [P, P]
     lib.mld_decode_bond_histogram.restype = I
+    lib.mld_code_set_truncation_kernel.argtypes = [P, I]
+    lib.mld_code_set_truncation_kernel.restype = I
     lib.mld_measure_fp32_peak.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]
     lib.mld_measure_fp32_peak.restype = I
     lib.mld_decode_launches.argtypes = []
@@ -283,6 +286,12 @@ class Code:
     def set_svd_cutoff(self, rel: float):
         """Relative singular-value cutoff of truncating chi (mld_code_set_svd_cutoff)."""
         _check(load().mld_code_set_svd_cutoff(ctypes.c_void_p(self.handle), float(rel)), "mld_code_set_svd_cutoff")
+
+    def set_truncation_kernel(self, which: int):
+        """0: chosen per chi (default); 1: rank-adaptive; 2: fixed-shape
+        (mld_code_set_truncation_kernel)."""
+        _check(load().mld_code_set_truncation_kernel(ctypes.c_void_p(self.handle), int(which)),
+               "mld_code_set_truncation_kernel")
 
     def executed_flops(self) -> float:
         """Flops executed by truncating sweeps since the last call (the

@@ -171,10 +171,16 @@ mld_status mld_autotune(const mld_code* Cc, int chi, int precision, int64_t samp
          cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
          cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         st = MLD_ERR_CUDA;
-    int best_w = 0;
+    // candidates: warps per CTA of the fixed-shape or untruncated kernel and,
+    // for a truncating chi, the rank-adaptive sweep (kernel 1) as well
+    const bool truncating = mld::make_plan(C->d, chi).svd_sites != 0;
+    const int saved_kernel = C->trunc_kernel;
+    int best_w = 0, best_k = 0;
     float best_ms = 0.f;
-    for (int w = 1; st == MLD_OK && w <= 8; w *= 2) {
-        C->force_warps = w;
+    for (int cand = truncating ? 0 : 1; st == MLD_OK && cand <= 4; ++cand) {
+        const int kern = cand == 0 ? 1 : 2, w = cand == 0 ? 4 : 1 << (cand - 1);
+        C->trunc_kernel = truncating ? kern : saved_kernel;
+        C->force_warps = cand == 0 ? 0 : w;
         mld_status r = mld_decode(C, dn, MLD_NOISE_TABLE, ds, sample_B, chi, precision, dl, nullptr, s);
         if (r != MLD_OK) { st = r; break; }
         cudaEventRecord(e0, s);
@@ -184,15 +190,22 @@ mld_status mld_autotune(const mld_code* Cc, int chi, int precision, int64_t samp
         if (cudaEventSynchronize(e1) != cudaSuccess) { st = MLD_ERR_CUDA; break; }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (best_w == 0 || ms < best_ms) { best_w = w; best_ms = ms; }
+        if (best_w == 0 || ms < best_ms) { best_w = w; best_k = kern; best_ms = ms; }
     }
     C->force_warps = 0;
+    C->trunc_kernel = saved_kernel;
     if (st == MLD_OK && best_w > 0) {
         const int key = chi * 4 + precision;
         bool found = false;
         for (auto& kv : C->tuned)
             if (kv.first == key) { kv.second = best_w; found = true; }
         if (!found) C->tuned.emplace_back(key, best_w);
+        if (truncating) {
+            found = false;
+            for (auto& kv : C->trunc_tuned)
+                if (kv.first == chi) { kv.second = best_k; found = true; }
+            if (!found) C->trunc_tuned.emplace_back(chi, best_k);
+        }
         if (chosen) *chosen = best_w;
         if (mld_decode_status(C) != MLD_OK) st = MLD_ERR_NUMERIC;
     }

@@ -1027,6 +1027,7 @@ mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, co
     a.off_q = P.off_q;
     a.off_svd = P.off_svd;
     a.per_warp = P.floats_per_warp;
+    a.cutoff = C->svd_cutoff;
     for (int i = 0; i <= mld::kMaxD; ++i) a.init_sizes[i] = i <= C->d ? P.init_sizes[i] : 0;
     int dev = 0, max_optin = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -1039,7 +1040,16 @@ mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, co
     // the mixed-precision path exists for the untruncated specialised kernel
     // (TF32 tensor-core products); BF16 and truncating chi run FP32 only
     if (precision == MLD_MIXED_BF16 || (precision == MLD_MIXED_TF32 && !exact)) return MLD_ERR_UNSUPPORTED;
-    if (P.svd_sites != 0) {
+    // truncating chi: the rank-adaptive sweep, or the fixed-shape one when its
+    // whole per-warp state fits 24 KB of shared memory (small chi and d, where
+    // its compile-free static shapes beat the runtime ones), unless the
+    // caller or mld_autotune chose
+    int which = C->trunc_kernel;
+    if (which == 0)
+        for (const auto& kv : C->trunc_tuned)
+            if (kv.first == chi) which = kv.second;
+    if (which == 0) which = P.floats_per_warp <= 6144 ? 2 : 1;
+    if (P.svd_sites != 0 && which == 1) {
         cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
         if (!mld::launch_noise_check(noise, noise_mode, noise_mode == MLD_NOISE_TABLE ? C->n : B, C->d_status, s))
             return MLD_ERR_CUDA;
@@ -1219,6 +1229,12 @@ mld_status mld_decode_grad(const mld_code* Cc, const float* noise, const uint64_
 mld_status mld_code_set_svd_cutoff(mld_code* C, double rel) {
     if (!C || !(rel >= 0.0) || !(rel < 1.0)) return MLD_ERR_INVALID_ARG;
     C->svd_cutoff = (float)rel;
+    return MLD_OK;
+}
+
+mld_status mld_code_set_truncation_kernel(mld_code* C, int which) {
+    if (!C || which < 0 || which > 2) return MLD_ERR_INVALID_ARG;
+    C->trunc_kernel = which;
     return MLD_OK;
 }
 

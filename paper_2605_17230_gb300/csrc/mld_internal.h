@@ -45,4 +45,9 @@ struct mld_code {
     int64_t* d_ovf = nullptr;
     int64_t ovf_cap = 0;
     float svd_cutoff = 1e-7f;
+    // which kernel runs a truncating chi: 0 chosen per chi (autotuned, else by
+    // the plan's size), 1 the rank-adaptive sweep, 2 the fixed-shape sweep;
+    // trunc_tuned holds mld_autotune's choice per chi
+    int trunc_kernel = 0;
+    std::vector<std::pair<int, int>> trunc_tuned;
 };

@@ -12,6 +12,7 @@
 #include <stdint.h>
 
 #include <mutex>
+#include <vector>
 
 #include "mld_checks.h"
 #include "mld_exact.h"
@@ -20,7 +21,7 @@
 namespace {
 
 // Scratch layout: [0, 256) status word, [256, ...) per-qubit destabiliser
-// masks of the code, n * 2 * syn_words uint64 (enough for d <= 13).
+// masks of the code, n * 2 * syn_words uint64 (enough for d <= 11).
 constexpr size_t kNoAllocBytes = 16384;
 constexpr size_t kStatusSlot = 256;
 constexpr int kMaxDevices = 64;
@@ -29,6 +30,20 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 std::mutex g_setup_mutex;
 void* g_scratch_ptr[kMaxDevices] = {};
+// FNV-1a hash of the destabiliser tables last written to each device's
+// scratch array (0: none yet), so that consecutive calls for one code skip
+// the upload; calls are serialised by the caller, as the array is shared
+uint64_t g_tables_written[kMaxDevices] = {};
+
+uint64_t table_hash(const std::vector<uint64_t>& t) {
+    uint64_t h = 1469598103934665603ULL;
+    for (uint64_t w : t)
+        for (int k = 0; k < 8; ++k) {
+            h ^= (w >> (8 * k)) & 0xffu;
+            h *= 1099511628211ULL;
+        }
+    return h | 1ULL;                 // never 0
+}
 
 __global__ void noalloc_argmax(const double* __restrict__ logP, uint8_t* __restrict__ am, int64_t B) {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -43,9 +58,10 @@ __global__ void noalloc_argmax(const double* __restrict__ logP, uint8_t* __restr
 // Device address of the scratch array for the current device. In host code
 // the array's name is only a host-side stand-in, so the address is looked up
 // once per device (with that device current) and cached.
-mld_status scratch_address(unsigned char** out) {
+mld_status scratch_address(unsigned char** out, int* device) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MLD_ERR_CUDA;
+    *device = dev;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_ptr[dev]) {
         void* p = nullptr;
@@ -61,6 +77,7 @@ mld_status scratch_address(unsigned char** out) {
 extern "C" mld_status mld_decode_noalloc(const mld_code* C, const float* noise, int noise_mode,
                                          const uint64_t* syndromes, int64_t B, int chi, int precision,
                                          double* logP, uint8_t* argmax, void* stream, int check_status) {
+    mld::NvtxRange trace("mld_decode_noalloc");
     if (!C || B < 0 || chi < 1) return MLD_ERR_INVALID_ARG;
     if (noise_mode != MLD_NOISE_TABLE && noise_mode != MLD_NOISE_DEPOL) return MLD_ERR_INVALID_ARG;
     if (precision != MLD_FP32 && precision != MLD_MIXED_BF16 && precision != MLD_MIXED_TF32)
@@ -71,11 +88,12 @@ extern "C" mld_status mld_decode_noalloc(const mld_code* C, const float* noise, 
     // only the untruncated FP32 sweep of the distances with a specialised
     // kernel, and only codes whose tables fit in the scratch array
     const size_t table_bytes = C->dmask.size() * sizeof(uint64_t);
-    if (precision != MLD_FP32 || mld::exact_floats_per_warp(C->d) == 0 || mld::make_plan(C->d, chi).svd_sites != 0 ||
-        kStatusSlot + table_bytes > kNoAllocBytes)
+    if (precision != MLD_FP32 || C->d > 11 || mld::exact_floats_per_warp(C->d) == 0 ||
+        mld::make_plan(C->d, chi).svd_sites != 0 || kStatusSlot + table_bytes > kNoAllocBytes)
         return MLD_ERR_UNSUPPORTED;
     unsigned char* scratch = nullptr;
-    mld_status st = scratch_address(&scratch);
+    int device = 0;
+    mld_status st = scratch_address(&scratch, &device);
     if (st != MLD_OK) return st;
     int dev = 0, max_optin = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -93,12 +111,20 @@ extern "C" mld_status mld_decode_noalloc(const mld_code* C, const float* noise, 
         if (warps > best) { best = warps; W = w; }
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    // every call rewrites what it reads: the status word starts at zero and
-    // the tables are those of this code
+    // the status word starts at zero in every call; the tables are uploaded
+    // only when the array holds another code's (the previous call's code is
+    // remembered per device)
     if (cudaMemsetAsync(scratch, 0, sizeof(int), s) != cudaSuccess) return MLD_ERR_CUDA;
-    if (cudaMemcpyAsync(scratch + kStatusSlot, C->dmask.data(), table_bytes, cudaMemcpyHostToDevice, s) !=
-        cudaSuccess)
-        return MLD_ERR_CUDA;
+    const uint64_t tables = table_hash(C->dmask);
+    {
+        std::lock_guard<std::mutex> lock(g_setup_mutex);
+        if (g_tables_written[device] != tables) {
+            if (cudaMemcpyAsync(scratch + kStatusSlot, C->dmask.data(), table_bytes, cudaMemcpyHostToDevice, s) !=
+                cudaSuccess)
+                return MLD_ERR_CUDA;
+            g_tables_written[device] = tables;
+        }
+    }
     if (!mld::launch_noise_check(noise, noise_mode, noise_mode == MLD_NOISE_TABLE ? C->n : B,
                                  reinterpret_cast<int*>(scratch), s))
         return MLD_ERR_CUDA;

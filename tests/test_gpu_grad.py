@@ -101,9 +101,10 @@ def test_gradient_rerun_bit_identical(mld):
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
 
 
-def test_gradient_d11_checkpoint_path(mld):
-    """d = 11 (beyond the dense on-chip states): MPS checkpoints and the
-    half-turn image's sweep, against the oracle's exact derivative."""
+def test_gradient_d11_one_block_per_sm(mld):
+    """d = 11: the dense adjoint with one block of 16 warps per SM (the
+    states fill its shared memory; L_c is read back from the block's global
+    slice), against the oracle's exact derivative."""
     d, chi, B = 11, 32, 3
     n, noise, E, syn = _setup(d, B, seed=11)
     code = mld.Code(d)

@@ -46,10 +46,11 @@ def workload(d, kind, B):
     return noise, E, synth.syndromes_of(d, E)
 
 
-def decode(mld, d, noise, syn, chi, cutoff=None):
+def decode(mld, d, noise, syn, chi, cutoff=None, kernel=0):
     code = mld.Code(d)
     if cutoff is not None:
         code.set_svd_cutoff(cutoff)
+    code.set_truncation_kernel(kernel)
     lp, am = code.decode(torch.tensor(noise, device="cuda"), torch.tensor(syn.view(np.int64), device="cuda"), chi)
     torch.cuda.synchronize()
     st = code.status()
@@ -124,15 +125,39 @@ def test_d17_chi128_vs_exact_oracle_64_syndromes(mld):
     np.testing.assert_array_equal(am[clear], np.argmax(ref, axis=1)[clear])
 
 
-@pytest.mark.parametrize("d,chi", [(9, 8), (11, 16)])
-def test_cutoff_zero_fixed_chi_rule_small(mld, d, chi):
-    """cutoff 0 at the truncating points of the d/p grid, against the FP64
+@pytest.mark.parametrize("d,chi", [(7, 4), (9, 8), (11, 16)])
+@pytest.mark.parametrize("cutoff", [None, 0.0])
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_both_truncation_kernels_small(mld, d, chi, cutoff, kernel):
+    """Both truncation kernels (1: rank-adaptive, 2: fixed-shape with values
+    below the cutoff written as zero) at the truncating points of the d/p
+    grid, with the default cutoff and with cutoff 0, against the FP64
     boundary-MPS oracle computed here (small sizes)."""
     noise, _, syn = workload(d, "depolarizing", 8)
     ref = omps.decode_mps(d, noise.astype(np.float64), syn, chi, xl_column=d - 1)
-    lp, _, _, hist = decode(mld, d, noise, syn, chi, 0.0)
+    lp, _, _, hist = decode(mld, d, noise, syn, chi, cutoff, kernel)
     check_lead_and_posterior(lp, ref)
-    assert np.flatnonzero(hist[1:]).max() + 1 <= chi
+    if kernel == 1:                       # only the rank-adaptive kernel counts bonds
+        assert 0 < np.flatnonzero(hist[1:]).max() + 1 <= chi
+    else:
+        assert hist.sum() == 0
+
+
+def test_autotune_picks_a_truncation_kernel(mld):
+    """mld_autotune on a truncating chi times the rank-adaptive kernel beside
+    the fixed-shape kernel's CTA shapes and keeps the faster; decodes after
+    it still match the oracle."""
+    d, chi = 9, 8
+    noise, _, syn = workload(d, "depolarizing", 8)
+    ref = omps.decode_mps(d, noise.astype(np.float64), syn, chi, xl_column=d - 1)
+    code = mld.Code(d)
+    w = mld.mld_autotune(code, chi, mld.MLD_FP32, 4096)
+    assert w in (1, 2, 4, 8)
+    lp, _ = code.decode(torch.tensor(noise, device="cuda"), torch.tensor(syn.view(np.int64), device="cuda"), chi)
+    torch.cuda.synchronize()
+    assert code.status() == 0
+    check_lead_and_posterior(lp.cpu().numpy(), ref)
+    code.close()
 
 
 def test_truncated_deterministic_and_counters(mld):
@@ -143,8 +168,8 @@ def test_truncated_deterministic_and_counters(mld):
     its bin 0 counts site steps that ran in the global spill arena."""
     d, chi, B = 11, 16, 300
     noise, _, syn = workload(d, "depolarizing", B)
-    a, _, fa, ha = decode(mld, d, noise, syn, chi)
-    b, _, fb, hb = decode(mld, d, noise, syn, chi)
+    a, _, fa, ha = decode(mld, d, noise, syn, chi, kernel=1)
+    b, _, fb, hb = decode(mld, d, noise, syn, chi, kernel=1)
     np.testing.assert_array_equal(a, b)
     assert fa == fb and np.array_equal(ha, hb)
     finite = np.isfinite(a).any(axis=1)
@@ -153,11 +178,16 @@ def test_truncated_deterministic_and_counters(mld):
     assert np.flatnonzero(ha[1:]).max() + 1 <= chi
 
 
-def test_svd_cutoff_argument_checks(mld):
+def test_svd_cutoff_and_kernel_argument_checks(mld):
     code = mld.Code(9)
     for bad in (-1e-3, 1.0, float("nan")):
         with pytest.raises(mld.MldError):
             code.set_svd_cutoff(bad)
     code.set_svd_cutoff(0.0)
     code.set_svd_cutoff(1e-6)
+    for bad in (-1, 3):
+        with pytest.raises(mld.MldError):
+            code.set_truncation_kernel(bad)
+    for ok in (0, 1, 2):
+        code.set_truncation_kernel(ok)
     code.close()

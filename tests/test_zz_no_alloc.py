@@ -55,3 +55,36 @@ def test_noalloc_rejects_what_it_does_not_cover():
         mld.mld_decode_noalloc(code.handle, noise, mld.MLD_NOISE_TABLE, sy, 4, 8, mld.MLD_FP32, lp)
     assert e.value.status == 2
     code.close()
+
+
+def test_noalloc_leaves_free_device_memory_unchanged():
+    """The property the entry point exists for: after one warm-up call (which
+    looks up the scratch array's address), further calls with both noise
+    modes, with and without the argmax, for two codes in turn, allocate no
+    device memory."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_17230_gb300 as mld
+    bufs = []
+    for d, chi in [(5, 4), (9, 32)]:
+        n = d * d
+        code = mld.Code(d)
+        table = synth.depolarizing(n, 0.1).astype(np.float32)
+        syn = synth.syndromes_of(d, synth.sample_errors(d, table, 512, seed=d))
+        bufs.append((code, chi, torch.tensor(table, device="cuda"), torch.full((512,), 0.1, device="cuda"),
+                     torch.tensor(syn.view(np.int64), device="cuda"),
+                     torch.empty((512, 4), dtype=torch.float64, device="cuda"),
+                     torch.empty((512,), dtype=torch.uint8, device="cuda")))
+    code, chi, table, depol, sy, lp, am = bufs[0]
+    mld.mld_decode_noalloc(code.handle, table, mld.MLD_NOISE_TABLE, sy, 512, chi, mld.MLD_FP32, lp, am)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        for code, chi, table, depol, sy, lp, am in bufs:
+            mld.mld_decode_noalloc(code.handle, table, mld.MLD_NOISE_TABLE, sy, 512, chi, mld.MLD_FP32, lp, am)
+            mld.mld_decode_noalloc(code.handle, depol, mld.MLD_NOISE_DEPOL, sy, 512, chi, mld.MLD_FP32, lp, None,
+                                   check_status=False)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    for b in bufs:
+        b[0].close()
