@@ -11,7 +11,7 @@ generator in synth/, syndromes extracted.
 
 Other workloads (--workload): mixed (the d=3..13 graph batch), large (d=17
 and 25 at truncating chi), ler (logical-error rates of the d/p grid against
-the oracle), grad, dmle, dem.
+the oracle), grad, dmle, dem, point (one (d, chi, p) decode point).
 
 Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle
 on the host cores instead (a bounded sample per step).
@@ -43,12 +43,13 @@ TF32_PER_BF16 = 1.1 / 2.25          # nominal dense TF32 / BF16 tensor rates of 
 # DRAM bytes per syndrome of the decode kernel (dram__bytes_read.sum + write.sum of one ncu
 # capture of 8,192 syndromes of the headline kernel), valid only for the kernel sources they
 # were taken on: any change to them makes the traffic unknown (null).
-TRAFFIC_SOURCES_SHA = "3d9a42386b4f2832"
-TRAFFIC_BYTES_PER_SYNDROME = {0: (282.880e3 + 0.512e3) / 8192, 2: (284.672e3 + 3.328e3) / 8192}
+TRAFFIC_SOURCES_SHA = "a2b856029856e7f9"
+TRAFFIC_BYTES_PER_SYNDROME = {0: (286.208e3 + 1.536e3) / 8192, 2: (286.208e3 + 0.0) / 8192}
 
 
-# sources of the headline kernel (decode_exact_kernel<9, *>): its plan, layout and templates
-TRAFFIC_SOURCES = ("mld_plan.h", "mld_exact_impl.cuh", "mld_exact.h", "mld_exact.cu", "mld_internal.h")
+# sources of the headline kernel (decode_exact_kernel<9, *>): its plan, layout and templates (the
+# host-side code object declared beside them in mld_internal.h does not enter the kernel)
+TRAFFIC_SOURCES = ("mld_plan.h", "mld_exact_impl.cuh", "mld_exact.h", "mld_exact.cu")
 
 
 def kernel_sources_sha():
@@ -250,10 +251,16 @@ def run_mixed(args):
         e1.record()
         torch.cuda.synchronize()
         res[prec] = (e0.elapsed_time(e1) / args.steps, g)
+    import oracle
     per_d = {}
     for k, (d, p, syn) in enumerate(host):
         a = items_by_prec[mld.MLD_FP32][k][5].cpu().numpy()
         b = items_by_prec[mld.MLD_MIXED_TF32][k][5].cpu().numpy()
+        # error of both precisions against the FP64 oracle on a sample of this distance's syndromes
+        ns = 256
+        ref, _ = oracle.decode(d, p[:ns].astype(np.float32).astype(np.float64), syn[:ns],
+                               threads=os.cpu_count() or 1)
+        fin = np.isfinite(ref)
         # this distance alone: one mld_decode per precision on the same batch
         rate = {}
         for prec in (mld.MLD_FP32, mld.MLD_MIXED_TF32):
@@ -267,6 +274,13 @@ def run_mixed(args):
             torch.cuda.synchronize()
             rate[prec] = per / (e0.elapsed_time(e1) / 1e3)
         per_d[str(d)] = {"chi": MIXED_CHI[d], "max_abs_dlogP_mixed_vs_fp32": float(np.abs(a - b).max()),
+                         "max_abs_dlogP_fp32_vs_oracle": float(np.abs(a[:ns][fin] - ref[fin]).max()),
+                         "max_abs_dlogP_mixed_vs_oracle": float(np.abs(b[:ns][fin] - ref[fin]).max()),
+                         "oracle_sample": ns,
+                         "mixed_product_path": ("split-TF32 mma.sync tensor-core products (hi.hi + hi.lo + lo.hi) "
+                                                "for data-site products of at least 32x16x32, FP32 elsewhere")
+                         if d in (9, 11) else "FP32 FFMA products (the split-TF32 path is slower at this d; "
+                                              "a mixed request runs the FP32 kernel)",
                          "fp32_syndromes_per_s_alone": rate[mld.MLD_FP32],
                          "mixed_syndromes_per_s_alone": rate[mld.MLD_MIXED_TF32]}
     ms32, msm = res[mld.MLD_FP32][0], res[mld.MLD_MIXED_TF32][0]
@@ -297,6 +311,47 @@ def _posterior(x):
     return np.exp(x - np.logaddexp.reduce(x, axis=1, keepdims=True))
 
 
+def run_point(args):
+    """One (d, chi, p) point of the untruncated or truncated sweep on its own: --point-batch
+    depolarizing-p syndromes (seed config_seed(1, d, p)), FP32 and the mixed request, --warmup
+    untimed decodes then --steps timed ones (CUDA events, L2 flushed between them); reports
+    syndromes/s per precision and the counted flops rate. The small cases the ncu summaries
+    capture run through this."""
+    import torch
+    import paper_2605_17230_gb300 as mld
+    d, chi, p, Bp = args.point_d, args.point_chi, args.point_p, args.point_batch
+    noise = synth.depolarizing(d * d, p).astype(np.float32)
+    syn = synth.syndromes_of(d, synth.sample_errors(d, noise, Bp, seed=synth.config_seed(1, d, p)))
+    code = mld.Code(d)
+    nz = torch.tensor(noise, device="cuda")
+    sy = torch.tensor(syn.view(np.int64), device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    out = {}
+    for name, prec in (("fp32", mld.MLD_FP32), ("mixed", mld.MLD_MIXED_TF32)):
+        for _ in range(args.warmup):
+            code.decode(nz, sy, chi, prec)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            code.decode(nz, sy, chi, prec)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        st = code.status()
+        if st != 0:
+            raise RuntimeError("device status: " + mld.mld_status_string(st))
+        t = float(np.median(ms))
+        out[name] = {"syndromes_per_s": Bp / (t / 1e3), "ms_median": t,
+                     "counted_tflops": code.flops(chi, prec) * Bp / t / 1e9}
+    code.close()
+    print(json.dumps({"metric": "syndromes/s of one decode point", "workload": "point",
+                      "config": {"d": d, "chi": chi, "p": p, "syndromes": Bp, "steps": args.steps,
+                                 "warmup": args.warmup}, **out, "data": "synthetic"}), flush=True)
+
+
 def run_large(args):
     """The scale workload: rotated d=17 and 25, depolarizing p=0.12 and biased eta=100 (p=0.12),
     16,384 syndromes per point (seed config_seed(5, d, 0.12)), chi = 32, 64, 128. Every point reports
@@ -306,13 +361,15 @@ def run_large(args):
     import torch
     import paper_2605_17230_gb300 as mld
     Bl = args.large_batch
-    chis = (32, 64, 128)
+    chis = tuple(sorted(args.large_chi))
     out = []
-    for d in (17, 25):
+    for d in args.large_d:
         code = mld.Code(d)
         n = d * d
         for name, noise in (("depolarizing p=0.12", synth.depolarizing(n, 0.12)),
                             ("biased eta=100 p=0.12", synth.biased(n, 0.12, 100.0))):
+            if name.split()[0] not in args.large_noise:
+                continue
             noise = noise.astype(np.float32)
             E = synth.sample_errors(d, noise, Bl, seed=synth.config_seed(5, d, 0.12))
             true = synth.true_class(d, E)
@@ -334,8 +391,8 @@ def run_large(args):
                 if st != 0:
                     raise RuntimeError("device status: " + mld.mld_status_string(st))
                 res[chi] = (lp.cpu().numpy(), am.cpu().numpy(), ms, code.executed_flops(), code.bond_histogram())
-            ref = res[128][0]
-            lead = np.argmax(ref, axis=1)
+            ref = res[128][0] if 128 in res else None
+            lead = np.argmax(ref, axis=1) if ref is not None else None
             rows = np.arange(Bl)
             for chi in chis:
                 lp, am, ms, fl, h = res[chi]
@@ -343,9 +400,11 @@ def run_large(args):
                 rec = {"d": d, "chi": chi, "noise": name, "syndromes": Bl, "ms": ms,
                        "syndromes_per_s": Bl / (ms / 1e3), "executed_tflops": fl / ms / 1e9,
                        "bonds": _hist_summary(h), "ler": k / Bl, "ler_ci95": wilson_interval(k, Bl),
-                       "max_abs_dlogP_leading_vs_chi128": float(np.abs(lp[rows, lead] - ref[rows, lead]).max()),
-                       "max_abs_dposterior_vs_chi128": float(np.abs(_posterior(lp) - _posterior(ref)).max()),
-                       "argmax_equals_chi128": float(np.mean(am == res[128][1]))}
+                       "max_abs_dlogP_leading_vs_chi128":
+                           None if ref is None else float(np.abs(lp[rows, lead] - ref[rows, lead]).max()),
+                       "max_abs_dposterior_vs_chi128":
+                           None if ref is None else float(np.abs(_posterior(lp) - _posterior(ref)).max()),
+                       "argmax_equals_chi128": None if ref is None else float(np.mean(am == res[128][1]))}
                 out.append(rec)
                 print(json.dumps(rec), flush=True)
         code.close()
@@ -534,14 +593,23 @@ def main():
     ap.add_argument("--batch", type=int, default=B, help="syndromes per GPU per step (default: the "
                     "65536 of the workload; smaller values only for profiling captures)")
     ap.add_argument("--workload", default="metric",
-                    choices=["metric", "mixed", "grad", "large", "ler", "dmle", "dem"],
+                    choices=["metric", "mixed", "grad", "large", "ler", "dmle", "dem", "point"],
                     help="metric: the headline d=9 line (default); mixed: the 1,048,576-syndrome mixed-d "
                          "graph batch; grad: the adjoint on the d=7 workload; dmle: full-batch noise "
                          "estimation from 1,048,576 unlabelled d=9 syndromes; dem: detector-picture decode of "
                          "a d=9 X/Y/Z mechanism model; large: d=17, 25 at chi 32..128 (truncating); "
-                         "ler: logical-error rates of the d/p grid against the oracle")
+                         "ler: logical-error rates of the d/p grid against the oracle; point: one (d, chi, p) "
+                         "decode point, FP32 and mixed")
     ap.add_argument("--large-batch", type=int, default=16384)
+    ap.add_argument("--large-d", type=int, nargs="+", default=[17, 25], help="large: distances")
+    ap.add_argument("--large-chi", type=int, nargs="+", default=[32, 64, 128],
+                    help="large: bond caps (the comparison columns need 128)")
+    ap.add_argument("--large-noise", nargs="+", default=["depolarizing", "biased"], help="large: noise models")
     ap.add_argument("--ler-batch", type=int, default=65536)
+    ap.add_argument("--point-d", type=int, default=13, help="point: distance")
+    ap.add_argument("--point-chi", type=int, default=64, help="point: bond cap")
+    ap.add_argument("--point-p", type=float, default=0.10, help="point: depolarizing p")
+    ap.add_argument("--point-batch", type=int, default=32768, help="point: syndromes per decode")
     ap.add_argument("--mixed-total", type=int, default=1 << 20)
     args = ap.parse_args()
     rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)
@@ -560,6 +628,8 @@ def main():
         return run_large(args) if rank == 0 else None
     if args.workload == "ler":
         return run_ler(args) if rank == 0 else None
+    if args.workload == "point":
+        return run_point(args) if rank == 0 else None
 
     import torch
     import paper_2605_17230_gb300 as mld
