@@ -467,7 +467,8 @@ def run_ler(args):
 def run_grad(args):
     """Adjoint of the sweep on the d=7 workload with per-qubit biased noise:
     gradient of sum_b ln Pr(l_true | s_b) over 65,536 syndromes (and the same
-    at d=9, chi=32 over 16,384 syndromes, reported as d9_value)."""
+    at d=9, chi=32 over 16,384 syndromes, d=11 chi=32 over 4,096 and d=13
+    chi=64 over 1,024, reported as d9_value, d11_value, d13_value)."""
     import torch
     import paper_2605_17230_gb300 as mld
 
@@ -513,6 +514,12 @@ def run_grad(args):
         _, v9, f9 = one(9, 32, 16384)
         line["d9_value"] = v9
         line["d9_forward_only_value"] = f9
+        _, v11, f11 = one(11, 32, 4096)
+        line["d11_value"] = v11
+        line["d11_forward_only_value"] = f11
+        _, v13, f13 = one(13, 64, 1024)
+        line["d13_value"] = v13
+        line["d13_forward_only_value"] = f13
     print(json.dumps(line), flush=True)
 
 

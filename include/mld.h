@@ -203,7 +203,10 @@ void mld_graph_destroy(mld_graph* graph);
 
 /* Time the candidate CTA shapes (warps per block) of this code, chi and
  * precision on a synthetic batch of the given size and keep the fastest for
- * later decodes of this code object (per chi and precision). For a
+ * later decodes of this code object (per chi and precision). Where the
+ * per-warp state exceeds a block's shared memory (d = 13 untruncated) the
+ * candidates are the resident warps per SM of the global-workspace sweep
+ * (2, 4, 8, 16; *chosen_warps reports that count). For a
  * truncating chi the rank-adaptive sweep (4 units per block) is a candidate
  * beside the fixed-shape sweep's shapes, and the faster kernel is kept for
  * that chi (unless mld_code_set_truncation_kernel forces one). Synchronous. */
@@ -219,9 +222,14 @@ mld_status mld_autotune(const mld_code* code, int chi, int precision, int64_t sa
  *   dnoise     device double[n][4]: dL/dp_{q,P} (all four entries of a row
  *              treated as independent) is ADDED to it.
  * Each qubit factor's environment is contracted exactly, so chi must not
- * truncate (MLD_ERR_UNSUPPORTED otherwise) and d <= 11. The left and right
- * boundary states are kept dense on chip (the right states are carried back
- * through each column by the transposed factors). FP32 contraction, FP64
+ * truncate (MLD_ERR_UNSUPPORTED otherwise) and d <= 13. The left and right
+ * boundary states are kept dense (the right states are carried back through
+ * each column by the transposed factors): on chip for d <= 11; at d = 13 the
+ * states inside a column (128 KB each) live in a device workspace of about
+ * 1.7 MB per resident block, the corner-column states on chip. The left
+ * state at every column boundary is stored by the forward pass (a
+ * checkpoint per column) and the states inside a column are recomputed from
+ * it during the backward pass. FP32 contraction, FP64
  * accumulation in a fixed order, so reruns give the same bits. Asynchronous
  * on stream; uses a device workspace owned by the code object (not reentrant
  * per code). */

@@ -173,12 +173,14 @@ mld_status mld_autotune(const mld_code* Cc, int chi, int precision, int64_t samp
         st = MLD_ERR_CUDA;
     // candidates: warps per CTA of the fixed-shape or untruncated kernel and,
     // for a truncating chi, the rank-adaptive sweep (kernel 1) as well
+    // (global-workspace states: resident warps per SM 2, 4, 8, 16)
     const bool truncating = mld::make_plan(C->d, chi).svd_sites != 0;
+    const int wscale = mld::state_in_global_workspace(C, chi) ? 2 : 1;
     const int saved_kernel = C->trunc_kernel;
     int best_w = 0, best_k = 0;
     float best_ms = 0.f;
     for (int cand = truncating ? 0 : 1; st == MLD_OK && cand <= 4; ++cand) {
-        const int kern = cand == 0 ? 1 : 2, w = cand == 0 ? 4 : 1 << (cand - 1);
+        const int kern = cand == 0 ? 1 : 2, w = cand == 0 ? 4 : wscale << (cand - 1);
         C->trunc_kernel = truncating ? kern : saved_kernel;
         C->force_warps = cand == 0 ? 0 : w;
         mld_status r = mld_decode(C, dn, MLD_NOISE_TABLE, ds, sample_B, chi, precision, dl, nullptr, s);

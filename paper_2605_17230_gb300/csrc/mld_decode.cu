@@ -803,10 +803,15 @@ mld_status grow(T** buf, size_t* have, size_t bytes) {
 }
 
 // Truncating chi: the rank-adaptive kernel (one warp per unit) over all units
-// with small slice capacities on every resident warp; the units it hands
-// back go to a second pass of the same kernel with large capacities on one
-// block of warps per 4 SMs, and what that hands back (bonds above 128) to the
-// fixed-shape kernel in global-workspace mode. Later passes read their unit
+// on every resident warp, with the small slice capacities for chi <= 48 and
+// the mid ones (bonds up to 64) above, or the small ones if the mid
+// workspace cannot be allocated; the units it hands back go to a second pass
+// of the same kernel with large capacities on one block of warps per 4 SMs,
+// and what that hands back (bonds above 128) to the fixed-shape kernel in
+// global-workspace mode. (A unit handed back restarts from its first column
+// on few warps, so the first pass's capacities decide how long that tail
+// is: with bond 48 the few d=25 units whose middle cuts keep up to 64
+// values took as long as the whole first pass.) Later passes read their unit
 // count on the device and exit at once when it is zero. Control block
 // (bytes): [0] queue head of pass 1, [8] of pass 2, [16] overflow count of
 // pass 1, [20] of pass 2, [24] executed flops (f64, accumulated), [32] bond
@@ -827,12 +832,19 @@ mld_status decode_truncated(mld_code* C, const mld::Plan& P, const mld::SiteStep
     const int upb = mld::trunc_units_per_block();
     int64_t blocks1 = (int64_t)bps * sms;
     if (blocks1 > (units + upb - 1) / upb) blocks1 = (units + upb - 1) / upb;
-    const bool pass2 = chi > mld::kTruncSmall.max_bond;   // otherwise only carry rows can overflow
     int64_t blocks2 = (sms + 3) / 4;
-    const size_t ws1 = (size_t)blocks1 * upb * mld::kTruncSmall.slice();
     const size_t ws2 = (size_t)blocks2 * upb * mld::kTruncLarge.slice();
-    mld_status st = grow(&C->d_tws, &C->tws_bytes, std::max(ws1, ws2) * sizeof(float));
+    mld::TruncCaps caps1 = chi > mld::kTruncSmall.max_bond ? mld::kTruncMid : mld::kTruncSmall;
+    mld_status st = grow(&C->d_tws, &C->tws_bytes,
+                         std::max((size_t)blocks1 * upb * caps1.slice(), ws2) * sizeof(float));
+    if (st == MLD_ERR_NOMEM && caps1.max_bond != mld::kTruncSmall.max_bond) {
+        (void)cudaGetLastError();                          // clear the failed allocation's error
+        caps1 = mld::kTruncSmall;
+        st = grow(&C->d_tws, &C->tws_bytes,
+                  std::max((size_t)blocks1 * upb * caps1.slice(), ws2) * sizeof(float));
+    }
     if (st != MLD_OK) return st;
+    const bool pass2 = chi > caps1.max_bond;   // otherwise only carry rows can overflow
     if (!C->d_tctl) {
         if (cudaMalloc(&C->d_tctl, kTctlBytes) != cudaSuccess) return MLD_ERR_NOMEM;
         if (cudaMemset(C->d_tctl, 0, kTctlBytes) != cudaSuccess) return MLD_ERR_CUDA;
@@ -861,7 +873,7 @@ mld_status decode_truncated(mld_code* C, const mld::Plan& P, const mld::SiteStep
     ta.chi = chi;
     ta.cutoff = C->svd_cutoff;
     ta.arena = kTruncArena;
-    ta.caps = mld::kTruncSmall;
+    ta.caps = caps1;
     ta.ws = C->d_tws;
     ta.next_unit = reinterpret_cast<unsigned long long*>(ctl);
     ta.in_list = nullptr;
@@ -922,6 +934,22 @@ mld_status decode_truncated(mld_code* C, const mld::Plan& P, const mld::SiteStep
 }
 
 }  // namespace
+
+namespace mld {
+// Whether the untruncated or fixed-shape sweep of this code at this chi keeps
+// its per-warp state in the global workspace (then mld_autotune's candidates
+// are resident warps per SM).
+bool state_in_global_workspace(const mld_code* C, int chi) {
+    const Plan P = make_plan(C->d, chi);
+    const bool exact = P.svd_sites == 0 && exact_floats_per_warp(C->d) > 0;
+    int dev = 0, max_optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return false;
+    const size_t pw = (size_t)(exact ? exact_floats_per_warp(C->d) : P.floats_per_warp) * sizeof(float);
+    return pw > (size_t)max_optin;
+}
+}  // namespace mld
 
 extern "C" {
 
@@ -1068,12 +1096,17 @@ mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, co
     int64_t gws_warps = 0;
     if (pw > (size_t)max_optin) {
         // state larger than a block's shared memory: persistent warps with
-        // global-memory workspaces (16 resident warps per SM, halved until
-        // the workspace is at most 8 GiB)
+        // global-memory workspaces (R resident warps per SM: 16, or the
+        // autotuned count; halved until the workspace is at most 8 GiB)
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MLD_ERR_CUDA;
-        W = 4;
-        int64_t nw = (int64_t)sms * 16;
+        int R = 16;
+        const int key = chi * 4 + precision;
+        for (const auto& kv : C->tuned)
+            if (kv.first == key && kv.second >= 1 && kv.second <= 64) R = kv.second;
+        if (C->force_warps > 0) R = C->force_warps;
+        W = R < 4 ? R : 4;
+        int64_t nw = (int64_t)sms * R;
         while (nw > (int64_t)sms * W && (size_t)nw * pw > ((size_t)8 << 30)) nw /= 2;
         const int64_t need = ((units + W - 1) / W) * W;
         if (nw > need) nw = need;
@@ -1185,7 +1218,7 @@ mld_status mld_decode_grad(const mld_code* Cc, const float* noise, const uint64_
     if (!C || B < 0 || chi < 1) return MLD_ERR_INVALID_ARG;
     if (B == 0) return MLD_OK;
     if (!noise || !syn || !dnoise || (reinterpret_cast<uintptr_t>(noise) & 15)) return MLD_ERR_INVALID_ARG;
-    if (C->d > 11) return MLD_ERR_UNSUPPORTED;
+    if (C->d > 13) return MLD_ERR_UNSUPPORTED;
     mld_status st = MLD_OK;
     const mld_code::PlanDev* pd = get_plan(C, chi, &st);
     if (!pd) return st;
@@ -1200,7 +1233,8 @@ mld_status mld_decode_grad(const mld_code* Cc, const float* noise, const uint64_
         return MLD_ERR_CUDA;
     if (!mld::grad_dense_supported(d)) return MLD_ERR_UNSUPPORTED;
     {
-        // dense states on chip: one block per (syndrome, class) unit
+        // dense states (on chip, or in the block's global slice at d = 13): one
+        // block per (syndrome, class) unit
         const int64_t blocks = mld::grad_dense_blocks(d, sms, B);
         if (blocks < 1) return MLD_ERR_CUDA;
         const size_t bytes = (size_t)blocks * mld::grad_dense_workspace_floats(d) * sizeof(float);

@@ -1,14 +1,16 @@
-// Dense adjoint of the untruncated sweep, d = 3..11: d ln Z_l / d p_{q,P}.
+// Dense adjoint of the untruncated sweep, d = 3..13: d ln Z_l / d p_{q,P}.
 // (Each block sums its units' gradients in a fixed order and a second
 // kernel adds the blocks' sums in block order: reruns are bit-identical.)
 //
 // Z is linear in every qubit factor, so dZ/dw_q is the environment of that
 // factor (Sec. 3.2.4: the contraction is differentiable in the local error
-// probabilities, which the estimation of Eq. 10 back-propagates). For d <= 11
-// the exact boundary state over one corner column has at most 2^(d+1)
-// entries (one plaquette variable per row, absent plaquettes pinned to 0), so
-// the states are kept dense on chip. One thread block owns one (syndrome,
-// class) unit:
+// probabilities, which the estimation of Eq. 10 back-propagates). The exact
+// boundary state over one corner column has at most 2^(d+1) entries (one
+// plaquette variable per row, absent plaquettes pinned to 0), so the states
+// are kept dense: on chip for d <= 11; at d = 13 (128 KB per state inside a
+// column) the states inside a column live in the block's global slice and
+// only the two corner-column states R stay on chip. One thread block owns one
+// (syndrome, class) unit:
 //   forward   L_{c+1} = T_c L_c for c = 0..d-1, T_c applied qubit factor by
 //             qubit factor to states over d+2 bits and rescaled by a power of
 //             two per column; L_1..L_{d-1} go to the block's global slice, and
@@ -54,12 +56,15 @@ struct GradShape {
     // block's global slice, each step's environment sums are reduced at once,
     // and the representative's bits are recomputed where they are needed
     static constexpr bool BIG = D >= 11;
+    // d >= 13: the G states (the states inside a column) are in the block's
+    // global slice too; a thread takes several rests per step
+    static constexpr bool HUGE = D >= 13;
     static constexpr int NW = NT / 32;
     static constexpr int NG = (D + 1) / 2;          // stored G states: r = 0, 2, .., d-1
     // shared memory (floats)
     static constexpr int off_w = 0;                          // 4N factor weights (slot order Wp)
-    static constexpr int off_g = (4 * N + 3) & ~3;           // NG states of SIZE
-    static constexpr int off_l = off_g + NG * SIZE;           // HALF: L_c for the environment pass
+    static constexpr int off_g = (4 * N + 3) & ~3;           // NG states of SIZE (on chip unless HUGE)
+    static constexpr int off_l = off_g + (HUGE ? 0 : NG * SIZE);   // HALF: L_c for the environment pass
     static constexpr int off_ra = off_l + (BIG ? 0 : HALF);   // HALF: R_{c+1} (and staging)
     static constexpr int off_rb = off_ra + HALF;              // HALF: R_c being formed
     static constexpr int off_red = off_rb + HALF;             // per-warp environment sums:
@@ -69,7 +74,9 @@ struct GradShape {
     static constexpr int off_rep = off_misc + 32;             // N ints: representative x + 2z
     static constexpr int floats = off_rep + (BIG ? 0 : N);
     static constexpr int lfloats = (D - 1) * HALF;            // global: L_1..L_{d-1}
-    static constexpr int slice = lfloats + 8 * N;              // + the block's 4N double gradient sums
+    static constexpr int goff = lfloats + 8 * N;               // + the block's 4N double gradient sums
+    static constexpr int slice = goff + (HUGE ? NG * SIZE : 0);   // + the G states (HUGE)
+    static_assert(goff % 4 == 0 && slice % 4 == 0, "16-byte aligned slices");
     // blocks per SM that shared memory allows (the register budget is held to it)
     static constexpr int FIT0 = (227 * 1024) / (floats * 4 + 1024);
     static constexpr int FIT = FIT0 < 1 ? 1 : FIT0;   // one block of up to 227 KB always fits
@@ -222,6 +229,17 @@ __device__ __forceinline__ void pair_offsets(int rs, int r, int lay, int (&o)[16
 
 __device__ __forceinline__ constexpr int g4(int b0, int b1, int b2, int b3) { return b0 | (b1 << 1) | (b2 << 2) | (b3 << 3); }
 
+// f(rs) for every rest rs of a pair step this thread owns: one (or none)
+// while the block has a thread per rest, every NT-th one beyond that (d = 13).
+template <int REST, int NT, typename F>
+__device__ __forceinline__ void for_rests(int tid, F&& f) {
+    if constexpr (REST <= NT) {
+        if (tid < REST) f(tid);
+    } else {
+        for (int rs = tid; rs < REST; rs += NT) f(rs);
+    }
+}
+
 // factor r on the sixteen entries: Y = state between the factors from X
 __device__ __forceinline__ void pair_first(const float (&X)[16], const float (&W)[4], float (&Y)[16]) {
 #pragma unroll
@@ -327,7 +345,8 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
     extern __shared__ float4 smem4[];
     float* sm = reinterpret_cast<float*>(smem4);
     float* wts = sm + S::off_w;
-    float* G = sm + S::off_g;              // G + gslot(r) * SIZE: the state before factor r
+    float* Lg = g.lws + (size_t)blockIdx.x * S::slice;
+    float* G = S::HUGE ? Lg + S::goff : sm + S::off_g;   // G + gslot(r) * SIZE: the state before factor r
     float* Lb = sm + S::off_l;             // (d <= 9 only)
     float* Rcur = sm + S::off_ra;
     float* Rnxt = sm + S::off_rb;
@@ -335,10 +354,8 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
     float* env = sm + S::off_env;
     float* misc = sm + S::off_misc;
     int* rep = reinterpret_cast<int*>(sm + S::off_rep);   // (d <= 9 only)
-    float* Lg = g.lws + (size_t)blockIdx.x * S::slice;
     double* acc = reinterpret_cast<double*>(Lg + S::lfloats);   // this block's dL/dp, summed in unit order
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool owns2 = tid < S::REST2;
 
     for (int e = tid; e < 4 * N; e += NT) acc[e] = 0.0;
 
@@ -389,10 +406,10 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
                 float W0[4], W1[4];
                 factor_weights<D>(wts, r, c, W0);
                 factor_weights<D>(wts, r + 1, c, W1);
-                if (owns2) {
+                for_rests<S::REST2, NT>(tid, [&](int rs) {
                     int oi[16], oo[16];
-                    pair_offsets<D>(tid, r, r, oi);
-                    pair_offsets<D>(tid, r, r + 2, oo);
+                    pair_offsets<D>(rs, r, r, oi);
+                    pair_offsets<D>(rs, r, r + 2, oo);
                     float X[16], Y[16], Z[16];
 #pragma unroll
                     for (int m = 0; m < 16; ++m) X[m] = Fa[oi[m]];
@@ -400,7 +417,7 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
                     pair_second(Y, W1, Z);
 #pragma unroll
                     for (int m = 0; m < 16; ++m) Fb[oo[m]] = Z[m];
-                }
+                });
                 __syncthreads();
                 float* t = Fa; Fa = Fb; Fb = t;
             }
@@ -466,10 +483,10 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
                 float W0[4], W1[4];
                 factor_weights<D>(wts, r, c, W0);
                 factor_weights<D>(wts, r + 1, c, W1);
-                if (owns2) {
+                for_rests<S::REST2, NT>(tid, [&](int rs) {
                     int oi[16], oo[16];
-                    pair_offsets<D>(tid, r, r + 2, oi);
-                    pair_offsets<D>(tid, r, r, oo);
+                    pair_offsets<D>(rs, r, r + 2, oi);
+                    pair_offsets<D>(rs, r, r, oo);
                     float Gz[16], Gy[16], Gx[16];
                     const float* Gn = G + gslot<D>(r + 2) * SIZE;
 #pragma unroll
@@ -479,7 +496,7 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
                     float* Go = G + gslot<D>(r) * SIZE;
 #pragma unroll
                     for (int m = 0; m < 16; ++m) Go[oo[m]] = Gx[m];
-                }
+                });
                 __syncthreads();
             }
             if (c > 0) {
@@ -509,14 +526,14 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
                 factor_weights<D>(wts, r + 1, c, W1);
                 float e[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // factor r, then factor r+1
                 float* Fb = G + gslot<D>(r) * SIZE;
-                if (owns2) {
+                for_rests<S::REST2, NT>(tid, [&](int rs) {
                     int o0[16], o2[16];
-                    pair_offsets<D>(tid, r, r, o0);
-                    pair_offsets<D>(tid, r, r + 2, o2);
+                    pair_offsets<D>(rs, r, r, o0);
+                    pair_offsets<D>(rs, r, r + 2, o2);
                     const float* Gn = G + gslot<D>(r + 2) * SIZE;
                     float X[16], Gz[16], Y[16], Gy[16];
                     if (r == 0) {
-                        const int core = tid << 3;     // rest bits above positions 0, 1, 2 (bit d+1 from g)
+                        const int core = rs << 3;      // rest bits above positions 0, 1, 2 (bit d+1 from g)
 #pragma unroll
                         for (int m = 0; m < 16; ++m) {
                             const int lg = core | (m & 7) | ((m >> 3) << (D + 1));
@@ -554,7 +571,7 @@ __global__ void __launch_bounds__(GradShape<D>::NT, GradShape<D>::MINB) grad_den
                     pair_second(Y, W1, Z);
 #pragma unroll
                     for (int m = 0; m < 16; ++m) Fb[o2[m]] = Z[m];
-                }
+                });
                 const float tot = reduce_scatter8(e, lane);
                 if ((lane & 3) == 0) {
                     const int slot = lane >> 2;
@@ -685,7 +702,7 @@ bool launch_d(const GradDenseArgs& a, int64_t blocks, cudaStream_t s) {
 
 }  // namespace
 
-bool grad_dense_supported(int d) { return d == 3 || d == 5 || d == 7 || d == 9 || d == 11; }
+bool grad_dense_supported(int d) { return d == 3 || d == 5 || d == 7 || d == 9 || d == 11 || d == 13; }
 
 int64_t grad_dense_blocks(int d, int sms, int64_t B) {
     switch (d) {
@@ -694,6 +711,7 @@ int64_t grad_dense_blocks(int d, int sms, int64_t B) {
         case 7: return blocks_d<7>(sms, B);
         case 9: return blocks_d<9>(sms, B);
         case 11: return blocks_d<11>(sms, B);
+        case 13: return blocks_d<13>(sms, B);
     }
     return 0;
 }
@@ -705,6 +723,7 @@ int64_t grad_dense_workspace_floats(int d) {
         case 7: return GradShape<7>::slice;
         case 9: return GradShape<9>::slice;
         case 11: return GradShape<11>::slice;
+        case 13: return GradShape<13>::slice;
     }
     return 0;
 }
@@ -716,6 +735,7 @@ bool launch_grad_dense(int d, const GradDenseArgs& a, int64_t blocks, cudaStream
         case 7: return launch_d<7>(a, blocks, s);
         case 9: return launch_d<9>(a, blocks, s);
         case 11: return launch_d<11>(a, blocks, s);
+        case 13: return launch_d<13>(a, blocks, s);
     }
     return false;
 }

@@ -1,4 +1,4 @@
-// Launcher of the dense adjoint for untruncated sweeps, d = 3..11.
+// Launcher of the dense adjoint for untruncated sweeps, d = 3..13.
 #pragma once
 
 #include <cuda_runtime.h>

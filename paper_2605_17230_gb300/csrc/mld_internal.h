@@ -30,7 +30,8 @@ struct mld_code {
     // global workspace for states larger than a block's shared memory
     float* d_gws = nullptr;
     size_t gws_bytes = 0;
-    // autotuned warps per CTA, keyed by chi * 4 + precision
+    // autotuned warps per CTA (resident warps per SM when the per-warp state
+    // is in the global workspace), keyed by chi * 4 + precision
     std::vector<std::pair<int, int>> tuned;
     int force_warps = 0;                 // set only while mld_autotune times a candidate
     // workspace of the adjoint kernel
@@ -51,3 +52,7 @@ struct mld_code {
     int trunc_kernel = 0;
     std::vector<std::pair<int, int>> trunc_tuned;
 };
+
+namespace mld {
+bool state_in_global_workspace(const mld_code* C, int chi);
+}

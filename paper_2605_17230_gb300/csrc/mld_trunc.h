@@ -7,8 +7,9 @@
 namespace mld {
 
 // Capacities of one unit's shapes and global slice (floats). The first pass
-// over all units uses the small ones with every resident warp; units that
-// exceed them are decoded by a second pass with the large ones on few warps.
+// over all units runs on every resident warp with the small ones (chi <= 48)
+// or the mid ones (bond 64, 4.5 MB per warp); units that exceed them are
+// decoded by a second pass with the large ones on few warps.
 struct TruncCaps {
     int max_bond;        // kept bond per cut
     int max_rows;        // carry rows
@@ -18,6 +19,7 @@ struct TruncCaps {
     __host__ __device__ int64_t slice() const { return 2 * mps + q + spill; }
 };
 constexpr TruncCaps kTruncSmall{48, 192, 128 * 1024, 256 * 1024, 64 * 1024};
+constexpr TruncCaps kTruncMid{64, 256, 256 * 1024, 512 * 1024, 128 * 1024};
 constexpr TruncCaps kTruncLarge{128, 512, 1024 * 1024, 2048 * 1024, 384 * 1024};
 
 struct TruncArgs {

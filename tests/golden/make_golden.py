@@ -9,7 +9,7 @@
   elements (first line of Eq. 7).
 * large_mps.txt: ln Z_l(s) of the FP64 boundary-MPS sweep (Sec. 3.2.1, left
   QR sweep then right-to-left SVD keeping min(chi, #values), no cutoff) for
-  d=13, 17 and 25: depolarizing p=0.12 and biased eta=100 at p=0.12,
+  d=13, 15, 17 and 25: depolarizing p=0.12 and biased eta=100 at p=0.12,
   syndromes from seed config_seed(5, d, 0.12), the X_L string of the l_X = 1
   classes on column d-1. Noise tables are the FP32-rounded ones the GPU tests
   pass.
@@ -31,8 +31,9 @@ import oracle  # noqa: E402
 import synth  # noqa: E402
 
 
-LARGE_CASES = [(13, 32, "depolarizing", 16), (13, 56, "depolarizing", 2), (17, 32, "depolarizing", 4),
-               (17, 64, "depolarizing", 4), (17, 32, "biased", 4), (17, 64, "biased", 4), (25, 32, "depolarizing", 2)]
+LARGE_CASES = [(13, 32, "depolarizing", 16), (13, 56, "depolarizing", 2), (15, 72, "depolarizing", 2),
+               (17, 32, "depolarizing", 4), (17, 64, "depolarizing", 4), (17, 32, "biased", 4), (17, 64, "biased", 4),
+               (25, 32, "depolarizing", 2)]
 
 
 def large_noise(d, kind):

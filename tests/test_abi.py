@@ -104,7 +104,8 @@ def test_host_side_argument_checks():
     assert grad(P(c5.handle), fake, fake, -1, 8, None, None, fake, None) == INVALID
     assert grad(P(c5.handle), fake, fake, 4, 0, None, None, fake, None) == INVALID
     assert grad(P(c5.handle), fake, fake, 4, 8, None, None, None, None) == INVALID       # no dnoise
-    assert grad(P(c13.handle), fake, fake, 4, 64, None, None, fake, None) == UNSUPPORTED
+    c15 = mld.Code(15)
+    assert grad(P(c15.handle), fake, fake, 4, 128, None, None, fake, None) == UNSUPPORTED   # d > 13
 
 
 def test_wilson_interval_matches_scipy():

@@ -122,6 +122,34 @@ def test_gradient_d11_one_block_per_sm(mld):
     np.testing.assert_allclose(dn.cpu().numpy(), ref, rtol=1e-4, atol=1e-4 * np.abs(ref).max())
 
 
+def test_gradient_d13_global_states(mld):
+    """d = 13, chi = 64 (untruncated): the states inside a column (128 KB
+    each) live in the block's global slice and each thread takes four rests
+    per pair step; ln Z and the gradient against the oracle's exact
+    derivative, two syndromes of per-qubit lognormal biased noise."""
+    d, chi, B = 13, 64, 2
+    n, noise, E, syn = _setup(d, B, seed=13)
+    code = mld.Code(d)
+    up = np.random.default_rng(13).normal(size=(B, 4))
+    nz = torch.tensor(noise, device="cuda")
+    sy = torch.tensor(syn.view(np.int64), device="cuda")
+    dn = torch.zeros((n, 4), dtype=torch.float64, device="cuda")
+    lp = torch.zeros((B, 4), dtype=torch.float64, device="cuda")
+    mld.mld_decode_grad(code.handle, nz, sy, B, chi, torch.tensor(up, device="cuda"), lp, dn)
+    torch.cuda.synchronize()
+    assert code.status() == 0
+    lz, g = oracle.coset_dlogz(d, noise.astype(np.float64), oracle.representatives(d, syn).reshape(-1, n))
+    np.testing.assert_allclose(lp.cpu().numpy(), lz.reshape(-1, 4), rtol=0, atol=1e-5)
+    ref = np.einsum("bl,blqp->qp", up, g.reshape(B, 4, n, 4))
+    np.testing.assert_allclose(dn.cpu().numpy(), ref, rtol=1e-4, atol=1e-4 * np.abs(ref).max())
+    # the autograd path at d = 13: d/dtheta of sum ln Z_l over the same units
+    tab = nz.double().requires_grad_(True)
+    mld.log_coset_probabilities(code, tab, sy, chi).sum().backward()
+    ref1 = g.reshape(B, 4, n, 4).sum(axis=(0, 1))
+    np.testing.assert_allclose(tab.grad.cpu().numpy(), ref1, rtol=1e-4, atol=1e-4 * np.abs(ref1).max())
+    code.close()
+
+
 def test_euler_identity_per_unit(mld):
     """sum_P p_{q,P} d ln Z / d p_{q,P} = 1 for every qubit (Z is linear in
     each row), for a single (syndrome, class) unit."""

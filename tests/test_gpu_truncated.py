@@ -1,5 +1,6 @@
 """Parity of the truncating sweep (chi below the exact bond 2^floor(d/2)) with
-the FP64 boundary-MPS oracle, at the sizes of the d=13, 17 and 25 workloads.
+the FP64 boundary-MPS oracle, at the sizes of the d=13, 17 and 25 workloads
+(and d=15, where cutoff 0 drives bonds past the first pass's capacity).
 
 The rank-adaptive kernel keeps k = min(chi, #{sigma > cutoff * sigma_1}) at
 every cut (default cutoff 1e-7, below FP32 resolution); with cutoff 0 it keeps
@@ -90,8 +91,8 @@ LARGE = [(13, 32, "depolarizing", 16), (17, 32, "depolarizing", 4), (17, 64, "de
 def test_large_d_vs_fp64_mps(mld, d, chi, kind, B, cutoff):
     """d = 13, 17, 25 at chi = 32 and 64 (the scale workloads), depolarizing
     p=0.12 and biased eta=100, with the default cutoff and with cutoff 0 (the
-    oracle's keep-min(chi, #values) rule, where chi = 64 sends units with
-    bonds above 48 to the second, large-capacity pass)."""
+    oracle's keep-min(chi, #values) rule, where chi = 64 keeps bonds above
+    48 in the first pass, which runs with the mid capacities above chi 48)."""
     ref = golden_large()[(d, chi, kind)]
     noise, _, syn = workload(d, kind, B)
     lp, am, flops, hist = decode(mld, d, noise, syn, chi, cutoff)
@@ -99,14 +100,26 @@ def test_large_d_vs_fp64_mps(mld, d, chi, kind, B, cutoff):
     assert flops > 0 and hist[1:].sum() > 0 and np.flatnonzero(hist[1:]).max() + 1 <= min(chi, 64)
 
 
-def test_pass2_bonds_above_48_vs_fp64_mps(mld):
+def test_mid_capacity_bonds_above_48_vs_fp64_mps(mld):
     """d=13, chi=56, cutoff 0: the middle cuts keep up to 56 values, beyond the
-    first pass's 48, so these units are decoded by the large-capacity pass."""
+    small capacities (bond 48), so the first pass runs with the mid ones
+    (bond 64) and decodes these units itself."""
     ref = golden_large()[(13, 56, "depolarizing")]
     noise, _, syn = workload(13, "depolarizing", 2)
     lp, _, _, hist = decode(mld, 13, noise, syn, 56, 0.0)
     check_lead_and_posterior(lp, ref)
-    assert hist[49:].sum() > 0                 # bonds above the first pass's cap occurred
+    assert hist[49:].sum() > 0                 # bonds above the small capacities occurred
+
+
+def test_pass2_bonds_above_64_vs_fp64_mps(mld):
+    """d=15, chi=72, cutoff 0: the middle cuts keep 72 values (the exact rank
+    is 128), beyond the first pass's bond 64, so these units are handed back
+    and decoded by the large-capacity pass."""
+    ref = golden_large()[(15, 72, "depolarizing")]
+    noise, _, syn = workload(15, "depolarizing", 2)
+    lp, _, _, hist = decode(mld, 15, noise, syn, 72, 0.0)
+    check_lead_and_posterior(lp, ref)
+    assert hist[64] > 0                        # the last bin counts kept bonds of 64 and more
 
 
 def test_d17_chi128_vs_exact_oracle_64_syndromes(mld):
