@@ -216,6 +216,18 @@ def run_reference(args, rank, world):
 MIXED_CHI = {3: 16, 5: 16, 7: 16, 9: 32, 11: 32, 13: 64}
 
 
+# what a mixed-precision request runs at each d of the mixed batch
+PRODUCT_PATH = {
+    0: "FP32 FFMA products (the split-TF32 path is slower at this d; a mixed request runs the FP32 kernel)",
+    9: "split-TF32 mma.sync tensor-core products (hi.hi + hi.lo + lo.hi) for data-site products of at "
+       "least 32x16x32, FP32 elsewhere",
+    11: "split-TF32 mma.sync tensor-core products (hi.hi + hi.lo + lo.hi) for data-site products of at "
+        "least 32x16x32, FP32 elsewhere",
+    13: "dense-state FP32 column transfer (untruncated chi; no product is MMA-shaped; a mixed request "
+        "runs the same kernel)",
+}
+
+
 def run_mixed(args):
     """Mixed batch (1,048,576 syndromes, d uniform over 3..13, p ~ U[0.02, 0.18]
     per syndrome, chi by d) decoded by one CUDA-graph launch."""
@@ -277,10 +289,7 @@ def run_mixed(args):
                          "max_abs_dlogP_fp32_vs_oracle": float(np.abs(a[:ns][fin] - ref[fin]).max()),
                          "max_abs_dlogP_mixed_vs_oracle": float(np.abs(b[:ns][fin] - ref[fin]).max()),
                          "oracle_sample": ns,
-                         "mixed_product_path": ("split-TF32 mma.sync tensor-core products (hi.hi + hi.lo + lo.hi) "
-                                                "for data-site products of at least 32x16x32, FP32 elsewhere")
-                         if d in (9, 11) else "FP32 FFMA products (the split-TF32 path is slower at this d; "
-                                              "a mixed request runs the FP32 kernel)",
+                         "mixed_product_path": PRODUCT_PATH.get(d, PRODUCT_PATH[0]),
                          "fp32_syndromes_per_s_alone": rate[mld.MLD_FP32],
                          "mixed_syndromes_per_s_alone": rate[mld.MLD_MIXED_TF32]}
     ms32, msm = res[mld.MLD_FP32][0], res[mld.MLD_MIXED_TF32][0]
@@ -323,6 +332,8 @@ def run_point(args):
     noise = synth.depolarizing(d * d, p).astype(np.float32)
     syn = synth.syndromes_of(d, synth.sample_errors(d, noise, Bp, seed=synth.config_seed(1, d, p)))
     code = mld.Code(d)
+    if args.point_exact_kernel:
+        code.set_exact_kernel(args.point_exact_kernel)
     nz = torch.tensor(noise, device="cuda")
     sy = torch.tensor(syn.view(np.int64), device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -349,7 +360,8 @@ def run_point(args):
     code.close()
     print(json.dumps({"metric": "syndromes/s of one decode point", "workload": "point",
                       "config": {"d": d, "chi": chi, "p": p, "syndromes": Bp, "steps": args.steps,
-                                 "warmup": args.warmup}, **out, "data": "synthetic"}), flush=True)
+                                 "warmup": args.warmup, "exact_kernel": args.point_exact_kernel},
+                      **out, "data": "synthetic"}), flush=True)
 
 
 def run_large(args):
@@ -617,6 +629,8 @@ def main():
     ap.add_argument("--point-chi", type=int, default=64, help="point: bond cap")
     ap.add_argument("--point-p", type=float, default=0.10, help="point: depolarizing p")
     ap.add_argument("--point-batch", type=int, default=32768, help="point: syndromes per decode")
+    ap.add_argument("--point-exact-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="point, untruncated chi: 0 by d, 1 boundary-MPS kernel, 2 dense-state kernel")
     ap.add_argument("--mixed-total", type=int, default=1 << 20)
     args = ap.parse_args()
     rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)

@@ -36,7 +36,7 @@ EXPORTED_SYMBOLS = ["mld_code_create_rotated", "mld_code_destroy", "mld_code_inf
                     "mld_graph_launch", "mld_graph_destroy", "mld_autotune", "mld_decode_grad",
                     "mld_decode_dem", "mld_status_string", "mld_code_set_svd_cutoff",
                     "mld_decode_executed_flops", "mld_decode_bond_histogram", "mld_measure_fp32_peak",
-                    "mld_code_set_truncation_kernel"]
+                    "mld_code_set_truncation_kernel", "mld_code_set_exact_kernel"]
 
 _lib = None
 
@@ -112,6 +112,8 @@ def load(build_if_missing: bool = True):
     lib.mld_decode_bond_histogram.restype = I
     lib.mld_code_set_truncation_kernel.argtypes = [P, I]
     lib.mld_code_set_truncation_kernel.restype = I
+    lib.mld_code_set_exact_kernel.argtypes = [P, I]
+    lib.mld_code_set_exact_kernel.restype = I
     lib.mld_measure_fp32_peak.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]
     lib.mld_measure_fp32_peak.restype = I
     lib.mld_decode_launches.argtypes = []
@@ -286,6 +288,13 @@ class Code:
     def set_svd_cutoff(self, rel: float):
         """Relative singular-value cutoff of truncating chi (mld_code_set_svd_cutoff)."""
         _check(load().mld_code_set_svd_cutoff(ctypes.c_void_p(self.handle), float(rel)), "mld_code_set_svd_cutoff")
+
+    def set_exact_kernel(self, which: int):
+        """Untruncated chi: 0 by d (default; the dense-state kernel at d=13),
+        1 the boundary-MPS kernel, 2 the dense-state kernel (d = 11, 13)
+        (mld_code_set_exact_kernel)."""
+        _check(load().mld_code_set_exact_kernel(ctypes.c_void_p(self.handle), int(which)),
+               "mld_code_set_exact_kernel")
 
     def set_truncation_kernel(self, which: int):
         """0: chosen per chi (default); 1: rank-adaptive; 2: fixed-shape

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "mld_checks.h"
+#include "mld_dense.h"
 #include "mld_internal.h"
 
 namespace {
@@ -171,18 +172,23 @@ mld_status mld_autotune(const mld_code* Cc, int chi, int precision, int64_t samp
          cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
          cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         st = MLD_ERR_CUDA;
-    // candidates: warps per CTA of the fixed-shape or untruncated kernel and,
-    // for a truncating chi, the rank-adaptive sweep (kernel 1) as well
-    // (global-workspace states: resident warps per SM 2, 4, 8, 16)
+    // candidates: warps per CTA of the fixed-shape or untruncated kernel
+    // (global-workspace states: resident warps per SM 2, 4, 8, 16); for a
+    // truncating chi the rank-adaptive sweep (kernel 1) as well; for an
+    // untruncated chi at d = 11, 13 the dense-state kernel as well
     const bool truncating = mld::make_plan(C->d, chi).svd_sites != 0;
+    const bool dense_cand = !truncating && mld::dense_exact_supported(C->d) && C->exact_kernel == 0;
+    const int saved_kernel = C->trunc_kernel, saved_exact = C->exact_kernel;
+    if (dense_cand) C->exact_kernel = 1;          // the boundary-MPS kernel's shapes
     const int wscale = mld::state_in_global_workspace(C, chi) ? 2 : 1;
-    const int saved_kernel = C->trunc_kernel;
-    int best_w = 0, best_k = 0;
+    int best_cand = 0, best_w = 0, best_k = 0;
+    bool have = false;
     float best_ms = 0.f;
-    for (int cand = truncating ? 0 : 1; st == MLD_OK && cand <= 4; ++cand) {
-        const int kern = cand == 0 ? 1 : 2, w = cand == 0 ? 4 : wscale << (cand - 1);
+    for (int cand = truncating ? 0 : (dense_cand ? -1 : 1); st == MLD_OK && cand <= 4; ++cand) {
+        const int kern = cand == 0 ? 1 : 2, w = cand < 0 ? 0 : (cand == 0 ? 4 : wscale << (cand - 1));
         C->trunc_kernel = truncating ? kern : saved_kernel;
-        C->force_warps = cand == 0 ? 0 : w;
+        C->exact_kernel = dense_cand ? (cand < 0 ? 2 : 1) : saved_exact;
+        C->force_warps = cand <= 0 ? 0 : w;
         mld_status r = mld_decode(C, dn, MLD_NOISE_TABLE, ds, sample_B, chi, precision, dl, nullptr, s);
         if (r != MLD_OK) { st = r; break; }
         cudaEventRecord(e0, s);
@@ -192,21 +198,31 @@ mld_status mld_autotune(const mld_code* Cc, int chi, int precision, int64_t samp
         if (cudaEventSynchronize(e1) != cudaSuccess) { st = MLD_ERR_CUDA; break; }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (best_w == 0 || ms < best_ms) { best_w = w; best_k = kern; best_ms = ms; }
+        if (!have || ms < best_ms) { have = true; best_cand = cand; best_w = w; best_k = kern; best_ms = ms; }
     }
     C->force_warps = 0;
     C->trunc_kernel = saved_kernel;
-    if (st == MLD_OK && best_w > 0) {
-        const int key = chi * 4 + precision;
+    C->exact_kernel = saved_exact;
+    if (st == MLD_OK && have) {
         bool found = false;
-        for (auto& kv : C->tuned)
-            if (kv.first == key) { kv.second = best_w; found = true; }
-        if (!found) C->tuned.emplace_back(key, best_w);
+        if (best_w > 0) {
+            const int key = chi * 4 + precision;
+            for (auto& kv : C->tuned)
+                if (kv.first == key) { kv.second = best_w; found = true; }
+            if (!found) C->tuned.emplace_back(key, best_w);
+        }
         if (truncating) {
             found = false;
             for (auto& kv : C->trunc_tuned)
                 if (kv.first == chi) { kv.second = best_k; found = true; }
             if (!found) C->trunc_tuned.emplace_back(chi, best_k);
+        }
+        if (dense_cand) {
+            const int which = best_cand < 0 ? 2 : 1;
+            found = false;
+            for (auto& kv : C->exact_tuned)
+                if (kv.first == chi) { kv.second = which; found = true; }
+            if (!found) C->exact_tuned.emplace_back(chi, which);
         }
         if (chosen) *chosen = best_w;
         if (mld_decode_status(C) != MLD_OK) st = MLD_ERR_NUMERIC;

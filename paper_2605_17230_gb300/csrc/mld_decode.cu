@@ -27,6 +27,7 @@
 #include "mld_checks.h"
 #include "mld_dem.h"
 #include "mld_grad.h"
+#include "mld_dense.h"
 #include "mld_internal.h"
 #include "mld_trunc.h"
 
@@ -936,11 +937,25 @@ mld_status decode_truncated(mld_code* C, const mld::Plan& P, const mld::SiteStep
 }  // namespace
 
 namespace mld {
+// Whether an untruncated decode of this code runs the dense-state kernel:
+// on request (mld_code_set_exact_kernel 2, d = 11 or 13), as mld_autotune
+// chose for this chi, or by default at d = 13, where the exact boundary MPS
+// (298 KB per unit) no longer fits shared memory and the dense state (128 KB)
+// does.
+bool uses_dense_exact(const mld_code* C, const Plan& P) {
+    if (P.svd_sites != 0 || !dense_exact_supported(C->d) || C->exact_kernel == 1) return false;
+    if (C->exact_kernel == 2) return true;
+    for (const auto& kv : C->exact_tuned)
+        if (kv.first == P.chi) return kv.second == 2;
+    return C->d == 13;
+}
+
 // Whether the untruncated or fixed-shape sweep of this code at this chi keeps
 // its per-warp state in the global workspace (then mld_autotune's candidates
 // are resident warps per SM).
 bool state_in_global_workspace(const mld_code* C, int chi) {
     const Plan P = make_plan(C->d, chi);
+    if (uses_dense_exact(C, P)) return false;
     const bool exact = P.svd_sites == 0 && exact_floats_per_warp(C->d) > 0;
     int dev = 0, max_optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -1010,13 +1025,24 @@ mld_status mld_code_layout(const mld_code* C, int32_t* type, int32_t* sup, uint8
 
 int mld_decode_launches(void) { return 3; }
 
+mld_status mld_code_set_exact_kernel(mld_code* C, int which) {
+    if (!C || which < 0 || which > 2) return MLD_ERR_INVALID_ARG;
+    if (which == 2 && !mld::dense_exact_supported(C->d)) return MLD_ERR_UNSUPPORTED;
+    C->exact_kernel = which;
+    return MLD_OK;
+}
+
 mld_status mld_decode_flops(const mld_code* C, int chi, int precision, double* out) {
     if (!C || chi < 1 || !out) return MLD_ERR_INVALID_ARG;
     if (precision != MLD_FP32 && precision != MLD_MIXED_BF16 && precision != MLD_MIXED_TF32)
         return MLD_ERR_INVALID_ARG;
-    // both kernels sweep columns 0..d-2 once per l_Z and the last column once
+    // every kernel sweeps columns 0..d-2 once per l_Z and the last column once
     // per class
     const mld::Plan P = mld::make_plan(C->d, chi);
+    if (mld::uses_dense_exact(C, P)) {
+        *out = mld::dense_exact_flops_per_syndrome(C->d);
+        return MLD_OK;
+    }
     *out = 2.0 * (P.flops_per_coset - P.flops_last_col) + 4.0 * P.flops_last_col;
     return MLD_OK;
 }
@@ -1083,6 +1109,28 @@ mld_status mld_decode(const mld_code* Cc, const float* noise, int noise_mode, co
             return MLD_ERR_CUDA;
         const mld_status ts = decode_truncated(C, P, pd->d_steps, noise, noise_mode, syn, B, chi, logP, s);
         if (ts != MLD_OK) return ts;
+        if (argmax) {
+            mld::argmax_kernel<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(logP, argmax, B);
+            if (cudaGetLastError() != cudaSuccess) return MLD_ERR_CUDA;
+        }
+        return MLD_OK;
+    }
+    if (mld::uses_dense_exact(C, P)) {
+        // untruncated, dense boundary state (FP32 for either precision: no
+        // product is MMA-shaped)
+        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+        if (!mld::launch_noise_check(noise, noise_mode, noise_mode == MLD_NOISE_TABLE ? C->n : B, C->d_status, s))
+            return MLD_ERR_CUDA;
+        mld::DenseArgs da;
+        da.dmask = C->d_dmask;
+        da.noise = noise;
+        da.syn = syn;
+        da.logP = logP;
+        da.status = C->d_status;
+        da.B = B;
+        da.words = C->words;
+        da.noise_mode = noise_mode;
+        if (!mld::launch_dense_exact(C->d, da, s)) return MLD_ERR_CUDA;
         if (argmax) {
             mld::argmax_kernel<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(logP, argmax, B);
             if (cudaGetLastError() != cudaSuccess) return MLD_ERR_CUDA;

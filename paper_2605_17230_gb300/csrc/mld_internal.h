@@ -51,8 +51,15 @@ struct mld_code {
     // trunc_tuned holds mld_autotune's choice per chi
     int trunc_kernel = 0;
     std::vector<std::pair<int, int>> trunc_tuned;
+    // which kernel runs an untruncated chi: 0 mld_autotune's choice for that
+    // chi if it timed one (exact_tuned), else by d (the dense-state kernel at
+    // d = 13, the boundary-MPS kernel elsewhere); 1 the boundary-MPS kernel;
+    // 2 the dense-state kernel (d = 11, 13)
+    int exact_kernel = 0;
+    std::vector<std::pair<int, int>> exact_tuned;
 };
 
 namespace mld {
 bool state_in_global_workspace(const mld_code* C, int chi);
+bool uses_dense_exact(const mld_code* C, const Plan& P);
 }

@@ -307,6 +307,63 @@ def test_d13_exact_global_workspace(mld, prec):
     check_argmax(am, ref)
 
 
+@pytest.mark.parametrize("d", [11, 13])
+@pytest.mark.parametrize("mode", ["table", "depolarizing"])
+def test_exact_kernels_dense_and_mps_vs_oracle(mld, d, mode):
+    """Untruncated chi at d = 11 and 13 by both kernels: the boundary-MPS
+    kernel (sites at the exact cut ranks) and the dense-state kernel (the
+    2^(d+2)-entry column state in shared memory, factors applied in place),
+    each against the FP64 oracle, with a per-qubit table and with one
+    depolarizing strength per syndrome; a ragged batch of 37 syndromes."""
+    n, chi, B = d * d, 2 ** (d // 2), 37
+    rng = np.random.default_rng(d)
+    if mode == "table":
+        noise = synth.lognormal_biased(n, seed=d).astype(np.float32)
+        E = synth.sample_errors(d, noise, B, seed=d + 1)
+        ref, _ = oracle.decode(d, noise.astype(np.float64), synth.syndromes_of(d, E))
+        dev_noise = torch.tensor(noise, device="cuda")
+        nmode = mld.MLD_NOISE_TABLE
+    else:
+        p = rng.uniform(0.02, 0.18, size=B).astype(np.float32)
+        E = np.stack([synth.sample_errors(d, synth.depolarizing(n, float(p[b])), 1, seed=100 * d + b)[0]
+                      for b in range(B)])
+        # the oracle gets the rows the kernels form in FP32: (1 - p, p/3, p/3, p/3)
+        rows = [np.array([np.float32(1) - p[b]] + [p[b] * np.float32(1.0 / 3.0)] * 3, np.float32)
+                for b in range(B)]
+        ref = np.concatenate([oracle.decode(d, np.tile(rows[b].astype(np.float64), (n, 1)),
+                                            synth.syndromes_of(d, E[b:b + 1]))[0] for b in range(B)])
+        dev_noise = torch.tensor(p, device="cuda")
+        nmode = mld.MLD_NOISE_DEPOL
+    syn = synth.syndromes_of(d, E)
+    sy = torch.tensor(syn.view(np.int64), device="cuda")
+    outs = {}
+    for which in (1, 2):
+        C = mld.Code(d)
+        C.set_exact_kernel(which)
+        lp = torch.empty((B, 4), dtype=torch.float64, device="cuda")
+        am = torch.empty((B,), dtype=torch.uint8, device="cuda")
+        mld.mld_decode(C.handle, dev_noise, nmode, sy, B, chi, mld.MLD_FP32, lp, am)
+        torch.cuda.synchronize()
+        assert C.status() == 0
+        outs[which] = lp.cpu().numpy()
+        np.testing.assert_allclose(outs[which], ref, rtol=0, atol=TOL)
+        check_argmax(am.cpu().numpy(), ref)
+        C.close()
+
+
+def test_exact_kernel_selector_arguments(mld):
+    C = mld.Code(9)
+    for bad in (-1, 3):
+        with pytest.raises(mld.MldError):
+            C.set_exact_kernel(bad)
+    with pytest.raises(mld.MldError) as e:
+        C.set_exact_kernel(2)              # no dense-state kernel at d = 9
+    assert e.value.status == 2
+    C.set_exact_kernel(1)
+    C.set_exact_kernel(0)
+    C.close()
+
+
 def test_d17_truncated_close_to_exact(mld):
     """d=17 at chi=16 (truncating, global workspace): the boundary-MPS value
     is an approximation of the exact contraction (Sec. 3.2.1: small chi
