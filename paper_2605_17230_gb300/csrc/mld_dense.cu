@@ -92,12 +92,40 @@ __device__ __forceinline__ void qubit_weights(const DenseArgs& a, int64_t b, int
     }
 }
 
+// Rest r_live of a step whose rest bits in `dead` are held at zero: r_live
+// with a zero inserted at every set bit of `dead` (ascending).
+__device__ __forceinline__ int expand_rest(int r_live, int dead) {
+    for (int m = dead; m; m &= m - 1) {
+        const int b = __ffs(m) - 1;
+        r_live = ((r_live >> b) << (b + 1)) | (r_live & ((1 << b) - 1));
+    }
+    return r_live;
+}
+
+// Index bits of a pair step at factor r of column c that stay outside the
+// step (rest bits) and carry an absent plaquette: a beta bit (0..r-1) of an
+// absent plaquette of corner column c+1, whose entries the column's end
+// discards, or an alpha bit (r+3..d) of an absent plaquette of corner column
+// c, whose entries are zero until the factor that sums it out. Rests with
+// such a bit set are skipped: the dead ones keep stale values nobody reads,
+// the zero ones stay zero. Returned as rest bits (index bit i < r is rest bit
+// i, index bit i > r+2 is rest bit i-3).
+template <int D>
+__host__ __device__ __forceinline__ int dead_pair_rest_bits(int r, int pa, int pb) {
+    constexpr int FULL = (1 << (D + 1)) - 1;
+    const int low = (1 << r) - 1;
+    const int idx_hi = ~pa & FULL & ~((1 << (r + 3)) - 1);
+    return (~pb & low) | ((idx_hi >> (r + 3)) << r);
+}
+
 // The D qubit factors of column c applied in place to the state S: pairs
-// (r, r+1) for even r, then the single factor D-1.
+// (r, r+1) for even r, then the single factor D-1, on the rests that hold
+// live entries.
 template <int D>
 __device__ __forceinline__ void column_in_place(float* S, const float* wts, int c, int tid) {
     using Sh = DenseShape<D>;
     constexpr int HALF = Sh::HALF;
+    const int pa = present_rows<D>(c), pb = present_rows<D>(c + 1);
 #pragma unroll 1
     for (int r = 0; r + 1 < D; r += 2) {
         float W0[4], W1[4];
@@ -108,7 +136,10 @@ __device__ __forceinline__ void column_in_place(float* S, const float* wts, int 
         for (int g = 0; g < 16; ++g)
             og[g] = sphys((g & 1) * (1 << r) + ((g >> 1) & 1) * (2 << r) + ((g >> 2) & 1) * (4 << r) +
                           (g >> 3) * HALF);
-        for_rests<Sh::REST2, Sh::NT>(tid, [&](int rs) {
+        const int dead = dead_pair_rest_bits<D>(r, pa, pb);
+        const int live = Sh::REST2 >> __popc(dead);
+        for (int k = tid; k < live; k += Sh::NT) {
+            const int rs = expand_rest(k, dead);
             const int base = sphys((rs & ((1 << r) - 1)) | ((rs >> r) << (r + 3)));
             float X[16], Y[16], Z[16];
 #pragma unroll
@@ -117,7 +148,7 @@ __device__ __forceinline__ void column_in_place(float* S, const float* wts, int 
             pair_second(Y, W1, Z);
 #pragma unroll
             for (int m = 0; m < 16; ++m) S[base ^ og[m]] = Z[m];
-        });
+        }
         __syncthreads();
     }
     {
@@ -127,15 +158,19 @@ __device__ __forceinline__ void column_in_place(float* S, const float* wts, int 
         int ok[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) ok[k] = sphys((k & 1) * (1 << r) + ((k >> 1) & 1) * (2 << r) + (k >> 2) * HALF);
-        for (int rs = tid; rs < Sh::REST1; rs += Sh::NT) {
-            const int base = sphys((rs & ((1 << r) - 1)) | ((rs >> r) << (r + 2)));
+        // the rest bits are beta_0..beta_{d-2}; dead where the plaquette is absent
+        const int dead = ~pb & ((1 << r) - 1);
+        const int live = Sh::REST1 >> __popc(dead);
+        for (int k = tid; k < live; k += Sh::NT) {
+            const int rs = expand_rest(k, dead);
+            const int base = sphys(rs);
             float x[8];   // x[b | a'<<1 | a<<2]: beta_r, alpha_{r+1}, alpha_r
 #pragma unroll
-            for (int k = 0; k < 8; ++k) x[k] = S[base ^ ok[k]];
+            for (int j = 0; j < 8; ++j) x[j] = S[base ^ ok[j]];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {   // k = b | b'<<1 | a'<<2
-                const int bb = k & 1, bp = (k >> 1) & 1, ap = k >> 2, i0 = bb | (ap << 1);
-                S[base ^ ok[k]] = fmaf(x[i0], W[jw(0, ap, bb, bp)], x[i0 | 4] * W[jw(1, ap, bb, bp)]);
+            for (int j = 0; j < 8; ++j) {   // j = b | b'<<1 | a'<<2
+                const int bb = j & 1, bp = (j >> 1) & 1, ap = j >> 2, i0 = bb | (ap << 1);
+                S[base ^ ok[j]] = fmaf(x[i0], W[jw(0, ap, bb, bp)], x[i0 | 4] * W[jw(1, ap, bb, bp)]);
             }
         }
         __syncthreads();
@@ -251,12 +286,35 @@ bool launch_d(const DenseArgs& a, int sms, cudaStream_t s) {
 
 bool dense_exact_supported(int d) { return d == 11 || d == 13; }
 
+template <int D>
+double flops_d() {
+    // per (syndrome, l_Z): columns 0..d-2 once and column d-1 twice; 96 flops
+    // per live rest of a pair step (two factors over sixteen entries, a fused
+    // multiply-add and a multiply each) and 24 per live rest of the single step
+    using Sh = DenseShape<D>;
+    auto rows = [](int j) {
+        int m = 0;
+        for (int i = 0; i <= D; ++i) m |= plaquette_is_check(D, i, j) ? 1 << i : 0;
+        return m;
+    };
+    double total = 0.0;
+    for (int c = 0; c < D; ++c) {
+        const int pa = rows(c), pb = rows(c + 1);
+        double col = 0.0;
+        for (int r = 0; r + 1 < D; r += 2)
+            col += 96.0 * (Sh::REST2 >> __builtin_popcount(dead_pair_rest_bits<D>(r, pa, pb)));
+        col += 24.0 * (Sh::REST1 >> __builtin_popcount(~pb & ((1 << (D - 1)) - 1)));
+        total += (c == D - 1 ? 2.0 : 1.0) * col;
+    }
+    return 2.0 * total;
+}
+
 double dense_exact_flops_per_syndrome(int d) {
-    // per (syndrome, l_Z): columns 0..d-2 once and column d-1 twice; a column
-    // is (d-1)/2 pair steps of 6 SIZE flops and one single step of 3 SIZE
-    if (!dense_exact_supported(d)) return 0.0;
-    const double size = (double)(1 << (d + 2));
-    return 2.0 * (d + 1) * 3.0 * size * d;
+    switch (d) {
+        case 11: return flops_d<11>();
+        case 13: return flops_d<13>();
+    }
+    return 0.0;
 }
 
 bool launch_dense_exact(int d, const DenseArgs& a, cudaStream_t s) {
