@@ -160,22 +160,38 @@ __device__ __noinline__ int qrcp(float* M, int K, int ld, int N, float* tau, int
             for (int rr = j + 1 + lane; rr < K; rr += 32) vj[rr] = (vj[rr] * sc) * scal;
         if (lane == 0) { vj[j] = beta; tau[j] = tj; }
         __syncwarp();
-        // H_j on columns j+1 .. N-1 (one per lane) and their norms below row j
-        for (int cc = j + 1 + lane; cc < N; cc += 32) {
-            float* col = M + cc * ld;
-            if (tj != 0.f) {
-                float w = col[j];
-#pragma unroll 2
-                for (int rr = j + 1; rr < K; ++rr) w = fmaf(vj[rr], col[rr], w);
-                w *= tj;
-                col[j] -= w;
-#pragma unroll 2
-                for (int rr = j + 1; rr < K; ++rr) col[rr] = fmaf(-vj[rr], w, col[rr]);
+        // H_j on columns j+1 .. N-1 and their norms below row j: a group of G
+        // lanes per column (G the largest power of two with (N-1-j) G <= 32),
+        // the rows dealt round-robin over the group, the dot product and the
+        // norm summed across it by shuffles
+        const int rem = N - 1 - j;
+        int G = 32;
+        while (G > 1 && rem * G > 32) G >>= 1;
+        const int groups = 32 / G, grp = lane / G, g = lane - grp * G;
+        for (int base = j + 1; base < N; base += groups) {
+            const int cc = base + grp;
+            const bool act = cc < N;
+            float* col = M + (act ? cc : j) * ld;
+            float w = 0.f;
+            if (act && tj != 0.f) {
+                if (g == 0) w = col[j];
+                for (int rr = j + 1 + g; rr < K; rr += G) w = fmaf(vj[rr], col[rr], w);
             }
+            for (int o = G >> 1; o > 0; o >>= 1) w += __shfl_xor_sync(kFull, w, o);
             float s = 0.f;
-#pragma unroll 2
-            for (int rr = j + 1; rr < K; ++rr) s = fmaf(col[rr], col[rr], s);
-            nrm[cc] = sqrtf(s);
+            if (act) {
+                if (tj != 0.f) {
+                    w *= tj;
+                    if (g == 0) col[j] -= w;
+                }
+                for (int rr = j + 1 + g; rr < K; rr += G) {
+                    const float x = tj != 0.f ? fmaf(-vj[rr], w, col[rr]) : col[rr];
+                    col[rr] = x;
+                    s = fmaf(x, x, s);
+                }
+            }
+            for (int o = G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+            if (act && g == 0) nrm[cc] = sqrtf(s);
         }
         __syncwarp();
         if (lane == 0) *fl += 3ULL * (K - j) + 6ULL * (K - j) * (N - 1 - j);
@@ -186,28 +202,40 @@ __device__ __noinline__ int qrcp(float* M, int K, int ld, int N, float* tau, int
 // Y <- Q Y for the columns of Y (column-major, leading dimension ldy), Q =
 // H_0 ... H_{nr-1} with reflectors V (column-major, leading dimension ldv,
 // v_j below row j) and tau. Columns n < split use set 0 (V0, tau0, nr0), the
-// others set 1. One column per lane.
+// others set 1. A group of G lanes per column (G the largest power of two
+// with ncols G <= 32), the rows dealt round-robin over the group and each
+// reflector's dot product summed across it by shuffles.
 __device__ __noinline__ void apply_q(const float* V0, const float* tau0, int nr0, const float* V1,
                                      const float* tau1, int nr1, int split, int ldv, int K, float* Y, int ldy,
                                      int ncols, unsigned long long* fl) {
     const int lane = threadIdx.x & 31;
-    for (int n = lane; n < ncols; n += 32) {
+    int G = 32;
+    while (G > 1 && ncols * G > 32) G >>= 1;
+    const int groups = 32 / G, grp = lane / G, g = lane - grp * G;
+    const int nrmax = nr0 > nr1 ? nr0 : nr1;
+    for (int base = 0; base < ncols; base += groups) {
+        const int n = base + grp;
+        const bool act = n < ncols;
         const bool s1 = n >= split;
         const float* Vs = s1 ? V1 : V0;
         const float* ts = s1 ? tau1 : tau0;
-        const int nr = s1 ? nr1 : nr0;
-        float* y = Y + n * ldy;
-        for (int j = nr - 1; j >= 0; --j) {
-            const float tj = ts[j];
-            if (tj == 0.f) continue;
+        const int nr = act ? (s1 ? nr1 : nr0) : 0;
+        float* y = Y + (act ? n : 0) * ldy;
+        // every lane runs nrmax steps so that the group shuffles stay uniform;
+        // lane g owns the rows r = g (mod G) in every step, so no lane reads
+        // another's writes (v_j[j] = 1 is implied)
+        for (int j = nrmax - 1; j >= 0; --j) {
+            const bool on = j < nr && ts[j] != 0.f;
             const float* v = Vs + j * ldv;
-            float w = y[j];
-#pragma unroll 2
-            for (int r = j + 1; r < K; ++r) w = fmaf(v[r], y[r], w);
-            w *= tj;
-            y[j] -= w;
-#pragma unroll 2
-            for (int r = j + 1; r < K; ++r) y[r] = fmaf(-v[r], w, y[r]);
+            const int r0 = j + ((g - j) & (G - 1));
+            float w = 0.f;
+            if (on)
+                for (int r = r0; r < K; r += G) w = fmaf(r == j ? 1.f : v[r], y[r], w);
+            for (int o = G >> 1; o > 0; o >>= 1) w += __shfl_xor_sync(kFull, w, o);
+            if (on) {
+                w *= ts[j];
+                for (int r = r0; r < K; r += G) y[r] = fmaf(r == j ? -1.f : -v[r], w, y[r]);
+            }
         }
     }
     if (lane == 0) {

@@ -138,6 +138,26 @@ def test_d17_chi128_vs_exact_oracle_64_syndromes(mld):
     np.testing.assert_array_equal(am[clear], np.argmax(ref, axis=1)[clear])
 
 
+@pytest.mark.parametrize("d", [17, 25])
+def test_chi8_suffices_well_below_threshold(mld, d):
+    """Sec. 3.2.1 reports that chi = 8 suffices at p = 5% up to d = 25: on 2,048
+    depolarizing p = 0.05 syndromes the chi = 8 decisions equal the chi = 64
+    ones wherever the chi = 64 top two cosets are more than 1e-3 apart, and the
+    leading coset's ln Z moves by less than 1e-2."""
+    n = d * d
+    noise = synth.depolarizing(n, 0.05).astype(np.float32)
+    syn = synth.syndromes_of(d, synth.sample_errors(d, noise, 2048, seed=synth.config_seed(5, d, 0.05)))
+    lp8, am8, _, h8 = decode(mld, d, noise, syn, 8)
+    lp64, am64, _, _ = decode(mld, d, noise, syn, 64)
+    top = np.sort(lp64, axis=1)
+    clear = top[:, -1] - top[:, -2] > 1e-3
+    np.testing.assert_array_equal(am8[clear], am64[clear])
+    lead = np.argmax(lp64, axis=1)
+    rows = np.arange(len(syn))
+    assert np.abs(lp8[rows, lead] - lp64[rows, lead]).max() < 1e-2
+    assert np.flatnonzero(h8[1:]).max() + 1 <= 8
+
+
 @pytest.mark.parametrize("d,chi", [(7, 4), (9, 8), (11, 16)])
 @pytest.mark.parametrize("cutoff", [None, 0.0])
 @pytest.mark.parametrize("kernel", [1, 2])
