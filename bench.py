@@ -573,31 +573,41 @@ def run_dem(args):
     """Detector-picture decode (Sec. 3.2.2) of a code-capacity error-mechanism
     model at d=9: X, Y and Z mechanisms on every qubit with lognormal rates
     (median 0.03, seed 5), 65,536 syndromes sampled from the mechanisms
-    (seed 6); all four classes per syndrome from one sweep."""
+    (seed 6); all four classes per syndrome from one sweep. The same model at
+    d=11 (16,384 syndromes) is reported as d11_value."""
     import torch
     import paper_2605_17230_gb300 as mld
-    d = 9
+
+    def one(d, Bd):
+        q, c, p = synth.mechanism_model(d, seed=5)
+        E = synth.sample_mechanisms(d, q, c, p, Bd, seed=6)
+        sy = torch.tensor(synth.syndromes_of(d, E).view(np.int64), device="cuda")
+        code = mld.Code(d)
+        for _ in range(max(1, args.warmup)):
+            code.decode_dem(q, c, p, sy)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            lp, am = code.decode_dem(q, c, p, sy)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        true = torch.tensor(synth.true_class(d, E).astype(np.int64), device="cuda")
+        ler = float((am.long() != true).float().mean().item())
+        code.close()
+        return ms, len(p), ler
+
     Bd = args.batch if args.batch != B else 65536
-    q, c, p = synth.mechanism_model(d, seed=5)
-    E = synth.sample_mechanisms(d, q, c, p, Bd, seed=6)
-    sy = torch.tensor(synth.syndromes_of(d, E).view(np.int64), device="cuda")
-    code = mld.Code(d)
-    for _ in range(max(1, args.warmup)):
-        code.decode_dem(q, c, p, sy)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        lp, am = code.decode_dem(q, c, p, sy)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    true = torch.tensor(synth.true_class(d, E).astype(np.int64), device="cuda")
+    ms, nm, ler = one(9, Bd)
     line = {"metric": "syndromes/s of the detector-picture decode (d=9, X/Y/Z mechanisms per qubit, 4 classes)",
             "workload": "dem", "value": Bd / (ms / 1e3), "unit": "syndromes/s", "ms_per_step": ms,
-            "syndromes": Bd, "mechanisms": int(len(p)), "steps": args.steps, "data": "synthetic",
-            "dtype": "f32 contraction, f64 ln Z",
-            "logical_error_rate": float((am.long() != true).float().mean().item())}
+            "syndromes": Bd, "mechanisms": int(nm), "steps": args.steps, "data": "synthetic",
+            "dtype": "f32 contraction, f64 ln Z", "logical_error_rate": ler}
+    if args.batch == B:
+        ms11, nm11, ler11 = one(11, 16384)
+        line.update({"d11_value": 16384 / (ms11 / 1e3), "d11_mechanisms": int(nm11),
+                     "d11_logical_error_rate": ler11})
     print(json.dumps(line), flush=True)
 
 

@@ -321,7 +321,8 @@ mld_status mld_decode_flops(const mld_code* code, int chi, int precision, double
  * The contraction is exact: one thread block per syndrome keeps the dense
  * boundary state over the open detectors' partial parities and both
  * logical parities, all four classes in one sweep; FP32 with power-of-two
- * rescaling per column, ln Z in FP64. d <= 9 (MLD_ERR_UNSUPPORTED
+ * rescaling per column, ln Z in FP64. d <= 11 (the state at d = 11 is
+ * 2^15 floats, one block of 512 threads per SM; MLD_ERR_UNSUPPORTED
  * otherwise); MLD_ERR_INVALID_ARG for a mechanism with a qubit outside
  * [0, n), a code outside 1..3 or p outside [0, 1]. Asynchronous on stream;
  * no device allocation. */

@@ -43,7 +43,7 @@
 namespace mld {
 namespace {
 
-constexpr int kDemMaxD = 9;
+constexpr int kDemMaxD = 11;
 
 struct DemParams {
     float P[kDemMaxD * kDemMaxD][4];                       // per qubit: Pr(E_q = e), e = x + 2z
@@ -65,7 +65,9 @@ struct DemShape {
     static constexpr int HALF = 1 << (D + 1);
     static constexpr int SIZE = 1 << (D + 4);
     static constexpr int SP = D + 1, OXP = D + 2, OZP = D + 3;   // spare and observable positions
-    static constexpr int NT = D >= 9 ? 128 : (D >= 7 ? 64 : 32);
+    // d = 11: the 128 KB state fills a block's shared memory; one block of
+    // 512 threads per SM
+    static constexpr int NT = D >= 11 ? 512 : (D >= 9 ? 128 : (D >= 7 ? 64 : 32));
     static constexpr int NW = NT / 32;
     static constexpr int NF = (D + 1) * (D + 1);
     static constexpr int off_f = 0, off_sf = SIZE, off_misc = off_sf + ((NF + 3) & ~3);   // one state, updated in place
@@ -73,7 +75,7 @@ struct DemShape {
     static constexpr int floats = off_misc + 32;
     static constexpr int FIT = (227 * 1024) / (floats * 4 + 1024);
     // keep room for ~96 registers a thread at d = 9 (fewer spill there), ~84 below
-    static constexpr int REGS = 65536 / (NT * (D >= 9 ? 96 : 84));
+    static constexpr int REGS = 65536 / (NT * (D >= 11 ? 128 : (D >= 9 ? 96 : 84)));
     static constexpr int MINB = FIT < REGS ? (FIT < 16 ? FIT : 16) : (REGS < 16 ? REGS : 16);
 };
 
@@ -430,6 +432,7 @@ extern "C" mld_status mld_decode_dem(const mld_code* Cc, const int32_t* mech_qub
         case 5: return launch_dem<5>(a, prm, s);
         case 7: return launch_dem<7>(a, prm, s);
         case 9: return launch_dem<9>(a, prm, s);
+        case 11: return launch_dem<11>(a, prm, s);
     }
     return MLD_ERR_UNSUPPORTED;
 }

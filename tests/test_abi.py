@@ -88,7 +88,7 @@ def test_host_side_argument_checks():
                     ([0], [1], [-0.1]), ([0], [1], [1.5]), ([0], [1], [np.nan])):
         assert dem(c5, q, c, p) == INVALID, (q, c, p)
     assert dem(c5, [0], [1], [0.1], n=-1) == INVALID
-    assert dem(c11, [0], [1], [0.1]) == UNSUPPORTED
+    assert dem(c13, [0], [1], [0.1]) == UNSUPPORTED
     # mld_decode(code, noise, mode, syn, B, chi, precision, logP, argmax, stream)
     dec = lambda *a: lib.mld_decode(*a)
     assert dec(P(c5.handle), fake, 0, fake, 0, 8, 0, fake, None, None) == OK

@@ -42,7 +42,7 @@ def _compare(lp, ref, atol=2e-5):
     np.testing.assert_allclose(lp[fin], ref[fin], rtol=0, atol=atol)
 
 
-@pytest.mark.parametrize("d,B", [(3, 256), (5, 301), (7, 257), (9, 65)])
+@pytest.mark.parametrize("d,B", [(3, 256), (5, 301), (7, 257), (9, 65), (11, 40)])
 def test_dem_vs_generator_oracle(mld, d, B):
     q, c, p = _model(d, seed=d)
     tab = oracle.dem_qubit_table(d, q, c, p)
@@ -131,9 +131,9 @@ def test_dem_degenerate_inputs(mld):
     for bad in (([25], [1], [0.1]), ([0], [0], [0.1]), ([0], [4], [0.1]), ([0], [1], [1.5]), ([0], [1], [np.nan])):
         with pytest.raises(mld.MldError):
             code.decode_dem(*bad, sy)
-    big = mld.Code(11)
+    big = mld.Code(13)
     with pytest.raises(mld.MldError):
-        big.decode_dem([0], [1], [0.1], torch.zeros((1, 2), dtype=torch.int64, device="cuda"))
+        big.decode_dem([0], [1], [0.1], torch.zeros((1, 3), dtype=torch.int64, device="cuda"))
 
 
 def test_dem_rerun_bit_identical(mld):
