@@ -1,0 +1,80 @@
+"""Chunked decoding to files with resume (paper_2605_17230_gb300.stream): an
+interrupted job continues from its progress record and ends with the same
+bits as one decode of the whole batch; another configuration is refused."""
+import json
+
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mld():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_17230_gb300 as m
+    m.load()
+    return m
+
+
+class Stop(Exception):
+    pass
+
+
+@pytest.mark.parametrize("mode", ["table", "depolarizing"])
+def test_interrupted_job_resumes_to_the_same_bits(mld, tmp_path, mode):
+    from paper_2605_17230_gb300 import stream
+    d, chi, B, chunk = 9, 32, 5 * 1024 + 77, 1024
+    n = d * d
+    code = mld.Code(d)
+    if mode == "table":
+        table = synth.depolarizing(n, 0.1).astype(np.float32)
+        syn = synth.syndromes_of(d, synth.sample_errors(d, table, B, seed=3))
+        noise = torch.tensor(table, device="cuda")
+        nmode = mld.MLD_NOISE_TABLE
+    else:
+        p = np.random.default_rng(4).uniform(0.02, 0.18, size=B).astype(np.float32)
+        syn = synth.syndromes_of(d, synth.sample_errors(d, synth.depolarizing(n, 0.1), B, seed=5))
+        noise = p
+        nmode = mld.MLD_NOISE_DEPOL
+    # reference: one decode of the whole batch
+    ref_lp = torch.empty((B, 4), dtype=torch.float64, device="cuda")
+    ref_am = torch.empty((B,), dtype=torch.uint8, device="cuda")
+    dn = noise if nmode == mld.MLD_NOISE_TABLE else torch.tensor(p, device="cuda")
+    mld.mld_decode(code.handle, dn, nmode, torch.tensor(syn.view(np.int64), device="cuda"), B, chi,
+                   mld.MLD_FP32, ref_lp, ref_am)
+    torch.cuda.synchronize()
+    prefix = str(tmp_path / "job")
+    seen = []
+
+    def stop_after_two(start, count):
+        seen.append((start, count))
+        if len(seen) == 2:
+            raise Stop()
+
+    with pytest.raises(Stop):
+        stream.decode_to_files(code, noise, syn, chi, prefix, chunk=chunk, noise_mode=nmode,
+                               on_chunk=stop_after_two)
+    with open(prefix + ".progress.json") as f:
+        assert json.load(f)["done"] == 2 * chunk
+    rest = []
+    lp, am = stream.decode_to_files(code, noise, syn, chi, prefix, chunk=chunk, noise_mode=nmode,
+                                    on_chunk=lambda s, c: rest.append((s, c)))
+    assert rest[0][0] == 2 * chunk and rest[-1] == (5 * chunk, 77)
+    np.testing.assert_array_equal(np.asarray(lp), ref_lp.cpu().numpy())
+    np.testing.assert_array_equal(np.asarray(am), ref_am.cpu().numpy())
+    # a finished job returns at once; another chi is refused
+    again = []
+    stream.decode_to_files(code, noise, syn, chi, prefix, chunk=chunk, noise_mode=nmode,
+                           on_chunk=lambda s, c: again.append(s))
+    assert again == []
+    with pytest.raises(ValueError):
+        stream.decode_to_files(code, noise, syn, 16, prefix, chunk=chunk, noise_mode=nmode)
+    # resume=False starts over and gives the same bits
+    lp2, _ = stream.decode_to_files(code, noise, syn, chi, prefix, chunk=chunk, noise_mode=nmode, resume=False)
+    np.testing.assert_array_equal(np.asarray(lp2), ref_lp.cpu().numpy())
+    code.close()
