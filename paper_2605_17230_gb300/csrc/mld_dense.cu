@@ -49,13 +49,18 @@ struct DenseShape {
 };
 
 // Shared-memory position of entry e of a state inside a column: bits 5, 6
-// and 7 XORed into the bank bits with masks 4, 9 and 18. The map is linear
+// and 7 XORed into the bank bits with masks 5, 9 and 18. The map is linear
 // over GF(2) and the same for every step, so a step rewrites its entries in
-// place; with these masks the 32 lanes of a warp (32 consecutive rests) hit 32
-// distinct banks for every pair step and the single step of d = 9, 11, 13
-// (checked exhaustively on the host).
+// place. The 32 lanes of a warp (32 consecutive rests) hit 32 distinct banks
+// in every pair and single step of d = 9, 11, 13 when no rest is skipped
+// (checked exhaustively on the host); of the three-mask swizzles with that
+// property, this one leaves the fewest same-bank pairs once the rests of
+// absent plaquettes are skipped (measured at d = 13: 5.6% of the
+// shared-memory wavefronts are conflicts, against 12.8% with masks 4, 9, 18).
+// Two more masks (bits 8 and 9) removed nearly all of them but cost 13% more
+// instructions and ran 8% slower: the kernel is issue-bound.
 __device__ __forceinline__ int sphys(int e) {
-    return e ^ (((e >> 5) & 1) ? 4 : 0) ^ (((e >> 6) & 1) ? 9 : 0) ^ (((e >> 7) & 1) ? 18 : 0);
+    return e ^ (((e >> 5) & 1) ? 5 : 0) ^ (((e >> 6) & 1) ? 9 : 0) ^ (((e >> 7) & 1) ? 18 : 0);
 }
 
 // Factor weights of the D qubits of column c for class (lx, lz), stored in
