@@ -221,8 +221,9 @@ PRODUCT_PATH = {
     0: "FP32 FFMA products (the split-TF32 path is slower at this d; a mixed request runs the FP32 kernel)",
     9: "split-TF32 mma.sync tensor-core products (hi.hi + hi.lo + lo.hi) for data-site products of at "
        "least 32x16x32, FP32 elsewhere",
-    11: "split-TF32 mma.sync tensor-core products (hi.hi + hi.lo + lo.hi) for data-site products of at "
-        "least 32x16x32, FP32 elsewhere",
+    11: "dense-state FP32 column transfer (untruncated chi; the faster exact kernel at this d, 2.6M "
+        "against 2.1M syndromes/s for the split-TF32 boundary-MPS kernel; a mixed request runs the same "
+        "kernel)",
     13: "dense-state FP32 column transfer (untruncated chi; no product is MMA-shaped; a mixed request "
         "runs the same kernel)",
 }

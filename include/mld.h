@@ -207,7 +207,7 @@ void mld_graph_destroy(mld_graph* graph);
  * per-warp state exceeds a block's shared memory (d = 13 untruncated) the
  * candidates are the resident warps per SM of the global-workspace sweep
  * (2, 4, 8, 16; *chosen_warps reports that count). At an untruncated chi
- * with d = 11 or 13 the dense-state kernel is a candidate too, and the faster
+ * with d = 9, 11 or 13 the dense-state kernel is a candidate too, and the faster
  * kernel is kept for that chi (*chosen_warps = 0 when it is the dense one),
  * unless mld_code_set_exact_kernel forces one. For a
  * truncating chi the rank-adaptive sweep (4 units per block) is a candidate
@@ -269,13 +269,15 @@ mld_status mld_code_set_truncation_kernel(mld_code* code, int which);
 /* Which kernel decodes an untruncated chi (chi >= 2^floor(d/2), where the
  * boundary MPS of Sec. 3.2.1 discards nothing and is the exact boundary state
  * over one corner column): 0 (default) mld_autotune's choice for that chi if
- * it timed one, else the dense-state kernel at d = 13 and the boundary-MPS
- * kernel elsewhere; 1 always the boundary-MPS kernel (sites at the exact
- * cut ranks, compile-time plan per d); 2 the dense-state kernel (d = 11, 13:
- * one block per (syndrome, l_Z) keeps the 2^(d+2)-entry state of a column
- * in shared memory and applies the qubit factors to it in place; FP32 for
- * either precision). Both give ln Z_l to FP32 accuracy. MLD_ERR_INVALID_ARG
- * for other values, MLD_ERR_UNSUPPORTED for 2 at other d. Host only. */
+ * it timed one, else the dense-state kernel at d = 11 and 13 (the faster
+ * one there) and the boundary-MPS kernel elsewhere; 1 always the
+ * boundary-MPS kernel (sites at the exact cut ranks, compile-time plan per
+ * d; split-TF32 tensor-core products for MLD_MIXED_TF32 at d = 9, 11); 2
+ * the dense-state kernel (d = 9, 11, 13: one block per (syndrome, l_Z) keeps
+ * the 2^(d+2)-entry state of a column in shared memory and applies the
+ * qubit factors to it in place; FP32 for either precision). Both give ln Z_l
+ * to FP32 accuracy. MLD_ERR_INVALID_ARG for other values,
+ * MLD_ERR_UNSUPPORTED for 2 at other d. Host only. */
 mld_status mld_code_set_exact_kernel(mld_code* code, int which);
 
 /* Floating-point operations executed by the truncating sweeps of this code

@@ -290,9 +290,9 @@ class Code:
         _check(load().mld_code_set_svd_cutoff(ctypes.c_void_p(self.handle), float(rel)), "mld_code_set_svd_cutoff")
 
     def set_exact_kernel(self, which: int):
-        """Untruncated chi: 0 by d (default; the dense-state kernel at d=13),
-        1 the boundary-MPS kernel, 2 the dense-state kernel (d = 11, 13)
-        (mld_code_set_exact_kernel)."""
+        """Untruncated chi: 0 by d (default; the dense-state kernel at d = 11
+        and 13), 1 the boundary-MPS kernel, 2 the dense-state kernel (d = 9,
+        11, 13) (mld_code_set_exact_kernel)."""
         _check(load().mld_code_set_exact_kernel(ctypes.c_void_p(self.handle), int(which)),
                "mld_code_set_exact_kernel")
 

@@ -175,7 +175,7 @@ mld_status mld_autotune(const mld_code* Cc, int chi, int precision, int64_t samp
     // candidates: warps per CTA of the fixed-shape or untruncated kernel
     // (global-workspace states: resident warps per SM 2, 4, 8, 16); for a
     // truncating chi the rank-adaptive sweep (kernel 1) as well; for an
-    // untruncated chi at d = 11, 13 the dense-state kernel as well
+    // untruncated chi at d = 9, 11, 13 the dense-state kernel as well
     const bool truncating = mld::make_plan(C->d, chi).svd_sites != 0;
     const bool dense_cand = !truncating && mld::dense_exact_supported(C->d) && C->exact_kernel == 0;
     const int saved_kernel = C->trunc_kernel, saved_exact = C->exact_kernel;

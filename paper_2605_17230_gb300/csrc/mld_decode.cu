@@ -938,16 +938,18 @@ mld_status decode_truncated(mld_code* C, const mld::Plan& P, const mld::SiteStep
 
 namespace mld {
 // Whether an untruncated decode of this code runs the dense-state kernel:
-// on request (mld_code_set_exact_kernel 2, d = 11 or 13), as mld_autotune
-// chose for this chi, or by default at d = 13, where the exact boundary MPS
-// (298 KB per unit) no longer fits shared memory and the dense state (128 KB)
-// does.
+// on request (mld_code_set_exact_kernel 2, d = 9, 11, 13), as mld_autotune
+// chose for this chi, or by default at d = 11 and 13, where it is the faster
+// exact kernel (measured: 2.61M against 2.07M syndromes/s for the split-TF32
+// boundary-MPS kernel at d = 11; 556k against 140k at d = 13, where the
+// exact boundary MPS needs 298 KB per unit and runs from global memory; at
+// d = 9 the boundary-MPS kernel is faster, 19.2M against 10.8M).
 bool uses_dense_exact(const mld_code* C, const Plan& P) {
     if (P.svd_sites != 0 || !dense_exact_supported(C->d) || C->exact_kernel == 1) return false;
     if (C->exact_kernel == 2) return true;
     for (const auto& kv : C->exact_tuned)
         if (kv.first == P.chi) return kv.second == 2;
-    return C->d == 13;
+    return C->d >= 11;
 }
 
 // Whether the untruncated or fixed-shape sweep of this code at this chi keeps

@@ -18,6 +18,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "mld_dense.h"
 #include "mld_dense_steps.cuh"
 
@@ -34,9 +36,9 @@ struct DenseShape {
     static constexpr int REST1 = SIZE >> 3;        // rests of a single step (eight entries)
     static constexpr int REST2 = SIZE >> 4;        // rests of a pair step (sixteen entries)
     // d = 13: one block of 16 warps per SM (shared memory); d = 11: two
-    // blocks of 8 warps (registers)
-    static constexpr int NT = D >= 13 ? 512 : 256;
-    static constexpr int MINB = D >= 13 ? 1 : 2;
+    // blocks of 8 warps, d = 9: four blocks of 4 warps (registers)
+    static constexpr int NT = D >= 13 ? 512 : (D >= 11 ? 256 : 128);
+    static constexpr int MINB = D >= 13 ? 1 : (D >= 11 ? 2 : 4);
     static constexpr int NW = NT / 32;
     // shared memory (floats)
     static constexpr int off_w = 0;                       // 4N factor weights (slot order Wp)
@@ -59,8 +61,19 @@ struct DenseShape {
 // shared-memory wavefronts are conflicts, against 12.8% with masks 4, 9, 18).
 // Two more masks (bits 8 and 9) removed nearly all of them but cost 13% more
 // instructions and ran 8% slower: the kernel is issue-bound.
-__device__ __forceinline__ int sphys(int e) {
+__host__ __device__ __forceinline__ constexpr int sphys(int e) {
     return e ^ (((e >> 5) & 1) ? 5 : 0) ^ (((e >> 6) & 1) ? 9 : 0) ^ (((e >> 7) & 1) ? 18 : 0);
+}
+
+// Position of entry m of a rest at `base`: base XOR the entry's swizzled bits.
+// From step bit 8 on the entry bits lie above the swizzle's source bits and
+// the base is zero at their positions, so the XOR is an addition of a
+// compile-time constant (which the shared-memory load and store take as
+// their immediate offset).
+template <int OFF, bool ADD>
+__device__ __forceinline__ int entry_at(int base) {
+    if constexpr (ADD) return base + OFF;
+    else return base ^ OFF;
 }
 
 // Factor weights of the D qubits of column c for class (lx, lz), stored in
@@ -123,63 +136,81 @@ __host__ __device__ __forceinline__ int dead_pair_rest_bits(int r, int pa, int p
     return (~pb & low) | ((idx_hi >> (r + 3)) << r);
 }
 
+// Pair step (R, R+1) of column c, in place on the live rests.
+template <int D, int R, int M>
+__device__ __forceinline__ constexpr int pair_off() {
+    return sphys((M & 1) * (1 << R) + ((M >> 1) & 1) * (2 << R) + ((M >> 2) & 1) * (4 << R) +
+                 (M >> 3) * DenseShape<D>::HALF);
+}
+
+template <int D, int R, int... Ms>
+__device__ __forceinline__ void pair_step(float* S, const float* wts, int c, int tid, int pa, int pb,
+                                          std::integer_sequence<int, Ms...>) {
+    using Sh = DenseShape<D>;
+    constexpr bool ADD = R >= 8;
+    float W0[4], W1[4];
+    factor_weights<D>(wts, R, c, W0);
+    factor_weights<D>(wts, R + 1, c, W1);
+    const int dead = dead_pair_rest_bits<D>(R, pa, pb);
+    const int live = Sh::REST2 >> __popc(dead);
+    for (int k = tid; k < live; k += Sh::NT) {
+        const int rs = expand_rest(k, dead);
+        const int base = sphys((rs & ((1 << R) - 1)) | ((rs >> R) << (R + 3)));
+        float X[16] = {S[entry_at<pair_off<D, R, Ms>(), ADD>(base)]...};
+        float Y[16], Z[16];
+        pair_first(X, W0, Y);
+        pair_second(Y, W1, Z);
+        ((S[entry_at<pair_off<D, R, Ms>(), ADD>(base)] = Z[Ms]), ...);
+    }
+    __syncthreads();
+}
+
+template <int D, int... Is>
+__device__ __forceinline__ void pair_steps(float* S, const float* wts, int c, int tid, int pa, int pb,
+                                           std::integer_sequence<int, Is...>) {
+    (pair_step<D, 2 * Is>(S, wts, c, tid, pa, pb, std::make_integer_sequence<int, 16>{}), ...);
+}
+
+// The single factor D-1 of column c, in place on the live rests.
+template <int D, int K>
+__device__ __forceinline__ constexpr int single_off() {
+    constexpr int R = D - 1;
+    return sphys((K & 1) * (1 << R) + ((K >> 1) & 1) * (2 << R) + (K >> 2) * DenseShape<D>::HALF);
+}
+
+template <int D, int... Ks>
+__device__ __forceinline__ void single_step(float* S, const float* wts, int c, int tid, int pb,
+                                            std::integer_sequence<int, Ks...>) {
+    using Sh = DenseShape<D>;
+    constexpr int R = D - 1;
+    constexpr bool ADD = R >= 8;
+    float W[4];
+    factor_weights<D>(wts, R, c, W);
+    // the rest bits are beta_0..beta_{d-2}; dead where the plaquette is absent
+    const int dead = ~pb & ((1 << R) - 1);
+    const int live = Sh::REST1 >> __popc(dead);
+    for (int k = tid; k < live; k += Sh::NT) {
+        const int base = sphys(expand_rest(k, dead));
+        const float x[8] = {S[entry_at<single_off<D, Ks>(), ADD>(base)]...};   // x[b | a'<<1 | a<<2]
+        float y[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {   // j = b | b'<<1 | a'<<2
+            const int bb = j & 1, bp = (j >> 1) & 1, ap = j >> 2, i0 = bb | (ap << 1);
+            y[j] = fmaf(x[i0], W[jw(0, ap, bb, bp)], x[i0 | 4] * W[jw(1, ap, bb, bp)]);
+        }
+        ((S[entry_at<single_off<D, Ks>(), ADD>(base)] = y[Ks]), ...);
+    }
+    __syncthreads();
+}
+
 // The D qubit factors of column c applied in place to the state S: pairs
 // (r, r+1) for even r, then the single factor D-1, on the rests that hold
-// live entries.
+// live entries (every step's offsets are compile-time constants).
 template <int D>
 __device__ __forceinline__ void column_in_place(float* S, const float* wts, int c, int tid) {
-    using Sh = DenseShape<D>;
-    constexpr int HALF = Sh::HALF;
     const int pa = present_rows<D>(c), pb = present_rows<D>(c + 1);
-#pragma unroll 1
-    for (int r = 0; r + 1 < D; r += 2) {
-        float W0[4], W1[4];
-        factor_weights<D>(wts, r, c, W0);
-        factor_weights<D>(wts, r + 1, c, W1);
-        int og[16];
-#pragma unroll
-        for (int g = 0; g < 16; ++g)
-            og[g] = sphys((g & 1) * (1 << r) + ((g >> 1) & 1) * (2 << r) + ((g >> 2) & 1) * (4 << r) +
-                          (g >> 3) * HALF);
-        const int dead = dead_pair_rest_bits<D>(r, pa, pb);
-        const int live = Sh::REST2 >> __popc(dead);
-        for (int k = tid; k < live; k += Sh::NT) {
-            const int rs = expand_rest(k, dead);
-            const int base = sphys((rs & ((1 << r) - 1)) | ((rs >> r) << (r + 3)));
-            float X[16], Y[16], Z[16];
-#pragma unroll
-            for (int m = 0; m < 16; ++m) X[m] = S[base ^ og[m]];
-            pair_first(X, W0, Y);
-            pair_second(Y, W1, Z);
-#pragma unroll
-            for (int m = 0; m < 16; ++m) S[base ^ og[m]] = Z[m];
-        }
-        __syncthreads();
-    }
-    {
-        constexpr int r = D - 1;
-        float W[4];
-        factor_weights<D>(wts, r, c, W);
-        int ok[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) ok[k] = sphys((k & 1) * (1 << r) + ((k >> 1) & 1) * (2 << r) + (k >> 2) * HALF);
-        // the rest bits are beta_0..beta_{d-2}; dead where the plaquette is absent
-        const int dead = ~pb & ((1 << r) - 1);
-        const int live = Sh::REST1 >> __popc(dead);
-        for (int k = tid; k < live; k += Sh::NT) {
-            const int rs = expand_rest(k, dead);
-            const int base = sphys(rs);
-            float x[8];   // x[b | a'<<1 | a<<2]: beta_r, alpha_{r+1}, alpha_r
-#pragma unroll
-            for (int j = 0; j < 8; ++j) x[j] = S[base ^ ok[j]];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {   // j = b | b'<<1 | a'<<2
-                const int bb = j & 1, bp = (j >> 1) & 1, ap = j >> 2, i0 = bb | (ap << 1);
-                S[base ^ ok[j]] = fmaf(x[i0], W[jw(0, ap, bb, bp)], x[i0 | 4] * W[jw(1, ap, bb, bp)]);
-            }
-        }
-        __syncthreads();
-    }
+    pair_steps<D>(S, wts, c, tid, pa, pb, std::make_integer_sequence<int, (D - 1) / 2>{});
+    single_step<D>(S, wts, c, tid, pb, std::make_integer_sequence<int, 8>{});
 }
 
 template <int D>
@@ -289,7 +320,7 @@ bool launch_d(const DenseArgs& a, int sms, cudaStream_t s) {
 
 }  // namespace
 
-bool dense_exact_supported(int d) { return d == 11 || d == 13; }
+bool dense_exact_supported(int d) { return d == 9 || d == 11 || d == 13; }
 
 template <int D>
 double flops_d() {
@@ -316,6 +347,7 @@ double flops_d() {
 
 double dense_exact_flops_per_syndrome(int d) {
     switch (d) {
+        case 9: return flops_d<9>();
         case 11: return flops_d<11>();
         case 13: return flops_d<13>();
     }
@@ -328,6 +360,7 @@ bool launch_dense_exact(int d, const DenseArgs& a, cudaStream_t s) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return false;
     switch (d) {
+        case 9: return launch_d<9>(a, sms, s);
         case 11: return launch_d<11>(a, sms, s);
         case 13: return launch_d<13>(a, sms, s);
     }

@@ -53,8 +53,8 @@ struct mld_code {
     std::vector<std::pair<int, int>> trunc_tuned;
     // which kernel runs an untruncated chi: 0 mld_autotune's choice for that
     // chi if it timed one (exact_tuned), else by d (the dense-state kernel at
-    // d = 13, the boundary-MPS kernel elsewhere); 1 the boundary-MPS kernel;
-    // 2 the dense-state kernel (d = 11, 13)
+    // d = 11, 13, the boundary-MPS kernel elsewhere); 1 the boundary-MPS
+    // kernel; 2 the dense-state kernel (d = 9, 11, 13)
     int exact_kernel = 0;
     std::vector<std::pair<int, int>> exact_tuned;
 };

@@ -266,20 +266,30 @@ def test_full_size_bench_config_sampled(mld):
 
 @pytest.mark.parametrize("d,chi", [(5, 4), (7, 8), (9, 32), (11, 32)])
 def test_mixed_tf32_vs_oracle_and_fp32(mld, d, chi):
-    """Mixed precision (split-TF32 tensor-core products, FP32 accumulate):
-    within 1e-5 of the oracle and of the FP32 path on every coset."""
+    """Mixed precision on the boundary-MPS kernel (split-TF32 tensor-core
+    products, FP32 accumulate): within 1e-5 of the oracle and of the FP32
+    path on every coset. (At d = 11 the default untruncated kernel is the
+    dense-state one; the boundary-MPS kernel is selected here.)"""
     n = d * d
     noise = synth.depolarizing(n, 0.12).astype(np.float32)
     E = synth.sample_errors(d, noise, 200, seed=31)
     syn = synth.syndromes_of(d, E)
     ref, _ = oracle.decode(d, noise, syn)
-    lp32, _ = gpu_decode(mld, d, noise, syn, chi)
-    lpm, am = gpu_decode(mld, d, noise, syn, chi, precision=mld.MLD_MIXED_TF32)
+    C = mld.Code(d)
+    C.set_exact_kernel(1)
+    nz = torch.tensor(noise, device="cuda")
+    sy = torch.tensor(syn.view(np.int64), device="cuda")
+    lp32, _ = C.decode(nz, sy, chi)
+    lpm, am = C.decode(nz, sy, chi, mld.MLD_MIXED_TF32)
+    torch.cuda.synchronize()
+    assert C.status() == 0
+    lp32, lpm, am = lp32.cpu().numpy(), lpm.cpu().numpy(), am.cpu().numpy()
     np.testing.assert_allclose(lpm, ref, rtol=0, atol=TOL)
     np.testing.assert_allclose(lpm, lp32, rtol=0, atol=TOL)
     check_argmax(am, ref)
     if d not in (9, 11):                 # tensor-core products only where they pay: FP32 kernel
         assert np.array_equal(lpm, lp32)
+    C.close()
 
 
 def test_mixed_unsupported_cases(mld):
@@ -307,10 +317,10 @@ def test_d13_exact_global_workspace(mld, prec):
     check_argmax(am, ref)
 
 
-@pytest.mark.parametrize("d", [11, 13])
+@pytest.mark.parametrize("d", [9, 11, 13])
 @pytest.mark.parametrize("mode", ["table", "depolarizing"])
 def test_exact_kernels_dense_and_mps_vs_oracle(mld, d, mode):
-    """Untruncated chi at d = 11 and 13 by both kernels: the boundary-MPS
+    """Untruncated chi at d = 9, 11 and 13 by both kernels: the boundary-MPS
     kernel (sites at the exact cut ranks) and the dense-state kernel (the
     2^(d+2)-entry column state in shared memory, factors applied in place),
     each against the FP64 oracle, with a per-qubit table and with one
@@ -352,12 +362,12 @@ def test_exact_kernels_dense_and_mps_vs_oracle(mld, d, mode):
 
 
 def test_exact_kernel_selector_arguments(mld):
-    C = mld.Code(9)
+    C = mld.Code(7)
     for bad in (-1, 3):
         with pytest.raises(mld.MldError):
             C.set_exact_kernel(bad)
     with pytest.raises(mld.MldError) as e:
-        C.set_exact_kernel(2)              # no dense-state kernel at d = 9
+        C.set_exact_kernel(2)              # no dense-state kernel at d = 7
     assert e.value.status == 2
     C.set_exact_kernel(1)
     C.set_exact_kernel(0)
