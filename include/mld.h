@@ -266,6 +266,16 @@ mld_status mld_code_set_svd_cutoff(mld_code* code, double rel);
  * same truncation rule. MLD_ERR_INVALID_ARG for other values. Host only. */
 mld_status mld_code_set_truncation_kernel(mld_code* code, int which);
 
+/* Largest bond capacity of the rank-adaptive sweep's first pass, which runs
+ * on every resident warp with a global slice per warp: 48 (2.25 MB a warp),
+ * 64 (4.5 MB) or 128 (17.8 MB; 45 GB on 152 SMs x 16 warps); 0 (default)
+ * the smallest of these that holds chi. Units whose bonds exceed the first
+ * pass's capacity restart in a second pass on few warps, a serial tail; a
+ * lower cap trades that tail for workspace. If a workspace cannot be
+ * allocated the next smaller capacities are used. MLD_ERR_INVALID_ARG for
+ * other values. Applies to later decodes of this code. Host only. */
+mld_status mld_code_set_truncation_workspace(mld_code* code, int max_bond);
+
 /* Which kernel decodes an untruncated chi (chi >= 2^floor(d/2), where the
  * boundary MPS of Sec. 3.2.1 discards nothing and is the exact boundary state
  * over one corner column): 0 (default) mld_autotune's choice for that chi if

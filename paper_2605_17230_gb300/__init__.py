@@ -36,7 +36,8 @@ EXPORTED_SYMBOLS = ["mld_code_create_rotated", "mld_code_destroy", "mld_code_inf
                     "mld_graph_launch", "mld_graph_destroy", "mld_autotune", "mld_decode_grad",
                     "mld_decode_dem", "mld_status_string", "mld_code_set_svd_cutoff",
                     "mld_decode_executed_flops", "mld_decode_bond_histogram", "mld_measure_fp32_peak",
-                    "mld_code_set_truncation_kernel", "mld_code_set_exact_kernel"]
+                    "mld_code_set_truncation_kernel", "mld_code_set_exact_kernel",
+                    "mld_code_set_truncation_workspace"]
 
 _lib = None
 
@@ -114,6 +115,8 @@ def load(build_if_missing: bool = True):
     lib.mld_code_set_truncation_kernel.restype = I
     lib.mld_code_set_exact_kernel.argtypes = [P, I]
     lib.mld_code_set_exact_kernel.restype = I
+    lib.mld_code_set_truncation_workspace.argtypes = [P, I]
+    lib.mld_code_set_truncation_workspace.restype = I
     lib.mld_measure_fp32_peak.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]
     lib.mld_measure_fp32_peak.restype = I
     lib.mld_decode_launches.argtypes = []
@@ -295,6 +298,12 @@ class Code:
         11, 13) (mld_code_set_exact_kernel)."""
         _check(load().mld_code_set_exact_kernel(ctypes.c_void_p(self.handle), int(which)),
                "mld_code_set_exact_kernel")
+
+    def set_truncation_workspace(self, max_bond: int):
+        """Bond capacity of the truncated sweep's first pass: 0 by chi
+        (default), 48, 64 or 128 (mld_code_set_truncation_workspace)."""
+        _check(load().mld_code_set_truncation_workspace(ctypes.c_void_p(self.handle), int(max_bond)),
+               "mld_code_set_truncation_workspace")
 
     def set_truncation_kernel(self, which: int):
         """0: chosen per chi (default); 1: rank-adaptive; 2: fixed-shape

@@ -804,15 +804,16 @@ mld_status grow(T** buf, size_t* have, size_t bytes) {
 }
 
 // Truncating chi: the rank-adaptive kernel (one warp per unit) over all units
-// on every resident warp, with the small slice capacities for chi <= 48 and
-// the mid ones (bonds up to 64) above, or the small ones if the mid
-// workspace cannot be allocated; the units it hands back go to a second pass
-// of the same kernel with large capacities on one block of warps per 4 SMs,
-// and what that hands back (bonds above 128) to the fixed-shape kernel in
-// global-workspace mode. (A unit handed back restarts from its first column
-// on few warps, so the first pass's capacities decide how long that tail
-// is: with bond 48 the few d=25 units whose middle cuts keep up to 64
-// values took as long as the whole first pass.) Later passes read their unit
+// on every resident warp, with the smallest slice capacities that hold bonds
+// of chi (bond 48, 64 or 128: 2.25, 4.5 or 17.8 MB per resident warp), or
+// smaller ones if that workspace cannot be allocated or the code's cap is
+// lower; the units it hands back go to a second pass of the same kernel with
+// the bond-128 capacities on one block of warps per 4 SMs, and what that
+// hands back (bonds above 128) to the fixed-shape kernel in global-workspace
+// mode. (A unit handed back restarts from its first column on few warps, so
+// the first pass's capacities decide how long that tail is: at d=25 with
+// bond 48 the few units whose middle cuts keep up to 64 values took as long
+// as the whole first pass, and at chi = 128 with bond 64 the tail cost 27%.) Later passes read their unit
 // count on the device and exit at once when it is zero. Control block
 // (bytes): [0] queue head of pass 1, [8] of pass 2, [16] overflow count of
 // pass 1, [20] of pass 2, [24] executed flops (f64, accumulated), [32] bond
@@ -835,12 +836,19 @@ mld_status decode_truncated(mld_code* C, const mld::Plan& P, const mld::SiteStep
     if (blocks1 > (units + upb - 1) / upb) blocks1 = (units + upb - 1) / upb;
     int64_t blocks2 = (sms + 3) / 4;
     const size_t ws2 = (size_t)blocks2 * upb * mld::kTruncLarge.slice();
-    mld::TruncCaps caps1 = chi > mld::kTruncSmall.max_bond ? mld::kTruncMid : mld::kTruncSmall;
+    // first-pass capacities: the smallest that hold bonds of chi (at most the
+    // cap set by mld_code_set_truncation_workspace); if that workspace cannot
+    // be allocated, the next smaller ones
+    const mld::TruncCaps order[3] = {mld::kTruncSmall, mld::kTruncMid, mld::kTruncLarge};
+    const int cap_bond = C->trunc_first_bond > 0 ? C->trunc_first_bond : mld::kTruncLarge.max_bond;
+    int ci = 0;
+    while (ci < 2 && chi > order[ci].max_bond && order[ci + 1].max_bond <= cap_bond) ++ci;
+    mld::TruncCaps caps1 = order[ci];
     mld_status st = grow(&C->d_tws, &C->tws_bytes,
                          std::max((size_t)blocks1 * upb * caps1.slice(), ws2) * sizeof(float));
-    if (st == MLD_ERR_NOMEM && caps1.max_bond != mld::kTruncSmall.max_bond) {
+    while (st == MLD_ERR_NOMEM && ci > 0) {
         (void)cudaGetLastError();                          // clear the failed allocation's error
-        caps1 = mld::kTruncSmall;
+        caps1 = order[--ci];
         st = grow(&C->d_tws, &C->tws_bytes,
                   std::max((size_t)blocks1 * upb * caps1.slice(), ws2) * sizeof(float));
     }
@@ -1319,6 +1327,14 @@ mld_status mld_code_set_svd_cutoff(mld_code* C, double rel) {
 mld_status mld_code_set_truncation_kernel(mld_code* C, int which) {
     if (!C || which < 0 || which > 2) return MLD_ERR_INVALID_ARG;
     C->trunc_kernel = which;
+    return MLD_OK;
+}
+
+mld_status mld_code_set_truncation_workspace(mld_code* C, int max_bond) {
+    if (!C || (max_bond != 0 && max_bond != mld::kTruncSmall.max_bond && max_bond != mld::kTruncMid.max_bond &&
+               max_bond != mld::kTruncLarge.max_bond))
+        return MLD_ERR_INVALID_ARG;
+    C->trunc_first_bond = max_bond;
     return MLD_OK;
 }
 

@@ -51,6 +51,9 @@ struct mld_code {
     // trunc_tuned holds mld_autotune's choice per chi
     int trunc_kernel = 0;
     std::vector<std::pair<int, int>> trunc_tuned;
+    // largest bond capacity of the rank-adaptive sweep's first pass (0: the
+    // smallest that holds chi, up to 128; else 48, 64 or 128)
+    int trunc_first_bond = 0;
     // which kernel runs an untruncated chi: 0 mld_autotune's choice for that
     // chi if it timed one (exact_tuned), else by d (the dense-state kernel at
     // d = 11, 13, the boundary-MPS kernel elsewhere); 1 the boundary-MPS

@@ -7,9 +7,9 @@
 namespace mld {
 
 // Capacities of one unit's shapes and global slice (floats). The first pass
-// over all units runs on every resident warp with the small ones (chi <= 48)
-// or the mid ones (bond 64, 4.5 MB per warp); units that exceed them are
-// decoded by a second pass with the large ones on few warps.
+// over all units runs on every resident warp with the smallest that hold
+// chi (bond 48, 64 or 128: 2.25, 4.5 or 17.8 MB per warp); units that exceed
+// them are decoded by a second pass with the large ones on few warps.
 struct TruncCaps {
     int max_bond;        // kept bond per cut
     int max_rows;        // carry rows

@@ -111,14 +111,25 @@ def test_mid_capacity_bonds_above_48_vs_fp64_mps(mld):
     assert hist[49:].sum() > 0                 # bonds above the small capacities occurred
 
 
-def test_pass2_bonds_above_64_vs_fp64_mps(mld):
+@pytest.mark.parametrize("first_bond", [0, 64])
+def test_bonds_above_64_vs_fp64_mps(mld, first_bond):
     """d=15, chi=72, cutoff 0: the middle cuts keep 72 values (the exact rank
-    is 128), beyond the first pass's bond 64, so these units are handed back
-    and decoded by the large-capacity pass."""
+    is 128). By default the first pass runs with the bond-128 capacities and
+    decodes these units itself; with its capacity capped at 64
+    (mld_code_set_truncation_workspace) they are handed back and decoded by
+    the second, large-capacity pass. Both against the FP64 oracle."""
     ref = golden_large()[(15, 72, "depolarizing")]
     noise, _, syn = workload(15, "depolarizing", 2)
-    lp, _, _, hist = decode(mld, 15, noise, syn, 72, 0.0)
-    check_lead_and_posterior(lp, ref)
+    code = mld.Code(15)
+    code.set_svd_cutoff(0.0)
+    code.set_truncation_kernel(1)
+    code.set_truncation_workspace(first_bond)
+    lp, _ = code.decode(torch.tensor(noise, device="cuda"), torch.tensor(syn.view(np.int64), device="cuda"), 72)
+    torch.cuda.synchronize()
+    assert code.status() == 0
+    hist = code.bond_histogram()
+    code.close()
+    check_lead_and_posterior(lp.cpu().numpy(), ref)
     assert hist[64] > 0                        # the last bin counts kept bonds of 64 and more
 
 
@@ -223,4 +234,9 @@ def test_svd_cutoff_and_kernel_argument_checks(mld):
             code.set_truncation_kernel(bad)
     for ok in (0, 1, 2):
         code.set_truncation_kernel(ok)
+    for bad in (-1, 1, 32, 100, 256):
+        with pytest.raises(mld.MldError):
+            code.set_truncation_workspace(bad)
+    for ok in (0, 48, 64, 128):
+        code.set_truncation_workspace(ok)
     code.close()
