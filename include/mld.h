@@ -122,9 +122,13 @@ mld_status mld_code_layout(const mld_code* code, int32_t* stab_type, int32_t* st
  *   argmax     device pointer uint8[B] or NULL: argmax_l Z_l(s), ties and
  *              all--inf rows go to the lowest class index.
  *   stream     cudaStream_t (NULL = legacy default stream).
+ * Which kernel runs: see mld_code_set_exact_kernel (untruncated chi; the
+ * same exact boundary state held as MPS sites or, at d = 11 and 13 by
+ * default, densely) and mld_code_set_truncation_kernel (truncating chi).
  * All arrays are caller-owned device memory; the call is asynchronous and
- * allocates nothing per call after the first call for a given (code, chi)
- * (which uploads the column plan). Status of the device work: see
+ * allocates nothing per call once a call for the same (code, chi) and at
+ * least the same B has been made (the first uploads the column plan and
+ * sizes the workspaces). Status of the device work: see
  * mld_decode_status; a noise row that is not a probability distribution
  * (an entry negative or non-finite, or the row's sum off 1 by more than
  * 1e-6) or a depolarizing strength outside [0, 1] is reported there as
