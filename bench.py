@@ -367,7 +367,8 @@ def run_point(args):
 
 def run_large(args):
     """The scale workload: rotated d=17 and 25, depolarizing p=0.12 and biased eta=100 (p=0.12),
-    16,384 syndromes per point (seed config_seed(5, d, 0.12)), chi = 32, 64, 128. Every point reports
+    16,384 syndromes per point (seed config_seed(5, d, p)), chi = 32, 64, 128 (--large-p, --large-d,
+    --large-chi and --large-noise change the grid; the comparison columns need chi = 128). Every point reports
     syndromes/s, the executed flops rate, the kept-bond histogram of the rank-adaptive truncation,
     the logical-error rate with its 95% Wilson interval, and the largest change of the leading
     coset's ln Z and of the posterior against the chi=128 run of the same syndromes."""
@@ -379,12 +380,13 @@ def run_large(args):
     for d in args.large_d:
         code = mld.Code(d)
         n = d * d
-        for name, noise in (("depolarizing p=0.12", synth.depolarizing(n, 0.12)),
-                            ("biased eta=100 p=0.12", synth.biased(n, 0.12, 100.0))):
+        pl = args.large_p
+        for name, noise in ((f"depolarizing p={pl:g}", synth.depolarizing(n, pl)),
+                            (f"biased eta=100 p={pl:g}", synth.biased(n, pl, 100.0))):
             if name.split()[0] not in args.large_noise:
                 continue
             noise = noise.astype(np.float32)
-            E = synth.sample_errors(d, noise, Bl, seed=synth.config_seed(5, d, 0.12))
+            E = synth.sample_errors(d, noise, Bl, seed=synth.config_seed(5, d, pl))
             true = synth.true_class(d, E)
             nz = torch.tensor(noise, device="cuda")
             sy = torch.tensor(synth.syndromes_of(d, E).view(np.int64), device="cuda")
@@ -635,6 +637,7 @@ def main():
     ap.add_argument("--large-chi", type=int, nargs="+", default=[32, 64, 128],
                     help="large: bond caps (the comparison columns need 128)")
     ap.add_argument("--large-noise", nargs="+", default=["depolarizing", "biased"], help="large: noise models")
+    ap.add_argument("--large-p", type=float, default=0.12, help="large: physical error rate")
     ap.add_argument("--ler-batch", type=int, default=65536)
     ap.add_argument("--point-d", type=int, default=13, help="point: distance")
     ap.add_argument("--point-chi", type=int, default=64, help="point: bond cap")
