@@ -78,3 +78,26 @@ def test_interrupted_job_resumes_to_the_same_bits(mld, tmp_path, mode):
     lp2, _ = stream.decode_to_files(code, noise, syn, chi, prefix, chunk=chunk, noise_mode=nmode, resume=False)
     np.testing.assert_array_equal(np.asarray(lp2), ref_lp.cpu().numpy())
     code.close()
+
+
+def test_truncated_job_resumes_to_the_same_bits(mld, tmp_path):
+    """The same at a truncating chi (d=11, chi=16, rank-adaptive sweep): units
+    are taken from a device queue in any order, but each is decoded by one
+    warp in a fixed order, so chunks give the bits of one whole decode."""
+    from paper_2605_17230_gb300 import stream
+    d, chi, B, chunk = 11, 16, 1000, 384
+    table = synth.depolarizing(d * d, 0.12).astype(np.float32)
+    syn = synth.syndromes_of(d, synth.sample_errors(d, table, B, seed=9))
+    code = mld.Code(d)
+    code.set_truncation_kernel(1)
+    noise = torch.tensor(table, device="cuda")
+    ref, _ = code.decode(noise, torch.tensor(syn.view(np.int64), device="cuda"), chi)
+    torch.cuda.synchronize()
+    prefix = str(tmp_path / "trunc")
+    with pytest.raises(Stop):
+        def stop(start, count):
+            raise Stop()
+        stream.decode_to_files(code, noise, syn, chi, prefix, chunk=chunk, on_chunk=stop)
+    lp, _ = stream.decode_to_files(code, noise, syn, chi, prefix, chunk=chunk)
+    np.testing.assert_array_equal(np.asarray(lp), ref.cpu().numpy())
+    code.close()
