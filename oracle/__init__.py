@@ -10,7 +10,9 @@ group enumeration and the derivative contractions. ``mps.py`` holds the
 boundary-MPS method of Sec. 3.2.1 in FP64 with numpy's QR and SVD, used to
 check truncated bond dimensions. ``dem_qubit_table`` and
 ``dem_bruteforce_table`` state what the detector picture (Sec. 3.2.2)
-computes for a code-capacity error-mechanism model.
+computes for a code-capacity error-mechanism model. ``kac_ward.py`` evaluates
+the coset sums under independent X/Z noise by Kac-Ward determinants
+(Sec. 3.1.3), a second exact method.
 """
 from __future__ import annotations
 
