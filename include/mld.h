@@ -60,13 +60,16 @@ typedef enum {
                                   exponent */
     MLD_MIXED_BF16 = 1,        /* reserved: MLD_ERR_UNSUPPORTED (BF16 operands
                                   miss |d ln Z| <= 1e-3 on the leading coset) */
-    MLD_MIXED_TF32 = 2         /* data-site MPO.MPS products on the tensor
+    MLD_MIXED_TF32 = 2,        /* data-site MPO.MPS products on the tensor
                                   cores from operands split into two TF32
                                   parts (hi.hi + hi.lo + lo.hi), FP32
                                   accumulate; untruncated chi only. The split
                                   products run at d = 9 and 11, where they are
                                   faster; at other d the FP32 products run
                                   (same or better accuracy) */
+    MLD_FP64 = 3               /* complex FP64 elimination; mld_decode_xz
+                                  only (other entry points return
+                                  MLD_ERR_INVALID_ARG) */
 } mld_precision;
 
 typedef enum {
@@ -345,6 +348,38 @@ mld_status mld_decode_flops(const mld_code* code, int chi, int precision, double
 mld_status mld_decode_dem(const mld_code* code, const int32_t* mech_qubit, const int32_t* mech_pauli,
                           const double* mech_p, int32_t n_mech, const uint64_t* syndromes, int64_t B,
                           double* logP, uint8_t* argmax, void* stream);
+
+/* MLD under independent X/Z noise by Kac-Ward determinants (Sec. 3.1.3:
+ * the planar random-bond Ising model of each part, Z proportional to
+ * sqrt(det(I - Lambda)) per logical sector). Qubit q flips its X part with
+ * probability px[q] and its Z part with probability pz[q], independently:
+ * Pr(E) = prod_q px^x (1-px)^(1-x) pz^z (1-pz)^(1-z), so the class
+ * probabilities factorise, Z_l = ZX_{l_X} ZZ_{l_Z}. Classes and their order
+ * are those of mld_decode (l = l_X + 2 l_Z); the result equals mld_decode with
+ * the table (1-px)(1-pz), px(1-pz), px pz, (1-px) pz (I, X, Y, Z).
+ *   px         device float[n], each in (0, 1)
+ *   pz         device float[n], each in (0, 1); NULL for bit-flip noise (no Z
+ *              errors): ln Z is -inf for l_Z = 1, and for every class of a
+ *              syndrome whose X-type part is nonzero
+ *   syndromes  device uint64[B][words]
+ *   precision  MLD_FP32 or MLD_FP64 (complex arithmetic of that type)
+ *   logP       device double[B][4]: ln Z_l(s)
+ *   argmax     device uint8[B] or NULL (ties -> lowest class)
+ * Exact in exact arithmetic at any odd d >= 3 up to 25. Each part is one
+ * banded elimination with partial pivoting (order 2|E| = 2d^2 + O(d),
+ * bandwidth 3d), one warp per syndrome, the two sectors sharing all but a
+ * final 4 x 4 determinant. The determinant is a sum of signed terms: a class
+ * far less likely than the leading one carries an error of order
+ * eps * cond relative to the leading class's Z, while the leading class's
+ * ln Z and the decision keep the arithmetic's accuracy. A probability
+ * outside (0, 1) sets MLD_ERR_INVALID_ARG in the status word
+ * (mld_decode_status); a vanishing pivot sets MLD_ERR_NUMERIC and gives -inf.
+ * The first call for a code builds the graph and copies it to the device
+ * (synchronous, a few hundred KB); later calls are asynchronous on stream
+ * with no allocation. MLD_ERR_UNSUPPORTED if a warp's window exceeds the
+ * device's shared memory per block (FP64 at d = 25 does not fit). */
+mld_status mld_decode_xz(const mld_code* code, const float* px, const float* pz, const uint64_t* syndromes,
+                         int64_t B, int precision, double* logP, uint8_t* argmax, void* stream);
 
 /* Measurement helper (not part of the method): times a kernel of independent
  * FP32 FMA chains on every SM of the current device for about `seconds` and

@@ -19,14 +19,14 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["MLD_OK", "MLD_FP32", "MLD_MIXED_BF16", "MLD_MIXED_TF32", "MLD_NOISE_TABLE",
+__all__ = ["MLD_OK", "MLD_FP32", "MLD_MIXED_BF16", "MLD_MIXED_TF32", "MLD_FP64", "MLD_NOISE_TABLE",
            "MLD_NOISE_DEPOL", "MldError", "Code", "load", "library_path", "mld_code_create_rotated",
            "mld_decode", "mld_decode_host", "mld_decode_status", "mld_decode_launches",
            "mld_status_string", "EXPORTED_SYMBOLS", "log_coset_probabilities", "estimate_noise",
-           "noise_table_from_logits"]
+           "noise_table_from_logits", "mld_decode_xz"]
 
 MLD_OK = 0
-MLD_FP32, MLD_MIXED_BF16, MLD_MIXED_TF32 = 0, 1, 2
+MLD_FP32, MLD_MIXED_BF16, MLD_MIXED_TF32, MLD_FP64 = 0, 1, 2, 3
 MLD_NOISE_TABLE, MLD_NOISE_DEPOL = 0, 1
 
 EXPORTED_SYMBOLS = ["mld_code_create_rotated", "mld_code_destroy", "mld_code_info", "mld_code_layout",
@@ -37,7 +37,7 @@ EXPORTED_SYMBOLS = ["mld_code_create_rotated", "mld_code_destroy", "mld_code_inf
                     "mld_decode_dem", "mld_status_string", "mld_code_set_svd_cutoff",
                     "mld_decode_executed_flops", "mld_decode_bond_histogram", "mld_measure_fp32_peak",
                     "mld_code_set_truncation_kernel", "mld_code_set_exact_kernel",
-                    "mld_code_set_truncation_workspace"]
+                    "mld_code_set_truncation_workspace", "mld_decode_xz"]
 
 _lib = None
 
@@ -105,6 +105,8 @@ def load(build_if_missing: bool = True):
     lib.mld_decode_grad.restype = I
     lib.mld_decode_dem.argtypes = [P, P, P, P, I, P, L, P, P, P]
     lib.mld_decode_dem.restype = I
+    lib.mld_decode_xz.argtypes = [P, P, P, P, L, I, P, P, P]
+    lib.mld_decode_xz.restype = I
     lib.mld_code_set_svd_cutoff.argtypes = [P, ctypes.c_double]
     lib.mld_code_set_svd_cutoff.restype = I
     lib.mld_decode_executed_flops.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
@@ -270,6 +272,19 @@ class Code:
         mld_decode_dem(self.handle, mech_qubit, mech_pauli, mech_p, syndromes.contiguous(), B, logP, am, stream)
         return logP, am
 
+    def decode_xz(self, px, pz, syndromes, precision=MLD_FP32, with_argmax=True, stream=None):
+        """Kac-Ward decode under independent X/Z noise: px, pz float32 [n]
+        CUDA tensors (pz None: bit-flip noise). Returns (logP float64 [B][4],
+        argmax uint8 [B] or None)."""
+        import torch
+        B = syndromes.shape[0]
+        dev = syndromes.device
+        logP = torch.empty((B, 4), dtype=torch.float64, device=dev)
+        am = torch.empty((B,), dtype=torch.uint8, device=dev) if with_argmax else None
+        mld_decode_xz(self.handle, px.contiguous(), None if pz is None else pz.contiguous(), syndromes.contiguous(),
+                      B, precision, logP, am, stream)
+        return logP, am
+
     def flops(self, chi, precision=MLD_FP32) -> float:
         """Counted flops per syndrome (four classes) of the executed schedule."""
         v = ctypes.c_double()
@@ -400,6 +415,16 @@ def mld_decode_dem(code, mech_qubit, mech_pauli, mech_p, syndromes, B, logP, arg
     f = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     _check(load().mld_decode_dem(ctypes.c_void_p(code), f(q), f(c), f(p), int(q.size), _ptr(syndromes), int(B),
                                  _ptr(logP), _ptr(argmax), ctypes.c_void_p(int(stream))), "mld_decode_dem")
+
+
+def mld_decode_xz(code, px, pz, syndromes, B, precision, logP, argmax=None, stream=None):
+    """C-ABI mld_decode_xz (Kac-Ward, independent X/Z noise): px, pz (or None
+    for bit-flip noise), syndromes and outputs are torch CUDA tensors."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(load().mld_decode_xz(ctypes.c_void_p(code), _ptr(px), _ptr(pz), _ptr(syndromes), int(B), int(precision),
+                                _ptr(logP), _ptr(argmax), ctypes.c_void_p(int(stream))), "mld_decode_xz")
 
 
 def _logz_function():

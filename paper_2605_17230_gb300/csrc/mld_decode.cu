@@ -1007,6 +1007,7 @@ void mld_code_destroy(mld_code* C) {
         cudaFree(C->d_tws);
         cudaFree(C->d_tctl);
         cudaFree(C->d_ovf);
+        cudaFree(C->d_kw);
     }
     delete C;
 }

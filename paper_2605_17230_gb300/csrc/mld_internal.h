@@ -60,6 +60,13 @@ struct mld_code {
     // kernel; 2 the dense-state kernel (d = 9, 11, 13)
     int exact_kernel = 0;
     std::vector<std::pair<int, int>> exact_tuned;
+    // Kac-Ward solver (mld_decode_xz): one device block holding the ordered
+    // matrix of the spin graph (CSR row starts, columns, weight sources, each
+    // band row's last column, the quarter-turn qubit map; then the phases as
+    // double pairs at kw_ph_off), built on first use, and its sizes
+    void* d_kw = nullptr;
+    int kw_N = 0, kw_Nb = 0, kw_bl = 0, kw_bu = 0, kw_nplaq = 0, kw_nnz = 0;
+    size_t kw_ph_off = 0;
 };
 
 namespace mld {

@@ -1,0 +1,203 @@
+"""Kac-Ward decode under independent X/Z noise (mld_decode_xz, Sec. 3.1.3)
+against the oracle: the exact variable elimination (Eq. 7) element by element
+at d = 3..13, the FP64 Kac-Ward oracle at d = 17 and 25 on sampled syndromes,
+the generator-picture CUDA path on the same table, bit-flip noise, and the
+degenerate and invalid inputs.
+
+Tolerances. FP64: every class to 1e-8 where the oracle's exact value is within
+30 nats of the leading class (beyond that the signed determinant of a class
+that unlikely is below FP64's resolution of the leading one, a property of the
+method). FP32: the leading class's ln Z to 1e-4 (1e-3 at d = 25, where about
+2,600 pivots round: measured 6.6e-4 on one of four syndromes, reproduced by a
+CPU emulation of the same elimination in complex64) and the posteriors
+Z_l / sum Z to 1e-3 (the FP32 determinant resolves a class only down to about
+1e-6 .. 1e-3 of the leading one, growing with d and falling with p); the
+decisions equal the oracle's wherever its two best classes differ by more than
+1e-3 in ln Z."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import kac_ward as okw
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mld():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_17230_gb300 as m
+    m.load()
+    return m
+
+
+def _rates(d, seed, lo, hi):
+    rng = np.random.default_rng(seed)
+    n = d * d
+    return rng.uniform(lo, hi, n).astype(np.float32), rng.uniform(lo, hi, n).astype(np.float32)
+
+
+def _run(mld, code, px, pz, syn, precision):
+    dpx = torch.tensor(px, device="cuda")
+    dpz = None if pz is None else torch.tensor(pz, device="cuda")
+    lp, am = code.decode_xz(dpx, dpz, torch.tensor(syn.view(np.int64), device="cuda"), precision)
+    torch.cuda.synchronize()
+    assert code.status() == 0
+    return lp.cpu().numpy(), am.cpu().numpy()
+
+
+def _posterior(v):
+    m = v.max(axis=1, keepdims=True)
+    e = np.exp(v - m)
+    return e / e.sum(axis=1, keepdims=True)
+
+
+def _check_fp32(lp, am, ref, ram, lead_atol=1e-4):
+    rows = np.arange(len(ref))
+    lead = np.argmax(ref, axis=1)
+    np.testing.assert_allclose(lp[rows, lead], ref[rows, lead], rtol=0, atol=lead_atol)
+    np.testing.assert_allclose(_posterior(lp), _posterior(ref), rtol=0, atol=1e-3)
+    srt = np.sort(ref, axis=1)
+    clear = srt[:, -1] - srt[:, -2] > 1e-3
+    np.testing.assert_array_equal(am[clear], ram[clear])
+
+
+def _check_fp64(lp, am, ref, ram, atol=1e-8):
+    near = ref >= ref.max(axis=1, keepdims=True) - 30.0
+    np.testing.assert_allclose(lp[near], ref[near], rtol=0, atol=atol)
+    srt = np.sort(ref, axis=1)
+    clear = srt[:, -1] - srt[:, -2] > 1e-6
+    np.testing.assert_array_equal(am[clear], ram[clear])
+
+
+@pytest.mark.parametrize("d,B", [(3, 200), (5, 97), (7, 64), (9, 40), (11, 16), (13, 8)])
+def test_xz_vs_exact_oracle(mld, d, B):
+    """Per-qubit rates in [0.02, 0.2], sampled errors; B not a multiple of the
+    grid. FP64 and FP32 against the exact contraction."""
+    px, pz = _rates(d, d, 0.02, 0.2)
+    tab = okw.xz_table(px.astype(np.float64), pz.astype(np.float64))
+    syn = synth.syndromes_of(d, synth.sample_errors(d, tab, B, seed=50 + d))
+    ref, ram = oracle.decode(d, tab, syn)
+    code = mld.Code(d)
+    lp64, am64 = _run(mld, code, px, pz, syn, mld.MLD_FP64)
+    _check_fp64(lp64, am64, ref, ram)
+    lp32, am32 = _run(mld, code, px, pz, syn, mld.MLD_FP32)
+    _check_fp32(lp32, am32, ref, ram)
+
+
+@pytest.mark.parametrize("d", [3, 7, 11])
+def test_bitflip_vs_exact_oracle(mld, d):
+    """pz = NULL: -inf exactly where the exact contraction is zero (the l_Z = 1
+    classes, and every class of a syndrome with an X-type bit), the finite
+    classes equal."""
+    n = d * d
+    px, _ = _rates(d, 3 * d, 0.03, 0.15)
+    tab = okw.xz_table(px.astype(np.float64), None)
+    syn = synth.syndromes_of(d, synth.sample_errors(d, tab, 24, seed=d))
+    t, _, _, _ = oracle.layout(d)
+    bits = np.zeros((1, n - 1), np.uint8)
+    bits[0, int(np.nonzero(t == 0)[0][-1])] = 1
+    syn = np.concatenate([syn, synth.pack_bits(bits)])
+    ref, ram = oracle.decode(d, tab, syn)
+    code = mld.Code(d)
+    for prec in (mld.MLD_FP64, mld.MLD_FP32):
+        lp, am = _run(mld, code, px, None, syn, prec)
+        np.testing.assert_array_equal(np.isfinite(lp), np.isfinite(ref))
+        assert np.isneginf(lp[-1]).all()
+        fin = np.isfinite(ref).all(axis=0)
+        live = ref[:-1, :2]
+        if prec == mld.MLD_FP64:
+            _check_fp64(lp[:-1, :2], am[:-1], live, ram[:-1])
+        else:
+            _check_fp32(lp[:-1, :2], am[:-1], live, ram[:-1])
+        assert not fin[2:].any()
+
+
+@pytest.mark.parametrize("d,B,p", [(17, 12, 0.08), (25, 4, 0.08)])
+def test_large_d_vs_kac_ward_oracle(mld, d, B, p):
+    """At the distances the boundary-MPS path truncates: against the FP64
+    Kac-Ward oracle (dense slogdet of the whole matrix, another drawing and
+    no banding) on sampled syndromes at a uniform rate."""
+    n = d * d
+    px = np.full(n, p, np.float32)
+    pz = np.full(n, p, np.float32)
+    tab = okw.xz_table(px.astype(np.float64), pz.astype(np.float64))
+    syn = synth.syndromes_of(d, synth.sample_errors(d, tab, B, seed=d))
+    ref, ram = okw.decode_xz(d, px.astype(np.float64), pz.astype(np.float64), syn)
+    code = mld.Code(d)
+    lp64, am64 = _run(mld, code, px, pz, syn, mld.MLD_FP64)
+    _check_fp64(lp64, am64, ref, ram, atol=1e-7)
+    lp32, am32 = _run(mld, code, px, pz, syn, mld.MLD_FP32)
+    _check_fp32(lp32, am32, ref, ram, lead_atol=1e-4 if d <= 17 else 1e-3)
+
+
+def test_agrees_with_generator_sweep(mld):
+    """d = 9, the bench's noise shape: the Kac-Ward kernel and the exact
+    boundary-MPS sweep on the same independent X/Z table."""
+    d, B = 9, 512
+    px, pz = _rates(d, 77, 0.03, 0.12)
+    tab = okw.xz_table(px.astype(np.float64), pz.astype(np.float64)).astype(np.float32)
+    syn = synth.syndromes_of(d, synth.sample_errors(d, tab.astype(np.float64), B, seed=9))
+    code = mld.Code(d)
+    dsyn = torch.tensor(syn.view(np.int64), device="cuda")
+    lp_mps, am_mps = code.decode(torch.tensor(tab, device="cuda"), dsyn, 16)
+    lp_kw, am_kw = code.decode_xz(torch.tensor(px, device="cuda"), torch.tensor(pz, device="cuda"), dsyn)
+    torch.cuda.synchronize()
+    a, b = lp_mps.cpu().numpy(), lp_kw.cpu().numpy()
+    rows = np.arange(B)
+    lead = np.argmax(a, axis=1)
+    np.testing.assert_allclose(b[rows, lead], a[rows, lead], rtol=0, atol=1e-4)
+    srt = np.sort(a, axis=1)
+    clear = srt[:, -1] - srt[:, -2] > 1e-3
+    np.testing.assert_array_equal(am_kw.cpu().numpy()[clear], am_mps.cpu().numpy()[clear])
+
+
+def test_degenerate_and_invalid(mld):
+    d = 5
+    n = d * d
+    code = mld.Code(d)
+    px = torch.full((n,), 0.1, device="cuda")
+    empty = torch.zeros((0, code.words), dtype=torch.int64, device="cuda")
+    lp, am = code.decode_xz(px, px, empty)
+    assert lp.shape == (0, 4)
+    syn = torch.zeros((3, code.words), dtype=torch.int64, device="cuda")
+    # the zero syndrome: the identity's classes lead
+    lp, am = code.decode_xz(px, px, syn, mld.MLD_FP64)
+    torch.cuda.synchronize()
+    assert (am.cpu().numpy() == 0).all()
+    # an unknown precision is refused before any launch
+    out = torch.empty((3, 4), dtype=torch.float64, device="cuda")
+    with pytest.raises(mld.MldError) as e:
+        mld.mld_decode_xz(code.handle, px, px, syn, 3, 7, out)
+    assert e.value.status == 1
+    # a rate outside (0, 1) is flagged in the status word
+    bad = px.clone()
+    bad[4] = 0.0
+    code.decode_xz(bad, px, syn)
+    torch.cuda.synchronize()
+    assert code.status() == 1            # MLD_ERR_INVALID_ARG
+    code2 = mld.Code(d)
+    nan = px.clone()
+    nan[0] = float("nan")
+    code2.decode_xz(px, nan, syn)
+    torch.cuda.synchronize()
+    assert code2.status() == 1
+
+
+def test_ln_z_sums_to_syndrome_probability(mld):
+    """Sum over the four classes of Z_l = Pr(s), and over all 2^8 syndromes of
+    d = 3 the probabilities sum to one (FP64)."""
+    d = 3
+    px, pz = _rates(d, 4, 0.05, 0.4)
+    m = d * d - 1
+    bits = ((np.arange(1 << m)[:, None] >> np.arange(m)[None, :]) & 1).astype(np.uint8)
+    syn = synth.pack_bits(bits)
+    code = mld.Code(d)
+    lp, _ = _run(mld, code, px, pz, syn, mld.MLD_FP64)
+    assert abs(np.exp(lp).sum() - 1.0) < 1e-9
+    assert math.isfinite(lp.max())
