@@ -11,7 +11,8 @@ generator in synth/, syndromes extracted.
 
 Other workloads (--workload): mixed (the d=3..13 graph batch), large (d=17
 and 25 at truncating chi), ler (logical-error rates of the d/p grid against
-the oracle), grad, dmle, dem, point (one (d, chi, p) decode point).
+the oracle), grad, dmle, dem, point (one (d, chi, p) decode point), kw (the
+Kac-Ward decode under independent X/Z noise, d=9..25).
 
 Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle
 on the host cores instead (a bounded sample per step).
@@ -614,6 +615,66 @@ def run_dem(args):
     print(json.dumps(line), flush=True)
 
 
+def run_kw(args):
+    """Kac-Ward decode (Sec. 3.1.3) under independent X/Z noise with
+    px = pz = p on every qubit (default 0.10): syndromes sampled from the
+    product table (seed config_seed(7, d, p)); per d the FP32 rate, the FP64
+    rate on a quarter of the batch, the logical-error rate, and on the same
+    syndromes the boundary-MPS decode (untruncated chi at d <= 13, chi = 32
+    above) with its rate and the number of decisions that differ."""
+    import torch
+    import paper_2605_17230_gb300 as mld
+
+    def timed(fn, steps):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, out
+
+    default_b = {5: 65536, 7: 65536, 9: 65536, 11: 32768, 13: 32768, 15: 16384, 17: 16384}
+    rows = []
+    for d in args.kw_d:
+        n, p = d * d, args.kw_p
+        Bd = args.kw_batch or default_b.get(d, 4096)
+        px = np.full(n, p, np.float32)
+        tab = synth.independent_xz(px, px)
+        E = synth.sample_errors(d, tab, Bd, seed=synth.config_seed(7, d, p))
+        true = torch.tensor(synth.true_class(d, E).astype(np.int64), device="cuda")
+        sy = torch.tensor(synth.syndromes_of(d, E).view(np.int64), device="cuda")
+        code = mld.Code(d)
+        dpx = torch.tensor(px, device="cuda")
+        ms32, (lp, am) = timed(lambda: code.decode_xz(dpx, dpx, sy, mld.MLD_FP32), args.steps)
+        B64 = max(1, Bd // 4)
+        ms64, (lp64, am64) = timed(lambda: code.decode_xz(dpx, dpx, sy[:B64], mld.MLD_FP64),
+                                   max(1, args.steps // 5))
+        if code.status() != 0:
+            raise RuntimeError("device status after the Kac-Ward decode")
+        row = {"d": d, "p": p, "syndromes": Bd, "fp32_value": Bd / (ms32 / 1e3), "fp32_ms": ms32,
+               "fp64_value": B64 / (ms64 / 1e3), "fp64_syndromes": B64,
+               "logical_error_rate": float((am.long() != true).float().mean().item()),
+               "fp32_fp64_decisions_differ": int((am[:B64] != am64).sum().item())}
+        if not args.kw_no_mps:
+            chi = 1 << (d // 2) if d <= 13 else 32
+            nz = torch.tensor(tab.astype(np.float32), device="cuda")
+            code.decode(nz, sy[:256], chi)
+            msm, (lpm, amm) = timed(lambda: code.decode(nz, sy, chi), max(1, args.steps // 10))
+            row.update({"mps_chi": chi, "mps_value": Bd / (msm / 1e3),
+                        "mps_decisions_differ": int((amm != am).sum().item()),
+                        "mps_logical_error_rate": float((amm.long() != true).float().mean().item())})
+        rows.append(row)
+        code.close()
+    line = {"metric": "syndromes/s of the Kac-Ward decode (independent X/Z noise, 4 classes)", "workload": "kw",
+            "unit": "syndromes/s", "data": "synthetic", "dtype": "complex f32 elimination, f64 ln Z",
+            "steps": args.steps, "warmup": args.warmup, "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -625,13 +686,18 @@ def main():
     ap.add_argument("--batch", type=int, default=B, help="syndromes per GPU per step (default: the "
                     "65536 of the workload; smaller values only for profiling captures)")
     ap.add_argument("--workload", default="metric",
-                    choices=["metric", "mixed", "grad", "large", "ler", "dmle", "dem", "point"],
+                    choices=["metric", "mixed", "grad", "large", "ler", "dmle", "dem", "point", "kw"],
                     help="metric: the headline d=9 line (default); mixed: the 1,048,576-syndrome mixed-d "
                          "graph batch; grad: the adjoint on the d=7 workload; dmle: full-batch noise "
                          "estimation from 1,048,576 unlabelled d=9 syndromes; dem: detector-picture decode of "
                          "a d=9 X/Y/Z mechanism model; large: d=17, 25 at chi 32..128 (truncating); "
                          "ler: logical-error rates of the d/p grid against the oracle; point: one (d, chi, p) "
-                         "decode point, FP32 and mixed")
+                         "decode point, FP32 and mixed; kw: the Kac-Ward decode under independent X/Z "
+                         "noise against the boundary-MPS decode of the same syndromes")
+    ap.add_argument("--kw-d", type=int, nargs="+", default=[9, 13, 17, 25], help="kw: distances")
+    ap.add_argument("--kw-p", type=float, default=0.10, help="kw: X and Z flip rate per qubit")
+    ap.add_argument("--kw-batch", type=int, default=0, help="kw: syndromes per decode (0: by d)")
+    ap.add_argument("--kw-no-mps", action="store_true", help="kw: skip the boundary-MPS comparison")
     ap.add_argument("--large-batch", type=int, default=16384)
     ap.add_argument("--large-d", type=int, nargs="+", default=[17, 25], help="large: distances")
     ap.add_argument("--large-chi", type=int, nargs="+", default=[32, 64, 128],
@@ -663,6 +729,8 @@ def main():
         return run_large(args) if rank == 0 else None
     if args.workload == "ler":
         return run_ler(args) if rank == 0 else None
+    if args.workload == "kw":
+        return run_kw(args) if rank == 0 else None
     if args.workload == "point":
         return run_point(args) if rank == 0 else None
 

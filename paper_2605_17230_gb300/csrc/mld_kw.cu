@@ -210,20 +210,21 @@ struct Cplx<double> {
 };
 
 constexpr int kKwMaxColsPerLane = 5;   // (bl + bu) / 32 rounded up; 5 covers d <= 25
+constexpr int kKwRowSlots = 32;        // successors per row, padded (at most d + 1 at a ghost)
+constexpr int kKwMaxChunks = 3;        // (bl + 2) / 32 rounded up: candidate rows of one step
 
 struct KwArgs {
-    // the graph (device copies)
-    const int* row_start;
-    const int* col;
-    const int* src;
-    const double2* ph;
+    // the graph (device copies): row i's successors at [i * 32, i * 32 + 32),
+    // column -1 for padding
+    const int* ecol;
+    const int* esrc;
+    const double2* eph;
     const int* ext0;
     const int* zmap;
     int N, Nb, bl, bu;
     int WR, WC, RS;     // window rows (bl + 1), window band columns (bl + bu + 1), row stride (WC + 4)
     int n, words;
     double cst;         // (n_plaq - n) ln 2
-    size_t warp_bytes;  // shared memory per warp
     // the decode
     const uint64_t* dmask;
     const float* px;
@@ -237,11 +238,11 @@ struct KwArgs {
 
 // Per-warp shared memory: the window rows (WR band slots, then the two border
 // rows; each RS entries: WC band columns by column index mod WC, the two
-// border columns, the two sector-1 columns), the multipliers and active-row
-// list of a step, the weights of the current part, the row map (logical row
-// mod WR -> slot) and each slot's last nonzero band column.
+// border columns, the two sector-1 columns), the weights of the current part,
+// the row map (logical row mod WR -> slot) and each slot's last nonzero band
+// column.
 struct KwLayout {
-    size_t a, mult, wt, map, ext, act, total;
+    size_t a, wt, map, ext, total;
 };
 
 __host__ __device__ inline size_t kw_align(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -249,37 +250,38 @@ __host__ __device__ inline size_t kw_align(size_t x) { return (x + 15) & ~(size_
 __host__ __device__ inline KwLayout kw_layout(int WR, int RS, int n, size_t cbytes) {
     KwLayout L;
     L.a = 0;
-    L.mult = kw_align(L.a + (size_t)(WR + 2) * RS * cbytes);
-    L.wt = kw_align(L.mult + (size_t)(WR + 2) * cbytes);
+    L.wt = kw_align(L.a + (size_t)(WR + 2) * RS * cbytes);
     L.map = kw_align(L.wt + (size_t)n * (cbytes / 2));
     L.ext = kw_align(L.map + (size_t)WR * 4);
-    L.act = kw_align(L.ext + (size_t)(WR + 2) * 4);
-    L.total = kw_align(L.act + (size_t)(WR + 2) * 4);
+    L.total = kw_align(L.ext + (size_t)(WR + 2) * 4);
     return L;
 }
 
+// This lane's successor of row i: its column (-1 if none) and its values in
+// sector 0 and, for the sector columns, sector 1.
 template <typename T, typename C>
-__device__ __forceinline__ C kw_entry(const KwArgs& a, const T* wt, int e, bool sector1) {
-    const int s = a.src[e];
-    const T w = s >= 0 ? wt[s] : (s == -1 ? T(1) : (sector1 ? T(-1) : T(1)));
-    const double2 p = a.ph[e];
-    C v;
-    v.x = -w * (T)p.x;
-    v.y = -w * (T)p.y;
-    return v;
+__device__ __forceinline__ int kw_fetch(const KwArgs& a, const T* wt, int i, int lane, C& v, C& v1) {
+    const int j = a.ecol[i * kKwRowSlots + lane];
+    if (j >= 0) {
+        const int s = a.esrc[i * kKwRowSlots + lane];
+        const double2 p = a.eph[i * kKwRowSlots + lane];
+        const T w = s >= 0 ? wt[s] : T(1);      // -1 and the sector edge in sector 0: weight 1
+        v = C{-w * (T)p.x, -w * (T)p.y};
+        v1 = s == -2 ? C{(T)p.x, (T)p.y} : v;   // the sector edge in sector 1: weight -1
+    }
+    return j;
 }
 
-// Writes band row i (its diagonal and successors) into a zeroed slot.
+// Writes band row i, fetched by kw_fetch on every lane, into a zeroed slot.
 template <typename T, typename C>
-__device__ __forceinline__ void kw_load_row(const KwArgs& a, const T* wt, C* R, int i, int lane) {
-    const int e0 = a.row_start[i], e1 = a.row_start[i + 1];
-    for (int e = e0 + lane; e < e1; e += 32) {
-        const int j = a.col[e];
+__device__ __forceinline__ void kw_place_row(const KwArgs& a, C* R, int i, int j, const C& v, const C& v1,
+                                             int lane) {
+    if (j >= 0) {
         if (j < a.Nb) {
-            R[j % a.WC] = kw_entry<T, C>(a, wt, e, false);
-            if (j >= a.Nb - 2) R[a.WC + 2 + (j - (a.Nb - 2))] = kw_entry<T, C>(a, wt, e, true);
+            R[j % a.WC] = v;
+            if (j >= a.Nb - 2) R[a.WC + 2 + (j - (a.Nb - 2))] = v1;
         } else {
-            R[a.WC + (j - a.Nb)] = kw_entry<T, C>(a, wt, e, false);
+            R[a.WC + (j - a.Nb)] = v;
         }
     }
     if (lane == 0) {
@@ -288,41 +290,52 @@ __device__ __forceinline__ void kw_load_row(const KwArgs& a, const T* wt, C* R, 
     }
 }
 
+template <typename C, typename T>
+__device__ __forceinline__ void kw_axpy(C& r, const C& m, const C& u) {
+    r.x -= m.x * u.x - m.y * u.y;
+    r.y -= m.x * u.y + m.y * u.x;
+}
+
 // ln Z of one part for both sectors (returned on every lane). Weights wt[q]
 // = (-1)^bit * (1 - 2p) for the part's qubits (turned-lattice index).
-template <typename T>
+template <typename T, int NT, int RU>
 __device__ void kw_part(const KwArgs& a, unsigned char* base, double out[2]) {
     using C = typename Cplx<T>::type;
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     const KwLayout L = kw_layout(a.WR, a.RS, a.n, sizeof(C));
     C* A = reinterpret_cast<C*>(base + L.a);
-    C* mult = reinterpret_cast<C*>(base + L.mult);
     const T* wt = reinterpret_cast<const T*>(base + L.wt);
     int* map = reinterpret_cast<int*>(base + L.map);
     int* ext = reinterpret_cast<int*>(base + L.ext);
-    int* act = reinterpret_cast<int*>(base + L.act);
     const int WR = a.WR, WC = a.WC, RS = a.RS, Nb = a.Nb;
+    const C zero = C{T(0), T(0)};
 
-    // initial window: band rows 0..WR-1, columns 0..WC-1, the border rows
-    for (int i = lane; i < (WR + 2) * RS; i += 32) A[i] = C{T(0), T(0)};
+    // initial window: band rows 0..WR-1 (columns 0..WC-1), the border rows
+    for (int i = lane; i < (WR + 2) * RS; i += 32) A[i] = zero;
     for (int r = lane; r < WR; r += 32) map[r] = r;
     __syncwarp();
     const int rows0 = WR < Nb ? WR : Nb;
     for (int i = 0; i < rows0; ++i) {
-        kw_load_row<T, C>(a, wt, A + (size_t)i * RS, i, lane);
+        C v, v1;
+        const int j = kw_fetch<T, C>(a, wt, i, lane, v, v1);
+        kw_place_row<T, C>(a, A + (size_t)i * RS, i, j, v, v1, lane);
         if (lane == 0) ext[i] = a.ext0[i];
     }
+    // border rows: entries in the first WC band columns, the border and the
+    // sector-1 columns now; later band columns when they enter the window
+    // (each lane keeps its entry of both rows)
+    int bj[2];
+    C bv[2];
     for (int t = 0; t < 2; ++t) {
-        const int i = Nb + t;
+        C v1;
+        bj[t] = kw_fetch<T, C>(a, wt, Nb + t, lane, bv[t], v1);
         C* R = A + (size_t)(WR + t) * RS;
-        for (int e = a.row_start[i] + lane; e < a.row_start[i + 1]; e += 32) {
-            const int j = a.col[e];
-            if (j >= Nb) R[WC + (j - Nb)] = kw_entry<T, C>(a, wt, e, false);
-            else {
-                if (j < WC) R[j] = kw_entry<T, C>(a, wt, e, false);
-                if (j >= Nb - 2) R[WC + 2 + (j - (Nb - 2))] = kw_entry<T, C>(a, wt, e, true);
-            }
+        const int j = bj[t];
+        if (j >= Nb) R[WC + (j - Nb)] = bv[t];
+        else if (j >= 0) {
+            if (j < WC) R[j] = bv[t];
+            if (j >= Nb - 2) R[WC + 2 + (j - (Nb - 2))] = v1;
         }
         if (lane == 0) R[WC + t].x += T(1);
     }
@@ -331,40 +344,52 @@ __device__ void kw_part(const KwArgs& a, unsigned char* base, double out[2]) {
     T mant = T(1);
     int expo = 0;
     bool dead = false;
-    int colk = 0;
-    for (int k = 0; k < Nb - 2; ++k, colk = (colk + 1 == WC) ? 0 : colk + 1) {
+    int colk = 0, kmod = 0;    // k mod WC, k mod WR
+    for (int k = 0; k < Nb - 2; ++k) {
         const int kend = (k + a.bl < Nb - 1) ? k + a.bl : Nb - 1;
+        // the row entering at the end of this step: fetched now, placed later
+        const int rin = k + WR;
+        C nv = zero, nv1 = zero;
+        int nj = -1, next = 0;
+        if (rin < Nb) {
+            nj = kw_fetch<T, C>(a, wt, rin, lane, nv, nv1);
+            next = a.ext0[rin];
+        }
         // pivot: the largest |entry| of column k among the band rows k..kend
         T best = T(-1);
-        int bi = k;
-        for (int r = k + lane; r <= kend; r += 32) {
-            const C v = A[(size_t)map[r % WR] * RS + colk];
+        int boff = 0;
+        for (int off = lane; off <= kend - k; off += 32) {
+            int mp = kmod + off;
+            if (mp >= WR) mp -= WR;
+            const C v = A[(size_t)map[mp] * RS + colk];
             const T m2 = v.x * v.x + v.y * v.y;
             if (m2 > best) {
                 best = m2;
-                bi = r;
+                boff = off;
             }
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
             const T ob = __shfl_xor_sync(FULL, best, o);
-            const int oi = __shfl_xor_sync(FULL, bi, o);
-            if (ob > best || (ob == best && oi < bi)) {
+            const int oo = __shfl_xor_sync(FULL, boff, o);
+            if (ob > best || (ob == best && oo < boff)) {
                 best = ob;
-                bi = oi;
+                boff = oo;
             }
         }
         if (!(best > T(0))) {
             dead = true;
             break;
         }
-        if (lane == 0 && bi != k) {
-            const int t0 = map[k % WR];
-            map[k % WR] = map[bi % WR];
-            map[bi % WR] = t0;
+        if (lane == 0 && boff != 0) {
+            int mp = kmod + boff;
+            if (mp >= WR) mp -= WR;
+            const int t0 = map[kmod];
+            map[kmod] = map[mp];
+            map[mp] = t0;
         }
         __syncwarp();
-        const int ps = map[k % WR];
+        const int ps = map[kmod];
         C* P = A + (size_t)ps * RS;
         const C u = P[colk];
         const T inv2 = T(1) / best;
@@ -375,86 +400,116 @@ __device__ void kw_part(const KwArgs& a, unsigned char* base, double out[2]) {
             mant = sizeof(T) == 4 ? (T)frexpf((float)mant, &e) : (T)frexp((double)mant, &e);
             expo += e;
         }
-        // multipliers of the rows below (band rows k+1..kend, then the border rows)
-        const int cnt1 = kend - k, ncand = cnt1 + 2;
-        int nact = 0;
-        for (int base_i = 0; base_i < ncand; base_i += 32) {
-            const int idx = base_i + lane;
-            const bool valid = idx < ncand;
-            const int s = !valid ? 0 : (idx < cnt1 ? map[(k + 1 + idx) % WR] : WR + (idx - cnt1));
-            C v = C{T(0), T(0)};
-            if (valid) v = A[(size_t)s * RS + colk];
-            const bool nz = valid && (v.x != T(0) || v.y != T(0));
-            const unsigned bal = __ballot_sync(FULL, nz);
-            if (nz) {
-                const int slot = nact + __popc(bal & ((1u << lane) - 1u));
-                act[slot] = s;
-                mult[slot] = C{v.x * inv.x - v.y * inv.y, v.x * inv.y + v.y * inv.x};
-                A[(size_t)s * RS + colk] = C{T(0), T(0)};
-            }
-            nact += __popc(bal);
-        }
         const int extp = ext[ps];
-        __syncwarp();
-        // the pivot row's columns k+1..extp (lane-strided) and its four extra columns
-        C U[kKwMaxColsPerLane];
-        int pc[kKwMaxColsPerLane];
+        // multipliers of the rows below (band rows k+1..kend, then the two
+        // border rows): candidate idx = 32 c + lane holds its slot and
+        // multiplier in registers; the ballot marks the nonzero ones
+        const int cnt1 = kend - k, ncand = cnt1 + 2;
+        int sl[kKwMaxChunks];
+        C mv[kKwMaxChunks];
+        unsigned msk[kKwMaxChunks];
 #pragma unroll
-        for (int t = 0; t < kKwMaxColsPerLane; ++t) {
+        for (int c = 0; c < kKwMaxChunks; ++c) {
+            const int idx = 32 * c + lane;
+            int s = 0;
+            C v = zero;
+            if (idx < cnt1) {
+                int mp = kmod + 1 + idx;
+                if (mp >= WR) mp -= WR;
+                s = map[mp];
+            } else if (idx < ncand) {
+                s = WR + (idx - cnt1);
+            }
+            if (idx < ncand) v = A[(size_t)s * RS + colk];
+            const bool nz = v.x != T(0) || v.y != T(0);
+            msk[c] = __ballot_sync(FULL, nz);
+            sl[c] = s;
+            mv[c] = C{v.x * inv.x - v.y * inv.y, v.x * inv.y + v.y * inv.x};
+            if (nz) {
+                A[(size_t)s * RS + colk] = zero;
+                if (s < WR && ext[s] < extp) ext[s] = extp;
+            }
+        }
+        // the pivot row's columns k+1..extp (lane-strided) and its four extra columns
+        C U[NT];
+        int pc[NT];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
             const int c = k + 1 + lane + 32 * t;
             int p = colk + 1 + lane + 32 * t;
             if (p >= WC) p -= WC;
             pc[t] = c <= extp ? p : -1;
-            U[t] = c <= extp ? P[p] : C{T(0), T(0)};
+            U[t] = c <= extp ? P[p] : zero;
         }
-        const C Ux = lane < 4 ? P[WC + lane] : C{T(0), T(0)};
-        for (int q = 0; q < nact; ++q) {
-            const int s = act[q];
-            const C m = mult[q];
-            C* R = A + (size_t)s * RS;
+        const C Ux = lane < 4 ? P[WC + lane] : zero;
+        // rank-one update, RU rows at a time: all loads, then the updates
 #pragma unroll
-            for (int t = 0; t < kKwMaxColsPerLane; ++t) {
-                if (pc[t] >= 0) {
-                    C r = R[pc[t]];
-                    r.x -= m.x * U[t].x - m.y * U[t].y;
-                    r.y -= m.x * U[t].y + m.y * U[t].x;
-                    R[pc[t]] = r;
+        for (int c = 0; c < kKwMaxChunks; ++c) {
+            unsigned mask = msk[c];
+            while (mask) {
+                int s[RU];
+                C m[RU];
+                bool ok[RU];
+#pragma unroll
+                for (int j = 0; j < RU; ++j) {
+                    ok[j] = mask != 0u;
+                    const int src = ok[j] ? __ffs(mask) - 1 : 0;
+                    mask &= mask - 1u;
+                    s[j] = __shfl_sync(FULL, sl[c], src);
+                    m[j].x = __shfl_sync(FULL, mv[c].x, src);
+                    m[j].y = __shfl_sync(FULL, mv[c].y, src);
+                }
+                C r[RU][NT], rx[RU];
+#pragma unroll
+                for (int j = 0; j < RU; ++j) {
+#pragma unroll
+                    for (int t = 0; t < NT; ++t)
+                        if (ok[j] && pc[t] >= 0) r[j][t] = A[(size_t)s[j] * RS + pc[t]];
+                    if (ok[j] && lane < 4) rx[j] = A[(size_t)s[j] * RS + WC + lane];
+                }
+#pragma unroll
+                for (int j = 0; j < RU; ++j) {
+#pragma unroll
+                    for (int t = 0; t < NT; ++t)
+                        if (ok[j] && pc[t] >= 0) {
+                            kw_axpy<C, T>(r[j][t], m[j], U[t]);
+                            A[(size_t)s[j] * RS + pc[t]] = r[j][t];
+                        }
+                    if (ok[j] && lane < 4) {
+                        kw_axpy<C, T>(rx[j], m[j], Ux);
+                        A[(size_t)s[j] * RS + WC + lane] = rx[j];
+                    }
                 }
             }
-            if (lane < 4) {
-                C r = R[WC + lane];
-                r.x -= m.x * Ux.x - m.y * Ux.y;
-                r.y -= m.x * Ux.y + m.y * Ux.x;
-                R[WC + lane] = r;
-            }
-            if (lane == 0 && s < WR && ext[s] < extp) ext[s] = extp;
         }
         __syncwarp();
-        // the pivot row leaves; row k + WR takes its slot; column k + WC enters
-        const int rin = k + WR;
+        // the pivot row leaves; row k + WR takes its slot; column k + WC
+        // enters (its position is colk)
         if (rin < Nb) {
-            for (int i = lane; i < RS; i += 32) P[i] = C{T(0), T(0)};
+            for (int i = lane; i < RS; i += 32) P[i] = zero;
             __syncwarp();
-            kw_load_row<T, C>(a, wt, P, rin, lane);
-            if (lane == 0) ext[ps] = a.ext0[rin];
+            kw_place_row<T, C>(a, P, rin, nj, nv, nv1, lane);
+            if (lane == 0) ext[ps] = next;
         }
         const int jn = k + WC;
-        if (jn < Nb && lane < 2) {
-            const int i = Nb + lane;
-            for (int e = a.row_start[i]; e < a.row_start[i + 1]; ++e)
-                if (a.col[e] == jn) A[(size_t)(WR + lane) * RS + colk] = kw_entry<T, C>(a, wt, e, false);
-        }
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+            if (bj[t] == jn && jn < Nb) A[(size_t)(WR + t) * RS + colk] = bv[t];
         __syncwarp();
+        colk = colk + 1 == WC ? 0 : colk + 1;
+        kmod = kmod + 1 == WR ? 0 : kmod + 1;
     }
 
-    // the last two band rows and the border rows against the sector columns
-    // (regular: sector 0; the carried copies: sector 1) and the border columns
     // ln prod |u_kk|^2 (the mantissa and exponent live on lane 0)
     const double lm = __shfl_sync(FULL, log((double)mant) + (double)expo * 0.69314718055994530942, 0);
+    // the last two band rows and the border rows against the sector columns
+    // (regular: sector 0; the carried copies: sector 1) and the border columns
     double res = -INFINITY;
     if (!dead && lane < 2) {
-        const int rows[4] = {map[(Nb - 2) % WR], map[(Nb - 1) % WR], WR, WR + 1};
-        const int cols[4] = {lane == 0 ? (Nb - 2) % WC : WC + 2, lane == 0 ? (Nb - 1) % WC : WC + 3, WC, WC + 1};
+        int m0 = kmod, m1 = kmod + 1 == WR ? 0 : kmod + 1;   // k = Nb - 2 here
+        const int rows[4] = {map[m0], map[m1], WR, WR + 1};
+        const int cols[4] = {lane == 0 ? colk : WC + 2, lane == 0 ? (colk + 1 == WC ? 0 : colk + 1) : WC + 3, WC,
+                             WC + 1};
         double fr[4][4], fi[4][4];
         for (int r = 0; r < 4; ++r)
             for (int c = 0; c < 4; ++c) {
@@ -463,7 +518,7 @@ __device__ void kw_part(const KwArgs& a, unsigned char* base, double out[2]) {
                 fi[r][c] = (double)v.y;
             }
         double lg = 0.0;
-        for (int c = 0; c < 4 && lg > -INFINITY; ++c) {
+        for (int c = 0; c < 4; ++c) {
             int p = c;
             double bm = -1.0;
             for (int r = c; r < 4; ++r) {
@@ -504,15 +559,15 @@ __device__ void kw_part(const KwArgs& a, unsigned char* base, double out[2]) {
 
 }  // namespace
 }  // namespace mld
-
 namespace mld {
 namespace {
 
 // One warp per syndrome, persistent over the batch: the representative's
 // bits from the destabiliser masks, the X part, the Z part (or the bit-flip
 // rule), then the four classes and the argmax.
-template <typename T>
+template <typename T, int NT>
 __global__ void __launch_bounds__(32) kw_decode_kernel(KwArgs a) {
+    constexpr int RU = sizeof(T) == 4 ? 4 : 2;   // rows per update group
     extern __shared__ __align__(16) unsigned char kw_smem[];
     using C = typename Cplx<T>::type;
     const int lane = threadIdx.x & 31;
@@ -539,7 +594,7 @@ __global__ void __launch_bounds__(32) kw_decode_kernel(KwArgs a) {
         }
         __syncwarp();
         double lx[2], lz[2];
-        kw_part<T>(a, base, lx);
+        kw_part<T, NT, RU>(a, base, lx);
         if (a.pz) {
             __syncwarp();
             for (int qt = lane; qt < n; qt += 32) {
@@ -552,7 +607,7 @@ __global__ void __launch_bounds__(32) kw_decode_kernel(KwArgs a) {
                 wt[qt] = (z ? T(-1) : T(1)) * (T(1) - T(2) * (T)p);
             }
             __syncwarp();
-            kw_part<T>(a, base, lz);
+            kw_part<T, NT, RU>(a, base, lz);
         } else {
             // no Z errors: only the coset holding the identity's z-part has
             // weight, and only if the representative has no z-bits
@@ -584,21 +639,30 @@ mld_status ensure_kw(mld_code* C) {
     if (C->d_kw) return MLD_OK;
     KwGraph g;
     if (!build_kw_graph(C->d, &g)) return MLD_ERR_UNSUPPORTED;
-    if ((g.bl + g.bu + 31) / 32 > kKwMaxColsPerLane) return MLD_ERR_UNSUPPORTED;
-    const int nnz = (int)g.col.size();
+    if ((g.bl + g.bu + 31) / 32 > kKwMaxColsPerLane || (g.bl + 2 + 31) / 32 > kKwMaxChunks)
+        return MLD_ERR_UNSUPPORTED;
+    const int N = g.N, S = kKwRowSlots;
     const std::vector<int> zmap = kw_zmap(C->d);
-    std::vector<int> ints;
-    ints.insert(ints.end(), g.row_start.begin(), g.row_start.end());
-    ints.insert(ints.end(), g.col.begin(), g.col.end());
-    ints.insert(ints.end(), g.src.begin(), g.src.end());
+    // row i's successors padded to S slots: columns (-1 pad), weight sources,
+    // then each band row's last column and the quarter-turn map; the phases
+    // as double pairs after them
+    std::vector<int> ints((size_t)2 * N * S, 0);
+    std::vector<double> ph((size_t)2 * N * S, 0.0);
+    for (int i = 0; i < N; ++i) {
+        const int e0 = g.row_start[i], e1 = g.row_start[i + 1];
+        if (e1 - e0 > S) return MLD_ERR_UNSUPPORTED;
+        for (int t = 0; t < S; ++t) {
+            const int e = e0 + t;
+            ints[(size_t)i * S + t] = e < e1 ? g.col[e] : -1;
+            ints[(size_t)N * S + (size_t)i * S + t] = e < e1 ? g.src[e] : 0;
+            ph[2 * ((size_t)i * S + t)] = e < e1 ? g.ph_re[e] : 0.0;
+            ph[2 * ((size_t)i * S + t) + 1] = e < e1 ? g.ph_im[e] : 0.0;
+        }
+    }
     ints.insert(ints.end(), g.ext0.begin(), g.ext0.end());
     ints.insert(ints.end(), zmap.begin(), zmap.end());
     const size_t ph_off = kw_align(ints.size() * sizeof(int));
-    std::vector<double> ph((size_t)2 * nnz);
-    for (int e = 0; e < nnz; ++e) {
-        ph[2 * (size_t)e] = g.ph_re[e];
-        ph[2 * (size_t)e + 1] = g.ph_im[e];
-    }
+    const int nnz = N * S;
     const size_t bytes = ph_off + ph.size() * sizeof(double);
     void* blob = nullptr;
     if (cudaMalloc(&blob, bytes) != cudaSuccess) return MLD_ERR_NOMEM;
@@ -619,28 +683,41 @@ mld_status ensure_kw(mld_code* C) {
     return MLD_OK;
 }
 
-template <typename T>
-mld_status launch_kw(KwArgs a, cudaStream_t s) {
+template <typename T, int NT>
+mld_status launch_kw_nt(const KwArgs& a, cudaStream_t s) {
     using C = typename Cplx<T>::type;
     const KwLayout L = kw_layout(a.WR, a.RS, a.n, sizeof(C));
-    a.warp_bytes = L.total;
     int dev = 0, sms = 0, smem_max = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return MLD_ERR_CUDA;
     if (L.total > (size_t)smem_max) return MLD_ERR_UNSUPPORTED;
-    if (cudaFuncSetAttribute(kw_decode_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) !=
+    if (cudaFuncSetAttribute(kw_decode_kernel<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) !=
         cudaSuccess)
         return MLD_ERR_CUDA;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kw_decode_kernel<T>, 32, L.total) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kw_decode_kernel<T, NT>, 32, L.total) != cudaSuccess ||
         per_sm < 1)
         return MLD_ERR_UNSUPPORTED;
     int64_t blocks = (int64_t)sms * per_sm;
     if (blocks > a.B) blocks = a.B;
-    kw_decode_kernel<T><<<(unsigned)blocks, 32, L.total, s>>>(a);
+    kw_decode_kernel<T, NT><<<(unsigned)blocks, 32, L.total, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? MLD_OK : MLD_ERR_CUDA;
+}
+
+// Columns of the pivot row per lane: (bl + bu) / 32 rounded up (2 at d <= 9,
+// 3 at d <= 13, 4 at d <= 17, 5 up to d = 25).
+template <typename T>
+mld_status launch_kw(const KwArgs& a, cudaStream_t s) {
+    switch ((a.bl + a.bu + 31) / 32) {
+        case 1:
+        case 2: return launch_kw_nt<T, 2>(a, s);
+        case 3: return launch_kw_nt<T, 3>(a, s);
+        case 4: return launch_kw_nt<T, 4>(a, s);
+        case 5: return launch_kw_nt<T, 5>(a, s);
+    }
+    return MLD_ERR_UNSUPPORTED;
 }
 
 }  // namespace
@@ -660,13 +737,12 @@ extern "C" mld_status mld_decode_xz(const mld_code* Cc, const float* px, const f
     if (st != MLD_OK) return st;
     KwArgs a;
     const int* ib = reinterpret_cast<const int*>(C->d_kw);
-    const int N = C->kw_N, Nb = C->kw_Nb, nnz = C->kw_nnz;
-    a.row_start = ib;
-    a.col = ib + (N + 1);
-    a.src = a.col + nnz;
-    a.ext0 = a.src + nnz;
+    const int N = C->kw_N, Nb = C->kw_Nb, S = kKwRowSlots;
+    a.ecol = ib;
+    a.esrc = ib + (size_t)N * S;
+    a.ext0 = ib + (size_t)2 * N * S;
     a.zmap = a.ext0 + Nb;
-    a.ph = reinterpret_cast<const double2*>(reinterpret_cast<const char*>(C->d_kw) + C->kw_ph_off);
+    a.eph = reinterpret_cast<const double2*>(reinterpret_cast<const char*>(C->d_kw) + C->kw_ph_off);
     a.N = N;
     a.Nb = Nb;
     a.bl = C->kw_bl;
@@ -677,7 +753,6 @@ extern "C" mld_status mld_decode_xz(const mld_code* Cc, const float* px, const f
     a.n = C->n;
     a.words = C->words;
     a.cst = (double)(C->kw_nplaq - C->n) * 0.69314718055994530942;
-    a.warp_bytes = 0;
     a.dmask = C->d_dmask;
     a.px = px;
     a.pz = pz;

@@ -129,6 +129,14 @@ def biased(n: int, p: float, eta: float) -> np.ndarray:
     return t
 
 
+def independent_xz(px, pz) -> np.ndarray:
+    """Independent X and Z flips with per-qubit rates px, pz: the table
+    (1-px)(1-pz), px(1-pz), px pz, (1-px) pz (I, X, Y, Z)."""
+    px = np.asarray(px, dtype=np.float64)
+    pz = np.asarray(pz, dtype=np.float64)
+    return np.stack([(1 - px) * (1 - pz), px * (1 - pz), px * pz, (1 - px) * pz], axis=1)
+
+
 def lognormal_biased(n: int, seed: int, median: float = 0.05, sigma: float = 0.5,
                      eta_lo: float = 1.0, eta_hi: float = 10.0) -> np.ndarray:
     """Per-qubit non-uniform biased noise: p_q = median*exp(sigma*N(0,1)) clipped
