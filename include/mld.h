@@ -367,8 +367,9 @@ mld_status mld_decode_dem(const mld_code* code, const int32_t* mech_qubit, const
  *   argmax     device uint8[B] or NULL (ties -> lowest class)
  * Exact in exact arithmetic at any odd d >= 3 up to 25. Each part is one
  * banded elimination with partial pivoting (order 2|E| = 2d^2 + O(d),
- * bandwidth 3d), one warp per syndrome, the two sectors sharing all but a
- * final 4 x 4 determinant. The determinant is a sum of signed terms: a class
+ * bandwidth 3d), one warp per syndrome up to d = 13 and one block of four
+ * warps per syndrome above, the two sectors sharing all but a final 4 x 4
+ * determinant. The determinant is a sum of signed terms: a class
  * far less likely than the leading one carries an error of order
  * eps * cond relative to the leading class's Z, while the leading class's
  * ln Z and the decision keep the arithmetic's accuracy. A probability
@@ -376,8 +377,9 @@ mld_status mld_decode_dem(const mld_code* code, const int32_t* mech_qubit, const
  * (mld_decode_status); a vanishing pivot sets MLD_ERR_NUMERIC and gives -inf.
  * The first call for a code builds the graph and copies it to the device
  * (synchronous, a few hundred KB); later calls are asynchronous on stream
- * with no allocation. MLD_ERR_UNSUPPORTED if a warp's window exceeds the
- * device's shared memory per block (FP64 at d = 25 does not fit). */
+ * with no allocation. MLD_ERR_UNSUPPORTED if a syndrome's window exceeds
+ * the device's shared memory per block (it fits up to d = 25 in FP64 on
+ * GB300: 200 KB). */
 mld_status mld_decode_xz(const mld_code* code, const float* px, const float* pz, const uint64_t* syndromes,
                          int64_t B, int precision, double* logP, uint8_t* argmax, void* stream);
 
