@@ -246,10 +246,10 @@ constexpr int kKwWarps = 4;
 // then the two border rows; each RS entries: WC band columns by column index
 // mod WC, the two border columns, the two sector-1 columns), the step's
 // active rows and multipliers, the weights of the current part, the row map
-// (logical row mod WR -> slot), each slot's last nonzero band column, and a
-// few control words.
+// (logical row mod WR -> slot), each slot's last nonzero band column, a few
+// control words and a copy of the step's pivot row.
 struct KwLayout {
-    size_t a, mult, wt, map, ext, act, ctl, total;
+    size_t a, mult, wt, map, ext, act, ctl, piv, total;
 };
 
 __host__ __device__ inline size_t kw_align(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -263,7 +263,8 @@ __host__ __device__ inline KwLayout kw_layout(int WR, int RS, int n, size_t cbyt
     L.ext = kw_align(L.map + (size_t)WR * 4);
     L.act = kw_align(L.ext + (size_t)(WR + 2) * 4);
     L.ctl = kw_align(L.act + (size_t)(WR + 2) * 4);
-    L.total = kw_align(L.ctl + 64);
+    L.piv = kw_align(L.ctl + 64);                          // a copy of the pivot row (block kernel)
+    L.total = kw_align(L.piv + (size_t)RS * cbytes);
     return L;
 }
 
@@ -653,6 +654,7 @@ __device__ __forceinline__ void kw_part_block(const KwArgs& a, unsigned char* ba
     int* act = reinterpret_cast<int*>(base + L.act);
     int* ctl = reinterpret_cast<int*>(base + L.ctl);          // [0] pivot slot, [1] its last column, [2] active rows, [3] dead
     double* res2 = reinterpret_cast<double*>(base + L.ctl + 32);
+    C* piv = reinterpret_cast<C*>(base + L.piv);
     const int WR = a.WR, WC = a.WC, RS = a.RS, Nb = a.Nb;
     const C zero = C{T(0), T(0)};
 
@@ -668,12 +670,12 @@ __device__ __forceinline__ void kw_part_block(const KwArgs& a, unsigned char* ba
         kw_place_row<T, C>(a, A + (size_t)i * RS, i, j, v, v1, lane);
         if (lane == 0) ext[i] = a.ext0[i];
     }
-    // border rows (warp 0): entries in the first WC band columns, the border
-    // and the sector-1 columns now; later band columns when they enter the
-    // window (each lane of warp 0 keeps its entry of both rows)
+    // border rows (warp W-1): entries in the first WC band columns, the
+    // border and the sector-1 columns now; later band columns when they enter
+    // the window (each lane of warp W-1 keeps its entry of both rows)
     int bj[2] = {-1, -1};
     C bv[2] = {zero, zero};
-    if (warp == 0) {
+    if (warp == W - 1) {
         for (int t = 0; t < 2; ++t) {
             C v1;
             bj[t] = kw_fetch<T, C>(a, wt, Nb + t, lane, bv[t], v1);
@@ -693,17 +695,20 @@ __device__ __forceinline__ void kw_part_block(const KwArgs& a, unsigned char* ba
     int expo = 0;
     bool dead = false;
     int colk = 0, kmod = 0;    // k mod WC, k mod WR
-    // the row entering at the end of a step (warp 0): fetched at its top
+    // the row entering during a step (warp W-1): fetched at its top while
+    // warp 0 takes the pivot, placed while the others update
     C nv = zero, nv1 = zero;
     int nj = -1, next = 0;
     for (int k = 0; k < Nb - 2; ++k) {
         const int rin = k + WR;
-        if (warp == 0) {
+        if (warp == W - 1) {
             nj = -1;
             if (rin < Nb) {
                 nj = kw_fetch<T, C>(a, wt, rin, lane, nv, nv1);
                 next = a.ext0[rin];
             }
+        }
+        if (warp == 0) {
             const int kend = (k + a.bl < Nb - 1) ? k + a.bl : Nb - 1;
             // pivot: the largest |entry| of column k among the band rows k..kend
             T best = T(-1);
@@ -776,6 +781,10 @@ __device__ __forceinline__ void kw_part_block(const KwArgs& a, unsigned char* ba
                     }
                     nact += __popc(bal);
                 }
+                // the pivot row's copy, so that its slot can take the entering
+                // row during the update
+                const C* P = A + (size_t)ps * RS;
+                for (int i = lane; i < RS; i += 32) piv[i] = P[i];
                 if (lane == 0) {
                     ctl[0] = ps;
                     ctl[1] = extp;
@@ -793,7 +802,22 @@ __device__ __forceinline__ void kw_part_block(const KwArgs& a, unsigned char* ba
         // row (lane-strided) and its four extra columns
         {
             const int ps = ctl[0], extp = ctl[1], nact = ctl[2];
-            const C* P = A + (size_t)ps * RS;
+            if (warp == W - 1) {
+                // the pivot row leaves: row k + WR takes its slot; column
+                // k + WC enters (its position is colk)
+                C* R = A + (size_t)ps * RS;
+                if (rin < Nb) {
+                    for (int i = lane; i < RS; i += 32) R[i] = zero;
+                    __syncwarp();
+                    kw_place_row<T, C>(a, R, rin, nj, nv, nv1, lane);
+                    if (lane == 0) ext[ps] = next;
+                }
+                const int jn = k + WC;
+#pragma unroll
+                for (int t = 0; t < 2; ++t)
+                    if (bj[t] == jn && jn < Nb) A[(size_t)(WR + t) * RS + colk] = bv[t];
+            }
+            const C* P = piv;
             C U[NT];
             int pc[NT];
 #pragma unroll
@@ -839,24 +863,6 @@ __device__ __forceinline__ void kw_part_block(const KwArgs& a, unsigned char* ba
             }
         }
         __syncthreads();
-        // warp 0: the pivot row leaves, row k + WR takes its slot; column
-        // k + WC enters (its position is colk). The other warps go on to the
-        // next step's barrier, which warp 0 reaches after the next pivot.
-        if (warp == 0) {
-            const int ps = ctl[0];
-            C* P = A + (size_t)ps * RS;
-            if (rin < Nb) {
-                for (int i = lane; i < RS; i += 32) P[i] = zero;
-                __syncwarp();
-                kw_place_row<T, C>(a, P, rin, nj, nv, nv1, lane);
-                if (lane == 0) ext[ps] = next;
-            }
-            const int jn = k + WC;
-#pragma unroll
-            for (int t = 0; t < 2; ++t)
-                if (bj[t] == jn && jn < Nb) A[(size_t)(WR + t) * RS + colk] = bv[t];
-            __syncwarp();
-        }
         colk = colk + 1 == WC ? 0 : colk + 1;
         kmod = kmod + 1 == WR ? 0 : kmod + 1;
     }
