@@ -675,6 +675,58 @@ def run_kw(args):
     print(json.dumps(line), flush=True)
 
 
+def run_kw_threshold(args):
+    """Logical-error rates under bit-flip noise (independent X flips with
+    probability p on every qubit, no Z errors) decoded exactly by the Kac-Ward
+    path, for d in --kw-d and p on a grid around the optimal threshold the
+    paper quotes for this channel (10.9%, the random-bond Ising model on the
+    Nishimori line; Sec. 3.1.2). Per point --kw-batch syndromes (default
+    16,384, seed config_seed(8, d, p)), the LER with its Wilson interval, and
+    the crossing of each pair of consecutive distances (linear interpolation
+    of the LER difference between grid points)."""
+    import torch
+    import paper_2605_17230_gb300 as mld
+
+    ps = args.kw_threshold_p
+    Bd = args.kw_batch or 16384
+    rows, ler = [], {}
+    for d in args.kw_d:
+        n = d * d
+        code = mld.Code(d)
+        for p in ps:
+            px = np.full(n, p, np.float32)
+            tab = synth.independent_xz(px, np.zeros(n))
+            E = synth.sample_errors(d, tab, Bd, seed=synth.config_seed(8, d, p))
+            true = synth.true_class(d, E)
+            sy = torch.tensor(synth.syndromes_of(d, E).view(np.int64), device="cuda")
+            t0 = time.time()
+            _, am = code.decode_xz(torch.tensor(px, device="cuda"), None, sy, mld.MLD_FP32)
+            torch.cuda.synchronize()
+            dt = time.time() - t0
+            if code.status() != 0:
+                raise RuntimeError("device status after the Kac-Ward decode")
+            k = int((am.cpu().numpy() != true).sum())
+            lo, hi = wilson_interval(k, Bd)
+            ler[(d, p)] = k / Bd
+            rows.append({"d": d, "p": p, "syndromes": Bd, "logical_error_rate": k / Bd, "ci95": [lo, hi],
+                         "seconds": dt})
+        code.close()
+    cross = []
+    ds = list(args.kw_d)
+    for d1, d2 in zip(ds, ds[1:]):
+        diff = [ler[(d2, p)] - ler[(d1, p)] for p in ps]
+        pc = None
+        for i in range(len(ps) - 1):
+            if diff[i] < 0 <= diff[i + 1]:
+                pc = ps[i] + (ps[i + 1] - ps[i]) * (-diff[i]) / (diff[i + 1] - diff[i])
+                break
+        cross.append({"d": [d1, d2], "p_cross": pc})
+    line = {"metric": "logical-error rate under bit-flip noise, exact MLD (Kac-Ward)", "workload": "kw-threshold",
+            "unit": "logical errors per syndrome", "data": "synthetic", "dtype": "complex f32 elimination, f64 ln Z",
+            "paper_threshold": 0.109, "rows": rows, "crossings": cross}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -686,18 +738,22 @@ def main():
     ap.add_argument("--batch", type=int, default=B, help="syndromes per GPU per step (default: the "
                     "65536 of the workload; smaller values only for profiling captures)")
     ap.add_argument("--workload", default="metric",
-                    choices=["metric", "mixed", "grad", "large", "ler", "dmle", "dem", "point", "kw"],
+                    choices=["metric", "mixed", "grad", "large", "ler", "dmle", "dem", "point", "kw",
+                             "kw-threshold"],
                     help="metric: the headline d=9 line (default); mixed: the 1,048,576-syndrome mixed-d "
                          "graph batch; grad: the adjoint on the d=7 workload; dmle: full-batch noise "
                          "estimation from 1,048,576 unlabelled d=9 syndromes; dem: detector-picture decode of "
                          "a d=9 X/Y/Z mechanism model; large: d=17, 25 at chi 32..128 (truncating); "
                          "ler: logical-error rates of the d/p grid against the oracle; point: one (d, chi, p) "
                          "decode point, FP32 and mixed; kw: the Kac-Ward decode under independent X/Z "
-                         "noise against the boundary-MPS decode of the same syndromes")
+                         "noise against the boundary-MPS decode of the same syndromes; kw-threshold: "
+                         "logical-error rates under bit-flip noise around the 10.9% threshold, exact")
     ap.add_argument("--kw-d", type=int, nargs="+", default=[9, 13, 17, 25], help="kw: distances")
     ap.add_argument("--kw-p", type=float, default=0.10, help="kw: X and Z flip rate per qubit")
     ap.add_argument("--kw-batch", type=int, default=0, help="kw: syndromes per decode (0: by d)")
     ap.add_argument("--kw-no-mps", action="store_true", help="kw: skip the boundary-MPS comparison")
+    ap.add_argument("--kw-threshold-p", type=float, nargs="+",
+                    default=[0.095, 0.100, 0.105, 0.110, 0.115, 0.120], help="kw-threshold: bit-flip rates")
     ap.add_argument("--large-batch", type=int, default=16384)
     ap.add_argument("--large-d", type=int, nargs="+", default=[17, 25], help="large: distances")
     ap.add_argument("--large-chi", type=int, nargs="+", default=[32, 64, 128],
@@ -731,6 +787,8 @@ def main():
         return run_ler(args) if rank == 0 else None
     if args.workload == "kw":
         return run_kw(args) if rank == 0 else None
+    if args.workload == "kw-threshold":
+        return run_kw_threshold(args) if rank == 0 else None
     if args.workload == "point":
         return run_point(args) if rank == 0 else None
 
