@@ -625,10 +625,12 @@ def run_kw(args):
     import torch
     import paper_2605_17230_gb300 as mld
 
-    def timed(fn, steps):
+    def timed(fn, steps, before=None):
         for _ in range(max(1, args.warmup)):
             fn()
         torch.cuda.synchronize()
+        if before is not None:
+            before()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(steps):
@@ -638,6 +640,7 @@ def run_kw(args):
         return e0.elapsed_time(e1) / steps, out
 
     default_b = {5: 65536, 7: 65536, 9: 65536, 11: 32768, 13: 32768, 15: 16384, 17: 16384}
+    peak, sms = mld.mld_measure_fp32_peak(2.0)
     rows = []
     for d in args.kw_d:
         n, p = d * d, args.kw_p
@@ -649,7 +652,9 @@ def run_kw(args):
         sy = torch.tensor(synth.syndromes_of(d, E).view(np.int64), device="cuda")
         code = mld.Code(d)
         dpx = torch.tensor(px, device="cuda")
-        ms32, (lp, am) = timed(lambda: code.decode_xz(dpx, dpx, sy, mld.MLD_FP32), args.steps)
+        ms32, (lp, am) = timed(lambda: code.decode_xz(dpx, dpx, sy, mld.MLD_FP32), args.steps,
+                               before=code.xz_executed_flops)
+        flops = code.xz_executed_flops() / (args.steps * Bd)
         B64 = max(1, Bd // 4)
         ms64, (lp64, am64) = timed(lambda: code.decode_xz(dpx, dpx, sy[:B64], mld.MLD_FP64),
                                    max(1, args.steps // 5))
@@ -658,7 +663,10 @@ def run_kw(args):
         row = {"d": d, "p": p, "syndromes": Bd, "fp32_value": Bd / (ms32 / 1e3), "fp32_ms": ms32,
                "fp64_value": B64 / (ms64 / 1e3), "fp64_syndromes": B64,
                "logical_error_rate": float((am.long() != true).float().mean().item()),
-               "fp32_fp64_decisions_differ": int((am[:B64] != am64).sum().item())}
+               "fp32_fp64_decisions_differ": int((am[:B64] != am64).sum().item()),
+               "executed_flops_per_syndrome": flops,
+               "roofline": {"bound": "alu", "achieved": flops * Bd / (ms32 / 1e3) / 1e12, "peak": peak,
+                            "unit": "TFLOP/s", "frac": flops * Bd / (ms32 / 1e3) / 1e12 / peak, "traffic": None}}
         if not args.kw_no_mps:
             chi = 1 << (d // 2) if d <= 13 else 32
             nz = torch.tensor(tab.astype(np.float32), device="cuda")
@@ -671,7 +679,10 @@ def run_kw(args):
         code.close()
     line = {"metric": "syndromes/s of the Kac-Ward decode (independent X/Z noise, 4 classes)", "workload": "kw",
             "unit": "syndromes/s", "data": "synthetic", "dtype": "complex f32 elimination, f64 ln Z",
-            "steps": args.steps, "warmup": args.warmup, "rows": rows}
+            "steps": args.steps, "warmup": args.warmup, "rows": rows,
+            "roofline_note": f"achieved = flops executed by the FP32 elimination (counted on the device: 6 per "
+                             f"multiplier, 8 per complex multiply-subtract of an updated column) / kernel time; peak = "
+                             f"FFMA microbenchmark on {sms} SMs (mld_measure_fp32_peak, 2 s)"}
     print(json.dumps(line), flush=True)
 
 

@@ -383,6 +383,13 @@ mld_status mld_decode_dem(const mld_code* code, const int32_t* mech_qubit, const
 mld_status mld_decode_xz(const mld_code* code, const float* px, const float* pz, const uint64_t* syndromes,
                          int64_t B, int precision, double* logP, uint8_t* argmax, void* stream);
 
+/* Floating-point operations executed by mld_decode_xz on this code since the
+ * last call (per elimination step: a complex multiplier, 6 flops, and a
+ * complex multiply-subtract, 8 flops, per updated column of every row with a
+ * nonzero multiplier, counted on the device from the step's actual extent),
+ * then reset to zero. The caller synchronises the decode streams first. */
+mld_status mld_decode_xz_executed_flops(const mld_code* code, double* flops);
+
 /* Measurement helper (not part of the method): times a kernel of independent
  * FP32 FMA chains on every SM of the current device for about `seconds` and
  * returns the sustained rate in TFLOP/s (2 flops per FMA) and the SM count,

@@ -37,7 +37,8 @@ EXPORTED_SYMBOLS = ["mld_code_create_rotated", "mld_code_destroy", "mld_code_inf
                     "mld_decode_dem", "mld_status_string", "mld_code_set_svd_cutoff",
                     "mld_decode_executed_flops", "mld_decode_bond_histogram", "mld_measure_fp32_peak",
                     "mld_code_set_truncation_kernel", "mld_code_set_exact_kernel",
-                    "mld_code_set_truncation_workspace", "mld_decode_xz"]
+                    "mld_code_set_truncation_workspace", "mld_decode_xz",
+                    "mld_decode_xz_executed_flops"]
 
 _lib = None
 
@@ -107,6 +108,8 @@ def load(build_if_missing: bool = True):
     lib.mld_decode_dem.restype = I
     lib.mld_decode_xz.argtypes = [P, P, P, P, L, I, P, P, P]
     lib.mld_decode_xz.restype = I
+    lib.mld_decode_xz_executed_flops.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+    lib.mld_decode_xz_executed_flops.restype = I
     lib.mld_code_set_svd_cutoff.argtypes = [P, ctypes.c_double]
     lib.mld_code_set_svd_cutoff.restype = I
     lib.mld_decode_executed_flops.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
@@ -284,6 +287,13 @@ class Code:
         mld_decode_xz(self.handle, px.contiguous(), None if pz is None else pz.contiguous(), syndromes.contiguous(),
                       B, precision, logP, am, stream)
         return logP, am
+
+    def xz_executed_flops(self) -> float:
+        """Flops executed by decode_xz since the last call (then reset)."""
+        v = ctypes.c_double()
+        _check(load().mld_decode_xz_executed_flops(ctypes.c_void_p(self.handle), ctypes.byref(v)),
+               "mld_decode_xz_executed_flops")
+        return v.value
 
     def flops(self, chi, precision=MLD_FP32) -> float:
         """Counted flops per syndrome (four classes) of the executed schedule."""

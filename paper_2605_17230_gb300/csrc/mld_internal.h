@@ -63,10 +63,12 @@ struct mld_code {
     // Kac-Ward solver (mld_decode_xz): one device block holding the ordered
     // matrix of the spin graph (CSR row starts, columns, weight sources, each
     // band row's last column, the quarter-turn qubit map; then the phases as
-    // double pairs at kw_ph_off), built on first use, and its sizes
+    // double pairs at kw_ph_off; an executed-flop counter at kw_cnt_off),
+    // built on first use, and its sizes
     void* d_kw = nullptr;
     int kw_N = 0, kw_Nb = 0, kw_bl = 0, kw_bu = 0, kw_nplaq = 0, kw_nnz = 0;
     size_t kw_ph_off = 0;
+    size_t kw_cnt_off = 0;               // executed-flop counter (double) in the same block
 };
 
 namespace mld {

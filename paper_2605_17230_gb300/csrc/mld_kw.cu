@@ -236,6 +236,7 @@ struct KwArgs {
     double* logP;
     uint8_t* argmax;
     int* status;
+    double* flops;      // executed-flop counter (one atomic add per part)
 };
 
 // Warps per syndrome window: warp 0 takes the pivot, the multipliers and the
@@ -352,6 +353,7 @@ __device__ __forceinline__ void kw_part_warp(const KwArgs& a, unsigned char* bas
     }
     __syncwarp();
 
+    double work = 0.0;   // executed flops (lane 0)
     T mant = T(1);
     int expo = 0;
     bool dead = false;
@@ -440,6 +442,14 @@ __device__ __forceinline__ void kw_part_warp(const KwArgs& a, unsigned char* bas
                 A[(size_t)s * RS + colk] = zero;
                 if (s < WR && ext[s] < extp) ext[s] = extp;
             }
+        }
+        if (lane == 0) {
+            int na = 0;
+#pragma unroll
+            for (int c = 0; c < kKwMaxChunks; ++c) na += __popc(msk[c]);
+            // per active row: a complex multiplier (6 flops) and a complex
+            // multiply-subtract (8 flops) per updated column
+            work += (double)na * (6.0 + 8.0 * (double)(extp - k + 4));
         }
         // the pivot row's columns k+1..extp (lane-strided) and its four extra columns
         C U[NT];
@@ -565,6 +575,7 @@ __device__ __forceinline__ void kw_part_warp(const KwArgs& a, unsigned char* bas
     }
     out[0] = __shfl_sync(FULL, res, 0);
     out[1] = __shfl_sync(FULL, res, 1);
+    if (lane == 0 && a.flops) atomicAdd(a.flops, work);
     if (dead && lane == 0) atomicOr(a.status, 1 << MLD_ERR_NUMERIC);
 }
 
@@ -691,6 +702,7 @@ __device__ __forceinline__ void kw_part_block(const KwArgs& a, unsigned char* ba
     }
     __syncthreads();
 
+    double work = 0.0;   // executed flops (warp 0, lane 0)
     T mant = T(1);
     int expo = 0;
     bool dead = false;
@@ -789,6 +801,7 @@ __device__ __forceinline__ void kw_part_block(const KwArgs& a, unsigned char* ba
                     ctl[0] = ps;
                     ctl[1] = extp;
                     ctl[2] = nact;
+                    work += (double)nact * (6.0 + 8.0 * (double)(extp - k + 4));
                 }
             }
         }
@@ -922,6 +935,7 @@ __device__ __forceinline__ void kw_part_block(const KwArgs& a, unsigned char* ba
         }
         if (lane < 2) res2[lane] = res;
         if (dead && lane == 0) atomicOr(a.status, 1 << MLD_ERR_NUMERIC);
+        if (lane == 0 && a.flops) atomicAdd(a.flops, work);
     }
     __syncthreads();
     out[0] = res2[0];
@@ -1026,7 +1040,8 @@ mld_status ensure_kw(mld_code* C) {
     ints.insert(ints.end(), zmap.begin(), zmap.end());
     const size_t ph_off = kw_align(ints.size() * sizeof(int));
     const int nnz = N * S;
-    const size_t bytes = ph_off + ph.size() * sizeof(double);
+    const size_t cnt_off = kw_align(ph_off + ph.size() * sizeof(double));
+    const size_t bytes = cnt_off + 16;
     void* blob = nullptr;
     if (cudaMalloc(&blob, bytes) != cudaSuccess) return MLD_ERR_NOMEM;
     if (cudaMemcpy(blob, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -1035,6 +1050,11 @@ mld_status ensure_kw(mld_code* C) {
         cudaFree(blob);
         return MLD_ERR_CUDA;
     }
+    if (cudaMemset((char*)blob + cnt_off, 0, 16) != cudaSuccess) {
+        cudaFree(blob);
+        return MLD_ERR_CUDA;
+    }
+    C->kw_cnt_off = cnt_off;
     C->kw_N = g.N;
     C->kw_Nb = g.Nb;
     C->kw_bl = g.bl;
@@ -1133,6 +1153,18 @@ extern "C" mld_status mld_decode_xz(const mld_code* Cc, const float* px, const f
     a.logP = logP;
     a.argmax = argmax;
     a.status = C->d_status;
+    a.flops = reinterpret_cast<double*>(reinterpret_cast<char*>(C->d_kw) + C->kw_cnt_off);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     return precision == MLD_FP64 ? launch_kw<double>(a, s) : launch_kw<float>(a, s);
+}
+
+extern "C" mld_status mld_decode_xz_executed_flops(const mld_code* Cc, double* out) {
+    mld_code* C = const_cast<mld_code*>(Cc);
+    if (!C || !out) return MLD_ERR_INVALID_ARG;
+    *out = 0.0;
+    if (!C->d_kw) return MLD_OK;
+    char* cnt = static_cast<char*>(C->d_kw) + C->kw_cnt_off;
+    if (cudaMemcpy(out, cnt, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return MLD_ERR_CUDA;
+    if (cudaMemset(cnt, 0, sizeof(double)) != cudaSuccess) return MLD_ERR_CUDA;
+    return MLD_OK;
 }

@@ -201,3 +201,23 @@ def test_ln_z_sums_to_syndrome_probability(mld):
     lp, _ = _run(mld, code, px, pz, syn, mld.MLD_FP64)
     assert abs(np.exp(lp).sum() - 1.0) < 1e-9
     assert math.isfinite(lp.max())
+
+
+def test_executed_flop_counter(mld):
+    """The device counter of the elimination's work: positive after a decode,
+    within the bound of a full window at every step (both parts), and reset by
+    the read."""
+    d, B = 9, 64
+    n = d * d
+    px, pz = _rates(d, 5, 0.05, 0.15)
+    tab = okw.xz_table(px.astype(np.float64), pz.astype(np.float64))
+    syn = synth.syndromes_of(d, synth.sample_errors(d, tab, B, seed=2))
+    code = mld.Code(d)
+    _run(mld, code, px, pz, syn, mld.MLD_FP32)      # builds the tables
+    code.xz_executed_flops()
+    _run(mld, code, px, pz, syn, mld.MLD_FP32)
+    f = code.xz_executed_flops() / B
+    # matrix order 2|E| = 184 at d = 9, band 27 / 26: per step at most 29 rows
+    # times (6 + 8 * (27 + 26 + 4)) flops, two parts
+    assert 0 < f <= 2 * 184 * 29 * (6 + 8 * 57)
+    assert code.xz_executed_flops() == 0.0
