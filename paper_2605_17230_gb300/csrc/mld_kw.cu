@@ -353,7 +353,7 @@ __device__ __forceinline__ void kw_part_warp(const KwArgs& a, unsigned char* bas
     }
     __syncwarp();
 
-    double work = 0.0;   // executed flops (lane 0)
+    long long rows_done = 0, cols_done = 0;   // multipliers and updated row-columns (lane 0)
     T mant = T(1);
     int expo = 0;
     bool dead = false;
@@ -447,9 +447,8 @@ __device__ __forceinline__ void kw_part_warp(const KwArgs& a, unsigned char* bas
             int na = 0;
 #pragma unroll
             for (int c = 0; c < kKwMaxChunks; ++c) na += __popc(msk[c]);
-            // per active row: a complex multiplier (6 flops) and a complex
-            // multiply-subtract (8 flops) per updated column
-            work += (double)na * (6.0 + 8.0 * (double)(extp - k + 4));
+            rows_done += na;
+            cols_done += (long long)na * (extp - k + 4);
         }
         // the pivot row's columns k+1..extp (lane-strided) and its four extra columns
         C U[NT];
@@ -575,7 +574,9 @@ __device__ __forceinline__ void kw_part_warp(const KwArgs& a, unsigned char* bas
     }
     out[0] = __shfl_sync(FULL, res, 0);
     out[1] = __shfl_sync(FULL, res, 1);
-    if (lane == 0 && a.flops) atomicAdd(a.flops, work);
+    // per active row a complex multiplier (6 flops), per updated column a
+    // complex multiply-subtract (8 flops)
+    if (lane == 0 && a.flops) atomicAdd(a.flops, 6.0 * (double)rows_done + 8.0 * (double)cols_done);
     if (dead && lane == 0) atomicOr(a.status, 1 << MLD_ERR_NUMERIC);
 }
 
@@ -702,7 +703,7 @@ __device__ __forceinline__ void kw_part_block(const KwArgs& a, unsigned char* ba
     }
     __syncthreads();
 
-    double work = 0.0;   // executed flops (warp 0, lane 0)
+    long long rows_done = 0, cols_done = 0;   // multipliers and updated row-columns (warp 0, lane 0)
     T mant = T(1);
     int expo = 0;
     bool dead = false;
@@ -801,7 +802,8 @@ __device__ __forceinline__ void kw_part_block(const KwArgs& a, unsigned char* ba
                     ctl[0] = ps;
                     ctl[1] = extp;
                     ctl[2] = nact;
-                    work += (double)nact * (6.0 + 8.0 * (double)(extp - k + 4));
+                    rows_done += nact;
+                    cols_done += (long long)nact * (extp - k + 4);
                 }
             }
         }
@@ -935,7 +937,9 @@ __device__ __forceinline__ void kw_part_block(const KwArgs& a, unsigned char* ba
         }
         if (lane < 2) res2[lane] = res;
         if (dead && lane == 0) atomicOr(a.status, 1 << MLD_ERR_NUMERIC);
-        if (lane == 0 && a.flops) atomicAdd(a.flops, work);
+        // per active row a complex multiplier (6 flops), per updated column a
+    // complex multiply-subtract (8 flops)
+    if (lane == 0 && a.flops) atomicAdd(a.flops, 6.0 * (double)rows_done + 8.0 * (double)cols_done);
     }
     __syncthreads();
     out[0] = res2[0];
