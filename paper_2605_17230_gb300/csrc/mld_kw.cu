@@ -18,9 +18,10 @@
 // their midpoint, I - Lambda is banded (bandwidth about 3d) apart from the tie
 // path's middle edge, which is ordered last as a two-row, two-column border,
 // and the sector edge's two columns are the last two of the band. One warp
-// (d <= 13) or one block of four warps (d >= 15: warp 0 takes the pivot, the
-// multipliers and the entering row, all four share the rank-one update)
-// eliminates one matrix with partial pivoting, streaming: only the rows and
+// (d <= 13) or one block of four warps (d >= 15, with look-ahead: while warps
+// 1-3 apply step k to columns k+2.., warp 0 applies it to column k+1, places
+// the entering row and takes step k+1's pivot and multipliers) eliminates
+// one matrix with partial pivoting, streaming: only the rows and
 // columns of the current band window are in shared memory (rows enter as the
 // elimination reaches them; a row leaves when it has been the pivot). The
 // border columns and a second copy of the two sector columns (their sector-1
@@ -239,18 +240,16 @@ struct KwArgs {
     double* flops;      // executed-flop counter (one atomic add per part)
 };
 
-// Warps per syndrome window: warp 0 takes the pivot, the multipliers and the
-// entering row; all of them share the rank-one update.
+// Warps per syndrome window of the look-ahead block kernel.
 constexpr int kKwWarps = 4;
 
-// Shared memory per block (one syndrome): the window rows (WR band slots,
-// then the two border rows; each RS entries: WC band columns by column index
-// mod WC, the two border columns, the two sector-1 columns), the step's
-// active rows and multipliers, the weights of the current part, the row map
-// (logical row mod WR -> slot), each slot's last nonzero band column, a few
-// control words and a copy of the step's pivot row.
+// Shared memory of the one-warp kernel: the window rows (WR band slots, then
+// the two border rows; each RS entries: WC band columns by column index mod
+// WC, the two border columns, the two sector-1 columns), the weights of the
+// current part, the row map (logical row mod WR -> slot) and each slot's last
+// nonzero band column.
 struct KwLayout {
-    size_t a, mult, wt, map, ext, act, ctl, piv, total;
+    size_t a, wt, map, ext, total;
 };
 
 __host__ __device__ inline size_t kw_align(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -258,14 +257,10 @@ __host__ __device__ inline size_t kw_align(size_t x) { return (x + 15) & ~(size_
 __host__ __device__ inline KwLayout kw_layout(int WR, int RS, int n, size_t cbytes) {
     KwLayout L;
     L.a = 0;
-    L.mult = kw_align(L.a + (size_t)(WR + 2) * RS * cbytes);
-    L.wt = kw_align(L.mult + (size_t)(WR + 2) * cbytes);
+    L.wt = kw_align(L.a + (size_t)(WR + 2) * RS * cbytes);
     L.map = kw_align(L.wt + (size_t)n * (cbytes / 2));
     L.ext = kw_align(L.map + (size_t)WR * 4);
-    L.act = kw_align(L.ext + (size_t)(WR + 2) * 4);
-    L.ctl = kw_align(L.act + (size_t)(WR + 2) * 4);
-    L.piv = kw_align(L.ctl + 64);                          // a copy of the pivot row (block kernel)
-    L.total = kw_align(L.piv + (size_t)RS * cbytes);
+    L.total = kw_align(L.ext + (size_t)(WR + 2) * 4);
     return L;
 }
 
@@ -649,31 +644,189 @@ __global__ void __launch_bounds__(32) kw_decode_warp_kernel(KwArgs a) {
     }
 }
 
-// ln Z of one part for both sectors (returned to every thread of the block).
-// Weights wt[q] = (-1)^bit * (1 - 2p) for the part's qubits (turned-lattice
-// index) are in shared memory. W warps per block, RU rows per update group.
-template <typename T, int NT, int RU, int W>
-__device__ __forceinline__ void kw_part_block(const KwArgs& a, unsigned char* base, double out[2]) {
+// ln|det| of the 4 x 4 complex matrix A[rows[r] * RS + cols[c]], in FP64
+// with partial pivoting (-inf if it is singular).
+template <typename C>
+__device__ __forceinline__ double kw_logdet4(const C* A, int RS, const int rows[4], const int cols[4]) {
+    double fr[4][4], fi[4][4];
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+            const C v = A[(size_t)rows[r] * RS + cols[c]];
+            fr[r][c] = (double)v.x;
+            fi[r][c] = (double)v.y;
+        }
+    double lg = 0.0;
+    for (int c = 0; c < 4; ++c) {
+        int p = c;
+        double bm = -1.0;
+        for (int r = c; r < 4; ++r) {
+            const double m2 = fr[r][c] * fr[r][c] + fi[r][c] * fi[r][c];
+            if (m2 > bm) {
+                bm = m2;
+                p = r;
+            }
+        }
+        if (!(bm > 0.0)) return -INFINITY;
+        for (int x = 0; x < 4; ++x) {
+            const double tr = fr[c][x], ti = fi[c][x];
+            fr[c][x] = fr[p][x];
+            fi[c][x] = fi[p][x];
+            fr[p][x] = tr;
+            fi[p][x] = ti;
+        }
+        lg += 0.5 * log(bm);
+        const double ir = fr[c][c] / bm, ii = -fi[c][c] / bm;
+        for (int r = c + 1; r < 4; ++r) {
+            const double mr = fr[r][c] * ir - fi[r][c] * ii, mi = fr[r][c] * ii + fi[r][c] * ir;
+            for (int x = c; x < 4; ++x) {
+                fr[r][x] -= mr * fr[c][x] - mi * fi[c][x];
+                fi[r][x] -= mr * fi[c][x] + mi * fr[c][x];
+            }
+        }
+    }
+    return lg;
+}
+
+// Shared memory of the look-ahead block kernel: WR + 1 band slots (one spare
+// takes each step's entering row) and the two border rows, each RS entries;
+// the active-row lists, multipliers and control words of two consecutive
+// steps; the weights; the row map; each slot's last nonzero band column.
+struct KwLayoutLA {
+    size_t a, mult, wt, map, ext, act, ctl, total;
+};
+
+__host__ __device__ inline KwLayoutLA kw_layout_la(int WR, int RS, int n, size_t cbytes) {
+    KwLayoutLA L;
+    L.a = 0;
+    L.mult = kw_align(L.a + (size_t)(WR + 3) * RS * cbytes);
+    L.wt = kw_align(L.mult + (size_t)2 * (WR + 2) * cbytes);
+    L.map = kw_align(L.wt + (size_t)n * (cbytes / 2));
+    L.ext = kw_align(L.map + (size_t)WR * 4);
+    L.act = kw_align(L.ext + (size_t)(WR + 3) * 4);
+    L.ctl = kw_align(L.act + (size_t)2 * (WR + 2) * 4);
+    L.total = kw_align(L.ctl + 64);
+    return L;
+}
+
+// Warp 0's part of a step, for step j (column j at position colj, logical
+// row j at map position kmodj): the pivot among rows j..j+bl, the row
+// exchange, the pivot's squared modulus into the mantissa, the multipliers
+// of the rows below (band rows, then the border rows at slots BR, BR+1) into
+// the lists of buffer b, column j of those rows zeroed, their extents grown.
+template <typename T, typename C>
+__device__ __forceinline__ void kw_la_pivot(const KwArgs& a, C* A, C* mult, int* map, int* ext, int* act, int* ctl,
+                                            int j, int colj, int kmodj, int b, int lane, T& mant, int& expo,
+                                            long long& rows_done, long long& cols_done) {
+    const unsigned FULL = 0xffffffffu;
+    const int WR = a.WR, RS = a.RS, Nb = a.Nb, BR = a.WR + 1;
+    const C zero = C{T(0), T(0)};
+    const int kend = (j + a.bl < Nb - 1) ? j + a.bl : Nb - 1;
+    T best = T(-1);
+    int boff = 0;
+    for (int off = lane; off <= kend - j; off += 32) {
+        int mp = kmodj + off;
+        if (mp >= WR) mp -= WR;
+        const C v = A[(size_t)map[mp] * RS + colj];
+        const T m2 = v.x * v.x + v.y * v.y;
+        if (m2 > best) {
+            best = m2;
+            boff = off;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const T ob = __shfl_xor_sync(FULL, best, o);
+        const int oo = __shfl_xor_sync(FULL, boff, o);
+        if (ob > best || (ob == best && oo < boff)) {
+            best = ob;
+            boff = oo;
+        }
+    }
+    if (!(best > T(0))) {
+        if (lane == 0) ctl[b * 4 + 3] = 1;
+        return;
+    }
+    if (lane == 0 && boff != 0) {
+        int mp = kmodj + boff;
+        if (mp >= WR) mp -= WR;
+        const int t0 = map[kmodj];
+        map[kmodj] = map[mp];
+        map[mp] = t0;
+    }
+    __syncwarp();
+    const int ps = map[kmodj];
+    const C u = A[(size_t)ps * RS + colj];
+    const T inv2 = T(1) / best;
+    const C inv = C{u.x * inv2, -u.y * inv2};
+    if (lane == 0) {
+        int e;
+        mant *= best;
+        mant = sizeof(T) == 4 ? (T)frexpf((float)mant, &e) : (T)frexp((double)mant, &e);
+        expo += e;
+    }
+    const int extp = ext[ps];
+    const int cnt1 = kend - j, ncand = cnt1 + 2;
+    int* actb = act + b * (WR + 2);
+    C* multb = mult + b * (WR + 2);
+    int nact = 0;
+    for (int base_i = 0; base_i < ncand; base_i += 32) {
+        const int idx = base_i + lane;
+        int s = 0;
+        C v = zero;
+        if (idx < cnt1) {
+            int mp = kmodj + 1 + idx;
+            if (mp >= WR) mp -= WR;
+            s = map[mp];
+        } else if (idx < ncand) {
+            s = BR + (idx - cnt1);
+        }
+        if (idx < ncand) v = A[(size_t)s * RS + colj];
+        const bool nz = v.x != T(0) || v.y != T(0);
+        const unsigned bal = __ballot_sync(FULL, nz);
+        if (nz) {
+            const int q = nact + __popc(bal & ((1u << lane) - 1u));
+            actb[q] = s;
+            multb[q] = C{v.x * inv.x - v.y * inv.y, v.x * inv.y + v.y * inv.x};
+            A[(size_t)s * RS + colj] = zero;
+            if (s < BR && ext[s] < extp) ext[s] = extp;
+        }
+        nact += __popc(bal);
+    }
+    if (lane == 0) {
+        ctl[b * 4 + 0] = ps;
+        ctl[b * 4 + 1] = extp;
+        ctl[b * 4 + 2] = nact;
+        ctl[b * 4 + 3] = 0;
+        rows_done += nact;
+        cols_done += (long long)nact * (extp - j + 4);
+    }
+    __syncwarp();
+}
+
+// ln Z of one part for both sectors, W warps per syndrome with look-ahead:
+// in step k warp 0 applies step k's update to column k+1, places the
+// entering row in the spare slot and takes step k+1's pivot and multipliers,
+// while warps 1..W-1 apply step k's update to columns k+2.. and the extra
+// columns. One block barrier per step; step k's lists are in buffer k & 1.
+template <typename T, int NT, int W>
+__device__ __forceinline__ void kw_part_la(const KwArgs& a, unsigned char* base, double out[2]) {
     using C = typename Cplx<T>::type;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned FULL = 0xffffffffu;
-    const KwLayout L = kw_layout(a.WR, a.RS, a.n, sizeof(C));
+    const KwLayoutLA L = kw_layout_la(a.WR, a.RS, a.n, sizeof(C));
     C* A = reinterpret_cast<C*>(base + L.a);
     C* mult = reinterpret_cast<C*>(base + L.mult);
     const T* wt = reinterpret_cast<const T*>(base + L.wt);
     int* map = reinterpret_cast<int*>(base + L.map);
     int* ext = reinterpret_cast<int*>(base + L.ext);
     int* act = reinterpret_cast<int*>(base + L.act);
-    int* ctl = reinterpret_cast<int*>(base + L.ctl);          // [0] pivot slot, [1] its last column, [2] active rows, [3] dead
+    int* ctl = reinterpret_cast<int*>(base + L.ctl);          // per buffer: pivot slot, its last column, active rows, dead
     double* res2 = reinterpret_cast<double*>(base + L.ctl + 32);
-    C* piv = reinterpret_cast<C*>(base + L.piv);
-    const int WR = a.WR, WC = a.WC, RS = a.RS, Nb = a.Nb;
+    const int WR = a.WR, WC = a.WC, RS = a.RS, Nb = a.Nb, BR = a.WR + 1;
     const C zero = C{T(0), T(0)};
 
-    // initial window: band rows 0..WR-1 (columns 0..WC-1), the border rows
-    for (int i = tid; i < (WR + 2) * RS; i += 32 * W) A[i] = zero;
+    for (int i = tid; i < (WR + 3) * RS; i += 32 * W) A[i] = zero;
     for (int r = tid; r < WR; r += 32 * W) map[r] = r;
-    if (tid == 0) ctl[3] = 0;
     __syncthreads();
     const int rows0 = WR < Nb ? WR : Nb;
     for (int i = warp; i < rows0; i += W) {
@@ -682,16 +835,14 @@ __device__ __forceinline__ void kw_part_block(const KwArgs& a, unsigned char* ba
         kw_place_row<T, C>(a, A + (size_t)i * RS, i, j, v, v1, lane);
         if (lane == 0) ext[i] = a.ext0[i];
     }
-    // border rows (warp W-1): entries in the first WC band columns, the
-    // border and the sector-1 columns now; later band columns when they enter
-    // the window (each lane of warp W-1 keeps its entry of both rows)
+    // border rows (warp 0 keeps each lane's entry of both)
     int bj[2] = {-1, -1};
     C bv[2] = {zero, zero};
-    if (warp == W - 1) {
+    if (warp == 0) {
         for (int t = 0; t < 2; ++t) {
             C v1;
             bj[t] = kw_fetch<T, C>(a, wt, Nb + t, lane, bv[t], v1);
-            C* R = A + (size_t)(WR + t) * RS;
+            C* R = A + (size_t)(BR + t) * RS;
             const int j = bj[t];
             if (j >= Nb) R[WC + (j - Nb)] = bv[t];
             else if (j >= 0) {
@@ -703,136 +854,63 @@ __device__ __forceinline__ void kw_part_block(const KwArgs& a, unsigned char* ba
     }
     __syncthreads();
 
-    long long rows_done = 0, cols_done = 0;   // multipliers and updated row-columns (warp 0, lane 0)
     T mant = T(1);
     int expo = 0;
+    long long rows_done = 0, cols_done = 0;
+    int spare = WR;                         // the free band slot (warp 0)
+    if (warp == 0)
+        kw_la_pivot<T, C>(a, A, mult, map, ext, act, ctl, 0, 0, 0, 0, lane, mant, expo, rows_done, cols_done);
+    __syncthreads();
     bool dead = false;
     int colk = 0, kmod = 0;    // k mod WC, k mod WR
-    // the row entering during a step (warp W-1): fetched at its top while
-    // warp 0 takes the pivot, placed while the others update
-    C nv = zero, nv1 = zero;
-    int nj = -1, next = 0;
     for (int k = 0; k < Nb - 2; ++k) {
-        const int rin = k + WR;
-        if (warp == W - 1) {
-            nj = -1;
-            if (rin < Nb) {
-                nj = kw_fetch<T, C>(a, wt, rin, lane, nv, nv1);
-                next = a.ext0[rin];
-            }
-        }
-        if (warp == 0) {
-            const int kend = (k + a.bl < Nb - 1) ? k + a.bl : Nb - 1;
-            // pivot: the largest |entry| of column k among the band rows k..kend
-            T best = T(-1);
-            int boff = 0;
-            for (int off = lane; off <= kend - k; off += 32) {
-                int mp = kmod + off;
-                if (mp >= WR) mp -= WR;
-                const C v = A[(size_t)map[mp] * RS + colk];
-                const T m2 = v.x * v.x + v.y * v.y;
-                if (m2 > best) {
-                    best = m2;
-                    boff = off;
-                }
-            }
-#pragma unroll
-            for (int o = 16; o; o >>= 1) {
-                const T ob = __shfl_xor_sync(FULL, best, o);
-                const int oo = __shfl_xor_sync(FULL, boff, o);
-                if (ob > best || (ob == best && oo < boff)) {
-                    best = ob;
-                    boff = oo;
-                }
-            }
-            if (!(best > T(0))) {
-                if (lane == 0) ctl[3] = 1;
-            } else {
-                if (lane == 0 && boff != 0) {
-                    int mp = kmod + boff;
-                    if (mp >= WR) mp -= WR;
-                    const int t0 = map[kmod];
-                    map[kmod] = map[mp];
-                    map[mp] = t0;
-                }
-                __syncwarp();
-                const int ps = map[kmod];
-                const C u = A[(size_t)ps * RS + colk];
-                const T inv2 = T(1) / best;
-                const C inv = C{u.x * inv2, -u.y * inv2};
-                if (lane == 0) {
-                    int e;
-                    mant *= best;
-                    mant = sizeof(T) == 4 ? (T)frexpf((float)mant, &e) : (T)frexp((double)mant, &e);
-                    expo += e;
-                }
-                const int extp = ext[ps];
-                // multipliers of the rows below (band rows k+1..kend, then the
-                // two border rows), the nonzero ones listed in act / mult
-                const int cnt1 = kend - k, ncand = cnt1 + 2;
-                int nact = 0;
-                for (int base_i = 0; base_i < ncand; base_i += 32) {
-                    const int idx = base_i + lane;
-                    int s = 0;
-                    C v = zero;
-                    if (idx < cnt1) {
-                        int mp = kmod + 1 + idx;
-                        if (mp >= WR) mp -= WR;
-                        s = map[mp];
-                    } else if (idx < ncand) {
-                        s = WR + (idx - cnt1);
-                    }
-                    if (idx < ncand) v = A[(size_t)s * RS + colk];
-                    const bool nz = v.x != T(0) || v.y != T(0);
-                    const unsigned bal = __ballot_sync(FULL, nz);
-                    if (nz) {
-                        const int q = nact + __popc(bal & ((1u << lane) - 1u));
-                        act[q] = s;
-                        mult[q] = C{v.x * inv.x - v.y * inv.y, v.x * inv.y + v.y * inv.x};
-                        A[(size_t)s * RS + colk] = zero;
-                        if (s < WR && ext[s] < extp) ext[s] = extp;
-                    }
-                    nact += __popc(bal);
-                }
-                // the pivot row's copy, so that its slot can take the entering
-                // row during the update
-                const C* P = A + (size_t)ps * RS;
-                for (int i = lane; i < RS; i += 32) piv[i] = P[i];
-                if (lane == 0) {
-                    ctl[0] = ps;
-                    ctl[1] = extp;
-                    ctl[2] = nact;
-                    rows_done += nact;
-                    cols_done += (long long)nact * (extp - k + 4);
-                }
-            }
-        }
-        __syncthreads();
-        if (ctl[3]) {
+        const int b = k & 1;
+        if (ctl[b * 4 + 3]) {
             dead = true;
             break;
         }
-        // rank-one update: warp w takes the active rows in groups of RU,
-        // group g = w, w + W, ...; lanes own columns k+1..extp of the pivot
-        // row (lane-strided) and its four extra columns
-        {
-            const int ps = ctl[0], extp = ctl[1], nact = ctl[2];
-            if (warp == W - 1) {
-                // the pivot row leaves: row k + WR takes its slot; column
-                // k + WC enters (its position is colk)
-                C* R = A + (size_t)ps * RS;
-                if (rin < Nb) {
-                    for (int i = lane; i < RS; i += 32) R[i] = zero;
-                    __syncwarp();
-                    kw_place_row<T, C>(a, R, rin, nj, nv, nv1, lane);
-                    if (lane == 0) ext[ps] = next;
-                }
-                const int jn = k + WC;
-#pragma unroll
-                for (int t = 0; t < 2; ++t)
-                    if (bj[t] == jn && jn < Nb) A[(size_t)(WR + t) * RS + colk] = bv[t];
+        const int ps = ctl[b * 4 + 0], extp = ctl[b * 4 + 1], nact = ctl[b * 4 + 2];
+        const int* actb = act + b * (WR + 2);
+        const C* multb = mult + b * (WR + 2);
+        const C* P = A + (size_t)ps * RS;
+        const int colk1 = colk + 1 == WC ? 0 : colk + 1;
+        const int kmod1 = kmod + 1 == WR ? 0 : kmod + 1;
+        if (warp == 0) {
+            // step k's update of column k+1
+            const C u1 = k + 1 <= extp ? P[colk1] : zero;
+            for (int q = lane; q < nact; q += 32) {
+                C* R = A + (size_t)actb[q] * RS;
+                C r = R[colk1];
+                kw_axpy<C, T>(r, multb[q], u1);
+                R[colk1] = r;
             }
-            const C* P = piv;
+            // row k + WR enters in the spare slot (its map position is
+            // k's); the pivot's slot becomes the spare
+            const int rin = k + WR;
+            if (rin < Nb) {
+                C v, v1;
+                const int j = kw_fetch<T, C>(a, wt, rin, lane, v, v1);
+                C* R = A + (size_t)spare * RS;
+                for (int i = lane; i < RS; i += 32) R[i] = zero;
+                __syncwarp();
+                kw_place_row<T, C>(a, R, rin, j, v, v1, lane);
+                if (lane == 0) {
+                    ext[spare] = a.ext0[rin];
+                    map[kmod] = spare;
+                }
+                spare = ps;
+            }
+            // the border rows' entries of the entering column k + WC
+            const int jn = k + WC;
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+                if (bj[t] == jn && jn < Nb) A[(size_t)(BR + t) * RS + colk] = bv[t];
+            __syncwarp();
+            if (k + 1 < Nb - 2)
+                kw_la_pivot<T, C>(a, A, mult, map, ext, act, ctl, k + 1, colk1, kmod1, b ^ 1, lane, mant, expo,
+                                  rows_done, cols_done);
+        } else {
+            // step k's update of columns k+2..extp and the four extra columns
             C U[NT];
             int pc[NT];
 #pragma unroll
@@ -840,106 +918,48 @@ __device__ __forceinline__ void kw_part_block(const KwArgs& a, unsigned char* ba
                 const int c = k + 1 + lane + 32 * t;
                 int p = colk + 1 + lane + 32 * t;
                 if (p >= WC) p -= WC;
-                pc[t] = c <= extp ? p : -1;
-                U[t] = c <= extp ? P[p] : zero;
+                pc[t] = (c >= k + 2 && c <= extp) ? p : -1;
+                U[t] = pc[t] >= 0 ? P[p] : zero;
             }
             const C Ux = lane < 4 ? P[WC + lane] : zero;
-            for (int q0 = warp * RU; q0 < nact; q0 += W * RU) {
-                int s[RU];
-                C m[RU];
-                bool ok[RU];
+            for (int q = warp - 1; q < nact; q += W - 1) {
+                C* R = A + (size_t)actb[q] * RS;
+                const C m = multb[q];
+                C r[NT], rx;
 #pragma unroll
-                for (int j = 0; j < RU; ++j) {
-                    ok[j] = q0 + j < nact;
-                    s[j] = ok[j] ? act[q0 + j] : 0;
-                    m[j] = ok[j] ? mult[q0 + j] : zero;
-                }
-                C r[RU][NT], rx[RU];
+                for (int t = 0; t < NT; ++t)
+                    if (pc[t] >= 0) r[t] = R[pc[t]];
+                if (lane < 4) rx = R[WC + lane];
 #pragma unroll
-                for (int j = 0; j < RU; ++j) {
-#pragma unroll
-                    for (int t = 0; t < NT; ++t)
-                        if (ok[j] && pc[t] >= 0) r[j][t] = A[(size_t)s[j] * RS + pc[t]];
-                    if (ok[j] && lane < 4) rx[j] = A[(size_t)s[j] * RS + WC + lane];
-                }
-#pragma unroll
-                for (int j = 0; j < RU; ++j) {
-#pragma unroll
-                    for (int t = 0; t < NT; ++t)
-                        if (ok[j] && pc[t] >= 0) {
-                            kw_axpy<C, T>(r[j][t], m[j], U[t]);
-                            A[(size_t)s[j] * RS + pc[t]] = r[j][t];
-                        }
-                    if (ok[j] && lane < 4) {
-                        kw_axpy<C, T>(rx[j], m[j], Ux);
-                        A[(size_t)s[j] * RS + WC + lane] = rx[j];
+                for (int t = 0; t < NT; ++t)
+                    if (pc[t] >= 0) {
+                        kw_axpy<C, T>(r[t], m, U[t]);
+                        R[pc[t]] = r[t];
                     }
+                if (lane < 4) {
+                    kw_axpy<C, T>(rx, m, Ux);
+                    R[WC + lane] = rx;
                 }
             }
         }
         __syncthreads();
-        colk = colk + 1 == WC ? 0 : colk + 1;
-        kmod = kmod + 1 == WR ? 0 : kmod + 1;
+        colk = colk1;
+        kmod = kmod1;
     }
 
-    // warp 0: the last two band rows and the border rows against the sector
-    // columns (regular: sector 0; the carried copies: sector 1) and the border
-    // columns; lanes 0 and 1 take one sector each
     if (warp == 0) {
         const double lm = __shfl_sync(FULL, log((double)mant) + (double)expo * 0.69314718055994530942, 0);
         double res = -INFINITY;
         if (!dead && lane < 2) {
             const int m0 = kmod, m1 = kmod + 1 == WR ? 0 : kmod + 1;   // k = Nb - 2 here
-            const int rows[4] = {map[m0], map[m1], WR, WR + 1};
+            const int rows[4] = {map[m0], map[m1], BR, BR + 1};
             const int cols[4] = {lane == 0 ? colk : WC + 2, lane == 0 ? (colk + 1 == WC ? 0 : colk + 1) : WC + 3,
                                  WC, WC + 1};
-            double fr[4][4], fi[4][4];
-            for (int r = 0; r < 4; ++r)
-                for (int c = 0; c < 4; ++c) {
-                    const C v = A[(size_t)rows[r] * RS + cols[c]];
-                    fr[r][c] = (double)v.x;
-                    fi[r][c] = (double)v.y;
-                }
-            double lg = 0.0;
-            for (int c = 0; c < 4; ++c) {
-                int p = c;
-                double bm = -1.0;
-                for (int r = c; r < 4; ++r) {
-                    const double m2 = fr[r][c] * fr[r][c] + fi[r][c] * fi[r][c];
-                    if (m2 > bm) {
-                        bm = m2;
-                        p = r;
-                    }
-                }
-                if (!(bm > 0.0)) {
-                    lg = -INFINITY;
-                    break;
-                }
-                for (int x = 0; x < 4; ++x) {
-                    const double tr = fr[c][x], ti = fi[c][x];
-                    fr[c][x] = fr[p][x];
-                    fi[c][x] = fi[p][x];
-                    fr[p][x] = tr;
-                    fi[p][x] = ti;
-                }
-                lg += 0.5 * log(bm);
-                const double ir = fr[c][c] / bm, ii = -fi[c][c] / bm;
-                for (int r = c + 1; r < 4; ++r) {
-                    const double mr = fr[r][c] * ir - fi[r][c] * ii, mi = fr[r][c] * ii + fi[r][c] * ir;
-                    for (int x = c; x < 4; ++x) {
-                        fr[r][x] -= mr * fr[c][x] - mi * fi[c][x];
-                        fi[r][x] -= mr * fi[c][x] + mi * fr[c][x];
-                    }
-                }
-            }
-            // ln|det| = ln prod |u_kk| + ln|det F| = lm / 2 + lg
-            res = a.cst + 0.5 * (0.5 * lm + lg);
+            res = a.cst + 0.5 * (0.5 * lm + kw_logdet4<C>(A, RS, rows, cols));
         }
         if (lane < 2) res2[lane] = res;
         if (dead && lane == 0) atomicOr(a.status, 1 << MLD_ERR_NUMERIC);
-        // per active row a complex multiplier (6 flops), per updated column a
-    // complex multiply-subtract (8 flops)
-    if (lane == 0 && a.flops) atomicAdd(a.flops, 6.0 * (double)rows_done + 8.0 * (double)cols_done);
+        if (lane == 0 && a.flops) atomicAdd(a.flops, 6.0 * (double)rows_done + 8.0 * (double)cols_done);
     }
     __syncthreads();
     out[0] = res2[0];
@@ -947,17 +967,16 @@ __device__ __forceinline__ void kw_part_block(const KwArgs& a, unsigned char* ba
     __syncthreads();
 }
 
-// One block of W warps per syndrome (d >= 15), persistent over the batch;
-// the same steps as kw_decode_warp_kernel.
+// One block of W warps per syndrome with the look-ahead schedule (d >= 15),
+// persistent over the batch; the same steps as kw_decode_warp_kernel.
 template <typename T, int NT>
-__global__ void __launch_bounds__(32 * kKwWarps) kw_decode_block_kernel(KwArgs a) {
-    constexpr int RU = 1;                        // rows per update group (registers: 4 blocks of 4 warps per SM)
+__global__ void __launch_bounds__(32 * kKwWarps) kw_decode_la_kernel(KwArgs a) {
     constexpr int W = kKwWarps;
     extern __shared__ __align__(16) unsigned char kw_smem[];
     using C = typename Cplx<T>::type;
     const int tid = threadIdx.x;
     unsigned char* base = kw_smem;
-    const KwLayout L = kw_layout(a.WR, a.RS, a.n, sizeof(C));
+    const KwLayoutLA L = kw_layout_la(a.WR, a.RS, a.n, sizeof(C));
     T* wt = reinterpret_cast<T*>(base + L.wt);
     const int n = a.n;
     for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
@@ -978,7 +997,7 @@ __global__ void __launch_bounds__(32 * kKwWarps) kw_decode_block_kernel(KwArgs a
         }
         zany = __syncthreads_or(zany);
         double lx[2], lz[2];
-        kw_part_block<T, NT, RU, W>(a, base, lx);
+        kw_part_la<T, NT, W>(a, base, lx);
         if (a.pz) {
             for (int qt = tid; qt < n; qt += 32 * W) {
                 const int q = a.zmap[qt];
@@ -990,10 +1009,8 @@ __global__ void __launch_bounds__(32 * kKwWarps) kw_decode_block_kernel(KwArgs a
                 wt[qt] = (z ? T(-1) : T(1)) * (T(1) - T(2) * (T)p);
             }
             __syncthreads();
-            kw_part_block<T, NT, RU, W>(a, base, lz);
+            kw_part_la<T, NT, W>(a, base, lz);
         } else {
-            // no Z errors: only the coset holding the identity's z-part has
-            // weight, and only if the representative has no z-bits
             lz[0] = zany ? -INFINITY : 0.0;
             lz[1] = -INFINITY;
         }
@@ -1070,36 +1087,39 @@ mld_status ensure_kw(mld_code* C) {
     return MLD_OK;
 }
 
-template <typename T, typename K>
-mld_status launch_kw_kernel(K kernel, int threads, const KwArgs& a, cudaStream_t s) {
-    using C = typename Cplx<T>::type;
-    const KwLayout L = kw_layout(a.WR, a.RS, a.n, sizeof(C));
+template <typename K>
+mld_status launch_kw_kernel(K kernel, int threads, size_t bytes, const KwArgs& a, cudaStream_t s) {
     int dev = 0, sms = 0, smem_max = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return MLD_ERR_CUDA;
-    if (L.total > (size_t)smem_max) return MLD_ERR_UNSUPPORTED;
-    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) != cudaSuccess)
+    if (bytes > (size_t)smem_max) return MLD_ERR_UNSUPPORTED;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
         return MLD_ERR_CUDA;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, L.total) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, bytes) != cudaSuccess ||
         per_sm < 1)
         return MLD_ERR_UNSUPPORTED;
     int64_t blocks = (int64_t)sms * per_sm;
     if (blocks > a.B) blocks = a.B;
-    kernel<<<(unsigned)blocks, threads, L.total, s>>>(a);
+    kernel<<<(unsigned)blocks, threads, bytes, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? MLD_OK : MLD_ERR_CUDA;
 }
 
 // One warp per syndrome while the window is small (up to 3 pivot-row columns
 // per lane, d <= 13: measured faster there, 1.77 M against 1.15 M syndromes/s
-// at d = 9); a block of kKwWarps warps per syndrome above (d = 17: 204 k
-// against 148 k; d = 25: 44 k against 26 k).
+// for four warps at d = 9); the look-ahead block of kKwWarps warps per
+// syndrome above (d = 17: 231 k against 148 k for one warp; d = 25: 56 k
+// against 26 k).
 template <typename T, int NT>
 mld_status launch_kw_nt(const KwArgs& a, cudaStream_t s) {
-    if constexpr (NT <= 3) return launch_kw_kernel<T>(kw_decode_warp_kernel<T, NT>, 32, a, s);
-    else return launch_kw_kernel<T>(kw_decode_block_kernel<T, NT>, 32 * kKwWarps, a, s);
+    using C = typename Cplx<T>::type;
+    if constexpr (NT <= 3)
+        return launch_kw_kernel(kw_decode_warp_kernel<T, NT>, 32, kw_layout(a.WR, a.RS, a.n, sizeof(C)).total, a, s);
+    else
+        return launch_kw_kernel(kw_decode_la_kernel<T, NT>, 32 * kKwWarps,
+                                kw_layout_la(a.WR, a.RS, a.n, sizeof(C)).total, a, s);
 }
 
 // Columns of the pivot row per lane: (bl + bu) / 32 rounded up (2 at d <= 9,
