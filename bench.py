@@ -738,6 +738,56 @@ def run_kw_threshold(args):
     print(json.dumps(line), flush=True)
 
 
+def run_kw_chi(args):
+    """Convergence of the truncated boundary-MPS decode to exact MLD at
+    distances the exact contraction cannot reach: independent X/Z noise with
+    px = pz = p (default 0.05 and 0.10), --kw-batch syndromes per point
+    (default 4,096, seed config_seed(9, d, p)), the Kac-Ward decode (FP64) as
+    the exact reference, and the boundary-MPS decode of the product table at
+    each chi of --kw-chi with the singular-value cutoff --kw-chi-cutoff:
+    decisions that differ from exact MLD, the largest |d ln Z| of the leading
+    class, both logical-error rates (Sec. 3.2.1: the bond needed to match
+    exact MLD)."""
+    import torch
+    import paper_2605_17230_gb300 as mld
+
+    Bd = args.kw_batch or 4096
+    rows = []
+    for d in args.kw_d:
+        n = d * d
+        code = mld.Code(d)
+        for p in args.kw_chi_p:
+            px = np.full(n, p, np.float32)
+            tab = synth.independent_xz(px, px)
+            E = synth.sample_errors(d, tab, Bd, seed=synth.config_seed(9, d, p))
+            true = synth.true_class(d, E)
+            sy = torch.tensor(synth.syndromes_of(d, E).view(np.int64), device="cuda")
+            dpx = torch.tensor(px, device="cuda")
+            lpx, amx = code.decode_xz(dpx, dpx, sy, mld.MLD_FP64)
+            nz = torch.tensor(tab.astype(np.float32), device="cuda")
+            code.set_svd_cutoff(args.kw_chi_cutoff)
+            lead = torch.argmax(lpx, dim=1)
+            row = {"d": d, "p": p, "syndromes": Bd,
+                   "exact_logical_error_rate": float((amx.cpu().numpy() != true).mean()), "chi": []}
+            for chi in args.kw_chi:
+                t0 = time.time()
+                lpm, amm = code.decode(nz, sy, chi)
+                torch.cuda.synchronize()
+                dt = time.time() - t0
+                dl = (lpm.gather(1, lead[:, None]) - lpx.gather(1, lead[:, None])).abs().max().item()
+                row["chi"].append({"chi": chi, "decisions_differ": int((amm != amx).sum().item()),
+                                   "max_abs_dlnZ_leading": dl, "seconds": dt,
+                                   "logical_error_rate": float((amm.cpu().numpy() != true).mean())})
+            if code.status() != 0:
+                raise RuntimeError("device status after the decodes")
+            rows.append(row)
+        code.close()
+    line = {"metric": "decisions of the truncated boundary-MPS decode that differ from exact MLD (Kac-Ward)",
+            "workload": "kw-chi", "unit": "syndromes", "data": "synthetic", "svd_cutoff": args.kw_chi_cutoff,
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -750,7 +800,7 @@ def main():
                     "65536 of the workload; smaller values only for profiling captures)")
     ap.add_argument("--workload", default="metric",
                     choices=["metric", "mixed", "grad", "large", "ler", "dmle", "dem", "point", "kw",
-                             "kw-threshold"],
+                             "kw-threshold", "kw-chi"],
                     help="metric: the headline d=9 line (default); mixed: the 1,048,576-syndrome mixed-d "
                          "graph batch; grad: the adjoint on the d=7 workload; dmle: full-batch noise "
                          "estimation from 1,048,576 unlabelled d=9 syndromes; dem: detector-picture decode of "
@@ -758,11 +808,15 @@ def main():
                          "ler: logical-error rates of the d/p grid against the oracle; point: one (d, chi, p) "
                          "decode point, FP32 and mixed; kw: the Kac-Ward decode under independent X/Z "
                          "noise against the boundary-MPS decode of the same syndromes; kw-threshold: "
-                         "logical-error rates under bit-flip noise around the 10.9% threshold, exact")
+                         "logical-error rates under bit-flip noise around the 10.9% threshold, exact; kw-chi: "
+                         "truncated boundary-MPS decisions against exact MLD at d=17, 25")
     ap.add_argument("--kw-d", type=int, nargs="+", default=[9, 13, 17, 25], help="kw: distances")
     ap.add_argument("--kw-p", type=float, default=0.10, help="kw: X and Z flip rate per qubit")
     ap.add_argument("--kw-batch", type=int, default=0, help="kw: syndromes per decode (0: by d)")
     ap.add_argument("--kw-no-mps", action="store_true", help="kw: skip the boundary-MPS comparison")
+    ap.add_argument("--kw-chi", type=int, nargs="+", default=[2, 4, 8, 16, 32], help="kw-chi: bond caps")
+    ap.add_argument("--kw-chi-p", type=float, nargs="+", default=[0.05, 0.10], help="kw-chi: X and Z flip rates")
+    ap.add_argument("--kw-chi-cutoff", type=float, default=1e-7, help="kw-chi: relative singular-value cutoff")
     ap.add_argument("--kw-threshold-p", type=float, nargs="+",
                     default=[0.095, 0.100, 0.105, 0.110, 0.115, 0.120], help="kw-threshold: bit-flip rates")
     ap.add_argument("--large-batch", type=int, default=16384)
@@ -800,6 +854,8 @@ def main():
         return run_kw(args) if rank == 0 else None
     if args.workload == "kw-threshold":
         return run_kw_threshold(args) if rank == 0 else None
+    if args.workload == "kw-chi":
+        return run_kw_chi(args) if rank == 0 else None
     if args.workload == "point":
         return run_point(args) if rank == 0 else None
 
