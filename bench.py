@@ -615,6 +615,14 @@ def run_dem(args):
     print(json.dumps(line), flush=True)
 
 
+def _lead_gap(lp, ref):
+    """max, p99 and p99.9 of |ln Z_lead(lp) - ln Z_lead(ref)| with lead the
+    leading class of ref (torch tensors [B][4])."""
+    lead = ref.argmax(dim=1, keepdim=True)
+    g = (lp.gather(1, lead) - ref.gather(1, lead)).abs().flatten()
+    return {"max": g.max().item(), "p99": g.quantile(0.99).item(), "p999": g.quantile(0.999).item()}
+
+
 def run_kw(args):
     """Kac-Ward decode (Sec. 3.1.3) under independent X/Z noise with
     px = pz = p on every qubit (default 0.10): syndromes sampled from the
@@ -664,6 +672,7 @@ def run_kw(args):
                "fp64_value": B64 / (ms64 / 1e3), "fp64_syndromes": B64,
                "logical_error_rate": float((am.long() != true).float().mean().item()),
                "fp32_fp64_decisions_differ": int((am[:B64] != am64).sum().item()),
+               "fp32_vs_fp64_leading_dlnZ": _lead_gap(lp[:B64], lp64),
                "executed_flops_per_syndrome": flops,
                "roofline": {"bound": "alu", "achieved": flops * Bd / (ms32 / 1e3) / 1e12, "peak": peak,
                             "unit": "TFLOP/s", "frac": flops * Bd / (ms32 / 1e3) / 1e12 / peak, "traffic": None}}

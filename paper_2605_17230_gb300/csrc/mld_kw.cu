@@ -30,10 +30,15 @@
 // the two border rows). ln|det| accumulates the pivots' squared moduli as a
 // mantissa and a power-of-two exponent. Complex FP32 or FP64.
 //
-// Floating point: ES sums signed terms. For a class far less likely than the
-// leading one they cancel, and its ln Z then carries an error of order
-// eps * cond(I - Lambda) relative to the leading class's Z; the leading class
-// and the decision keep full accuracy (measured figures in the tests).
+// Floating point: ES sums signed terms, so the elimination loses accuracy
+// with the conditioning of I - Lambda: a class far less likely than the
+// leading one can carry an error of order eps * cond relative to the leading
+// class's Z, and at low error rates (large |t|, an ill-conditioned matrix)
+// even the leading class can: measured against FP64 over 4,096 syndromes,
+// complex FP32 keeps the leading ln Z within 1.1e-3 at p = 0.10 up to d = 25,
+// but reaches 0.097 (p = 0.05) and 0.29 (p = 0.02) at d = 25 on rare
+// syndromes, and one decision of 4,096 differed at d = 17, p = 0.02. FP64 is
+// the accurate mode.
 #include <math.h>
 #include <stdint.h>
 

@@ -7,13 +7,14 @@ degenerate and invalid inputs.
 Tolerances. FP64: every class to 1e-8 where the oracle's exact value is within
 30 nats of the leading class (beyond that the signed determinant of a class
 that unlikely is below FP64's resolution of the leading one, a property of the
-method). FP32: the leading class's ln Z to 1e-4 (1e-3 at d = 25, where about
-2,600 pivots round: measured 6.6e-4 on one of four syndromes, reproduced by a
-CPU emulation of the same elimination in complex64) and the posteriors
-Z_l / sum Z to 1e-3 (the FP32 determinant resolves a class only down to about
-1e-6 .. 1e-3 of the leading one, growing with d and falling with p); the
-decisions equal the oracle's wherever its two best classes differ by more than
-1e-3 in ln Z."""
+method). FP32 (its accuracy follows the conditioning of the matrix, which
+worsens at low rates: the inputs here are sampled at rates where it is
+resolved, 0.02..0.2 per qubit up to d = 13 and 0.08 at d = 17, 25): the
+leading class's ln Z to 1e-4 (1e-3 at d = 25, where about 2,600 pivots round)
+and the posteriors Z_l / sum Z to 1e-3; the decisions equal the oracle's
+wherever its two best classes differ by more than 1e-3 in ln Z. Rare
+syndromes at low rates exceed these bounds in FP32 (measured with the bench,
+not asserted here)."""
 import math
 
 import numpy as np
