@@ -252,3 +252,24 @@ def test_truncated_sweep_against_exact_mld(mld, cutoff, atol):
     srt = np.sort(exact, axis=1)
     clear = srt[:, -1] - srt[:, -2] > 1e-3
     np.testing.assert_array_equal(am[clear], am_exact[clear])
+
+
+def test_fp32_against_fp64_near_threshold_d25(mld):
+    """The regime the complex-FP32 path is for: d = 25, px = pz = 0.10. Over
+    512 syndromes its leading-class ln Z is within 2e-3 of the FP64 path
+    (measured over 4,096: max 1.1e-3) and its decisions are the FP64 ones
+    wherever FP64's two best classes differ by more than 1e-3."""
+    d, B, p = 25, 512, 0.10
+    n = d * d
+    px = np.full(n, p, np.float32)
+    tab = okw.xz_table(px.astype(np.float64), px.astype(np.float64))
+    syn = synth.syndromes_of(d, synth.sample_errors(d, tab, B, seed=25))
+    code = mld.Code(d)
+    l64, a64 = _run(mld, code, px, px, syn, mld.MLD_FP64)
+    l32, a32 = _run(mld, code, px, px, syn, mld.MLD_FP32)
+    rows = np.arange(B)
+    lead = np.argmax(l64, axis=1)
+    np.testing.assert_allclose(l32[rows, lead], l64[rows, lead], rtol=0, atol=2e-3)
+    srt = np.sort(l64, axis=1)
+    clear = srt[:, -1] - srt[:, -2] > 1e-3
+    np.testing.assert_array_equal(a32[clear], a64[clear])
