@@ -695,6 +695,64 @@ def run_kw(args):
     print(json.dumps(line), flush=True)
 
 
+def _crossings(ler, ds, ps):
+    """Where the LER curves of consecutive distances cross: the first sign
+    change of ler(d2, p) - ler(d1, p) along ps, by linear interpolation."""
+    cross = []
+    for d1, d2 in zip(ds, ds[1:]):
+        diff = [ler[(d2, p)] - ler[(d1, p)] for p in ps]
+        pc = None
+        for i in range(len(ps) - 1):
+            if diff[i] < 0 <= diff[i + 1]:
+                pc = ps[i] + (ps[i + 1] - ps[i]) * (-diff[i]) / (diff[i + 1] - diff[i])
+                break
+        cross.append({"d": [d1, d2], "p_cross": pc})
+    return cross
+
+
+def run_threshold(args):
+    """Logical-error rates under depolarizing noise around the optimal
+    threshold the paper quotes for it (18.9%, Sec. 3.1.2), decoded by the
+    boundary-MPS path: untruncated chi at d <= 13 (2^floor(d/2)), --thr-chi
+    above. Per point --thr-batch syndromes (seed config_seed(10, d, p)), the
+    LER with its Wilson interval, the decode rate, and the crossings of
+    consecutive distances."""
+    import torch
+    import paper_2605_17230_gb300 as mld
+
+    ps, Bd = args.thr_p, args.thr_batch
+    rows, ler = [], {}
+    for d in args.thr_d:
+        n = d * d
+        chi = 1 << (d // 2) if d <= 13 else args.thr_chi
+        code = mld.Code(d)
+        for p in ps:
+            tab = synth.depolarizing(n, p)
+            E = synth.sample_errors(d, tab, Bd, seed=synth.config_seed(10, d, p))
+            true = synth.true_class(d, E)
+            sy = torch.tensor(synth.syndromes_of(d, E).view(np.int64), device="cuda")
+            nz = torch.tensor(tab.astype(np.float32), device="cuda")
+            code.decode(nz, sy[:256], chi)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, am = code.decode(nz, sy, chi)
+            e1.record()
+            torch.cuda.synchronize()
+            if code.status() != 0:
+                raise RuntimeError("device status after the decode")
+            k = int((am.cpu().numpy() != true).sum())
+            lo, hi = wilson_interval(k, Bd)
+            ler[(d, p)] = k / Bd
+            rows.append({"d": d, "chi": chi, "p": p, "syndromes": Bd, "logical_error_rate": k / Bd,
+                         "ci95": [lo, hi], "syndromes_per_s": Bd / (e0.elapsed_time(e1) / 1e3)})
+        code.close()
+    line = {"metric": "logical-error rate under depolarizing noise, boundary-MPS MLD", "workload": "threshold",
+            "unit": "logical errors per syndrome", "data": "synthetic", "dtype": "f32 sweep, f64 ln Z",
+            "paper_threshold": 0.189, "rows": rows, "crossings": _crossings(ler, list(args.thr_d), ps)}
+    print(json.dumps(line), flush=True)
+
+
 def run_kw_threshold(args):
     """Logical-error rates under bit-flip noise (independent X flips with
     probability p on every qubit, no Z errors) decoded exactly by the Kac-Ward
@@ -731,16 +789,7 @@ def run_kw_threshold(args):
             rows.append({"d": d, "p": p, "syndromes": Bd, "logical_error_rate": k / Bd, "ci95": [lo, hi],
                          "seconds": dt})
         code.close()
-    cross = []
-    ds = list(args.kw_d)
-    for d1, d2 in zip(ds, ds[1:]):
-        diff = [ler[(d2, p)] - ler[(d1, p)] for p in ps]
-        pc = None
-        for i in range(len(ps) - 1):
-            if diff[i] < 0 <= diff[i + 1]:
-                pc = ps[i] + (ps[i + 1] - ps[i]) * (-diff[i]) / (diff[i + 1] - diff[i])
-                break
-        cross.append({"d": [d1, d2], "p_cross": pc})
+    cross = _crossings(ler, list(args.kw_d), ps)
     line = {"metric": "logical-error rate under bit-flip noise, exact MLD (Kac-Ward)", "workload": "kw-threshold",
             "unit": "logical errors per syndrome", "data": "synthetic", "dtype": "complex f32 elimination, f64 ln Z",
             "paper_threshold": 0.109, "rows": rows, "crossings": cross}
@@ -815,7 +864,7 @@ def main():
                     "65536 of the workload; smaller values only for profiling captures)")
     ap.add_argument("--workload", default="metric",
                     choices=["metric", "mixed", "grad", "large", "ler", "dmle", "dem", "point", "kw",
-                             "kw-threshold", "kw-chi"],
+                             "kw-threshold", "kw-chi", "threshold"],
                     help="metric: the headline d=9 line (default); mixed: the 1,048,576-syndrome mixed-d "
                          "graph batch; grad: the adjoint on the d=7 workload; dmle: full-batch noise "
                          "estimation from 1,048,576 unlabelled d=9 syndromes; dem: detector-picture decode of "
@@ -824,12 +873,18 @@ def main():
                          "decode point, FP32 and mixed; kw: the Kac-Ward decode under independent X/Z "
                          "noise against the boundary-MPS decode of the same syndromes; kw-threshold: "
                          "logical-error rates under bit-flip noise around the 10.9% threshold, exact; kw-chi: "
-                         "truncated boundary-MPS decisions against exact MLD at d=17, 25")
+                         "truncated boundary-MPS decisions against exact MLD at d=17, 25; threshold: "
+                         "logical-error rates under depolarizing noise around the 18.9% threshold")
     ap.add_argument("--kw-d", type=int, nargs="+", default=[9, 13, 17, 25], help="kw: distances")
     ap.add_argument("--kw-p", type=float, default=0.10, help="kw: X and Z flip rate per qubit")
     ap.add_argument("--kw-batch", type=int, default=0, help="kw: syndromes per decode (0: by d)")
     ap.add_argument("--kw-no-mps", action="store_true", help="kw: skip the boundary-MPS comparison")
     ap.add_argument("--kw-chi", type=int, nargs="+", default=[2, 4, 8, 16, 32], help="kw-chi: bond caps")
+    ap.add_argument("--thr-d", type=int, nargs="+", default=[9, 13, 17], help="threshold: distances")
+    ap.add_argument("--thr-p", type=float, nargs="+", default=[0.170, 0.175, 0.180, 0.185, 0.190, 0.195],
+                    help="threshold: depolarizing rates")
+    ap.add_argument("--thr-batch", type=int, default=32768, help="threshold: syndromes per point")
+    ap.add_argument("--thr-chi", type=int, default=64, help="threshold: bond cap above d = 13")
     ap.add_argument("--kw-chi-p", type=float, nargs="+", default=[0.05, 0.10], help="kw-chi: X and Z flip rates")
     ap.add_argument("--kw-chi-cutoff", type=float, default=1e-7, help="kw-chi: relative singular-value cutoff")
     ap.add_argument("--kw-threshold-p", type=float, nargs="+",
@@ -871,6 +926,8 @@ def main():
         return run_kw_threshold(args) if rank == 0 else None
     if args.workload == "kw-chi":
         return run_kw_chi(args) if rank == 0 else None
+    if args.workload == "threshold":
+        return run_threshold(args) if rank == 0 else None
     if args.workload == "point":
         return run_point(args) if rank == 0 else None
 
