@@ -863,6 +863,19 @@ __device__ __forceinline__ void kw_part_la(const KwArgs& a, unsigned char* base,
     int expo = 0;
     long long rows_done = 0, cols_done = 0;
     int spare = WR;                         // the free band slot (warp 0)
+    // warp 0 reads the table entries of the row entering at step k during
+    // step k-1 (column, weight source, phase, extent), off its critical path
+    int fj = -1, fs = 0, fext = 0;
+    double2 fph = make_double2(0.0, 0.0);
+    auto prefetch = [&](int i) {
+        if (i < Nb) {
+            fj = a.ecol[i * kKwRowSlots + lane];
+            fs = a.esrc[i * kKwRowSlots + lane];
+            fph = a.eph[i * kKwRowSlots + lane];
+            fext = a.ext0[i];
+        }
+    };
+    if (warp == 0) prefetch(WR);
     if (warp == 0)
         kw_la_pivot<T, C>(a, A, mult, map, ext, act, ctl, 0, 0, 0, 0, lane, mant, expo, rows_done, cols_done);
     __syncthreads();
@@ -893,14 +906,17 @@ __device__ __forceinline__ void kw_part_la(const KwArgs& a, unsigned char* base,
             // k's); the pivot's slot becomes the spare
             const int rin = k + WR;
             if (rin < Nb) {
-                C v, v1;
-                const int j = kw_fetch<T, C>(a, wt, rin, lane, v, v1);
+                const int j = fj, ext_in = fext;
+                const T w = fs >= 0 ? wt[fs] : T(1);
+                const C v = C{-w * (T)fph.x, -w * (T)fph.y};
+                const C v1 = fs == -2 ? C{(T)fph.x, (T)fph.y} : v;
+                prefetch(rin + 1);
                 C* R = A + (size_t)spare * RS;
                 for (int i = lane; i < RS; i += 32) R[i] = zero;
                 __syncwarp();
                 kw_place_row<T, C>(a, R, rin, j, v, v1, lane);
                 if (lane == 0) {
-                    ext[spare] = a.ext0[rin];
+                    ext[spare] = ext_in;
                     map[kmod] = spare;
                 }
                 spare = ps;
