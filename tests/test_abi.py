@@ -117,3 +117,49 @@ def test_wilson_interval_matches_scipy():
         lo, hi = bench.wilson_interval(k, n)
         ref = stats.binomtest(k, n).proportion_ci(confidence_level=0.95, method="wilson")
         assert abs(lo - ref.low) < 1e-9 and abs(hi - ref.high) < 1e-9
+
+
+def test_kac_ward_host_side_argument_checks():
+    """mld_decode_xz refuses what the host can see before it touches a GPU:
+    an unknown precision, a negative batch, missing buffers; B = 0 is a no-op;
+    the flop counter of a code that never ran the path reads zero."""
+    import ctypes
+    lib = mld.load()
+    P = ctypes.c_void_p
+    OK, INVALID = 0, 1
+    fake = P(4096)            # aligned, never dereferenced on these paths
+    c5 = mld.Code(5)
+    xz = lib.mld_decode_xz
+    h = P(c5.handle)
+    assert xz(None, fake, fake, fake, 4, mld.MLD_FP32, fake, None, None) == INVALID
+    assert xz(h, fake, fake, fake, 4, 7, fake, None, None) == INVALID              # precision
+    assert xz(h, fake, fake, fake, 4, mld.MLD_MIXED_TF32, fake, None, None) == INVALID
+    assert xz(h, fake, fake, fake, -1, mld.MLD_FP32, fake, None, None) == INVALID
+    assert xz(h, fake, fake, fake, 0, mld.MLD_FP64, fake, None, None) == OK          # nothing to do
+    assert xz(h, None, fake, fake, 4, mld.MLD_FP32, fake, None, None) == INVALID     # no px
+    assert xz(h, fake, None, None, 4, mld.MLD_FP32, fake, None, None) == INVALID     # no syndromes
+    assert xz(h, fake, fake, fake, 4, mld.MLD_FP32, None, None, None) == INVALID     # no logP
+    assert c5.xz_executed_flops() == 0.0
+
+
+def test_threshold_crossings_and_leading_gap():
+    """The bench's curve-crossing interpolation and leading-class gap on
+    hand-made inputs: two lines crossing at 0.105, curves that never cross,
+    and a gap measured on the reference's leading class."""
+    torch = pytest.importorskip("torch")
+    import bench
+    ps = [0.09, 0.10, 0.11, 0.12]
+    ler = {}
+    for p in ps:
+        ler[(9, p)] = 0.5 * p + 0.05
+        ler[(13, p)] = 1.5 * p - 0.055          # equal at p = 0.105
+        ler[(17, p)] = 1.5 * p - 0.1            # below d = 13 everywhere
+    cross = bench._crossings(ler, [9, 13, 17], ps)
+    assert cross[0]["d"] == [9, 13] and abs(cross[0]["p_cross"] - 0.105) < 1e-12
+    assert cross[1]["p_cross"] is None
+    ref = torch.tensor([[-1.0, -2.0, -3.0, -4.0], [-5.0, -0.5, -9.0, -9.0]], dtype=torch.float64)
+    lp = ref.clone()
+    lp[0, 0] += 0.25          # the leading class of row 0
+    lp[1, 2] += 7.0           # a non-leading class of row 1: not counted
+    g = bench._lead_gap(lp, ref)
+    assert abs(g["max"] - 0.25) < 1e-12
