@@ -1,4 +1,6 @@
-"""Chunked decoding of a syndrome array larger than one launch, with resume.
+"""Chunked decoding of a syndrome array larger than one launch, with resume
+(the boundary-MPS decode, ``decode_to_files``, and the Kac-Ward decode under
+independent X/Z noise, ``decode_xz_to_files``).
 
 Decoding is stateless per syndrome, so a long job is a sequence of chunks. The
 results go to two ``.npy`` files opened as memory maps (``<prefix>.logp.npy``,
@@ -14,7 +16,7 @@ refused.
 The host-to-device copy of the next chunk overlaps the decode of the current
 one: the syndromes are staged in two pinned buffers and copied on a stream of
 their own, and the compute stream waits on the copy's event. Every chunk is one
-``mld_decode`` call through the C ABI.
+``mld_decode`` (or ``mld_decode_xz``) call through the C ABI.
 """
 from __future__ import annotations
 
@@ -24,7 +26,7 @@ import os
 
 import numpy as np
 
-from . import MLD_FP32, MLD_NOISE_DEPOL, MLD_NOISE_TABLE, MldError, mld_decode
+from . import MLD_FP32, MLD_NOISE_DEPOL, MLD_NOISE_TABLE, MldError, mld_decode, mld_decode_xz
 
 PROGRESS_VERSION = 1
 
@@ -91,8 +93,6 @@ def decode_to_files(code, noise, syndromes: np.ndarray, chi: int, prefix: str, c
     the same job is continued; otherwise the job starts over. ``on_chunk(start,
     count)`` is called after each chunk's results and progress are stored.
     Returns the two result memory maps."""
-    import torch
-
     syndromes = np.asarray(syndromes) if not isinstance(syndromes, np.memmap) else syndromes
     if syndromes.ndim != 2 or syndromes.dtype not in (np.uint64, np.int64):
         raise ValueError("syndromes must be a uint64 array [B][words]")
@@ -118,11 +118,64 @@ def decode_to_files(code, noise, syndromes: np.ndarray, chi: int, prefix: str, c
     if start0 >= B:
         return logp, am
 
+    def launch(dsyn, dnoise, n, out_lp, out_am, stream):
+        nz = dnoise if noise_mode == MLD_NOISE_DEPOL else noise
+        mld_decode(code.handle, nz, noise_mode, dsyn, n, chi, precision, out_lp, out_am, stream)
+
+    return _run_chunks(code, syndromes, words, chunk, prog, logp, am, launch,
+                       noise if noise_mode == MLD_NOISE_DEPOL else None, on_chunk)
+
+
+def decode_xz_to_files(code, px, pz, syndromes: np.ndarray, prefix: str, chunk: int = 1 << 18,
+                       precision: int = MLD_FP32, resume: bool = True, on_chunk=None):
+    """The same for the Kac-Ward decode under independent X/Z noise
+    (``mld_decode_xz``): px, pz are CUDA float32 tensors [n] (pz None for
+    bit-flip noise). The progress record also holds the method and a
+    fingerprint of the rates, so a job resumed with other rates is refused."""
+    syndromes = np.asarray(syndromes) if not isinstance(syndromes, np.memmap) else syndromes
+    if syndromes.ndim != 2 or syndromes.dtype not in (np.uint64, np.int64):
+        raise ValueError("syndromes must be a uint64 array [B][words]")
+    B, words = int(syndromes.shape[0]), int(syndromes.shape[1])
+    if words != code.words:
+        raise ValueError(f"{words} syndrome words per row, the code has {code.words}")
+    if chunk < 1:
+        raise ValueError("chunk must be positive")
+    h = hashlib.sha1(px.detach().cpu().numpy().tobytes())
+    if pz is not None:
+        h.update(pz.detach().cpu().numpy().tobytes())
+    config = {"method": "kac-ward", "d": int(code.d), "precision": int(precision), "bitflip": pz is None,
+              "rates_sha1": h.hexdigest(), "B": B, "words": words, "syndromes_sha1": fingerprint(syndromes)}
+    prog = Progress(prefix + ".progress.json", config)
+    have = resume and prog.load()
+    logp, am = _open_outputs(prefix, B, fresh=not have)
+    if not have:
+        prog.save(0)
+    if prog.done >= B:
+        return logp, am
+    pxc = px.contiguous()
+    pzc = None if pz is None else pz.contiguous()
+
+    def launch(dsyn, dnoise, n, out_lp, out_am, stream):
+        mld_decode_xz(code.handle, pxc, pzc, dsyn, n, precision, out_lp, out_am, stream)
+
+    return _run_chunks(code, syndromes, words, chunk, prog, logp, am, launch, None, on_chunk)
+
+
+def _run_chunks(code, syndromes, words, chunk, prog, logp, am, launch, per_syn, on_chunk):
+    """The chunk loop shared by both decoders: rows prog.done.. of
+    ``syndromes`` in chunks, the next chunk's host-to-device copy (and its
+    per-syndrome noise ``per_syn``, if any) overlapping the current decode,
+    ``launch(dsyn, dnoise, n, out_logP, out_argmax, stream)`` per chunk, the
+    results and the progress record stored after each."""
+    import torch
+
+    B = int(syndromes.shape[0])
+    start0 = prog.done
     dev = torch.device("cuda", torch.cuda.current_device())
     n_max = min(chunk, B - start0)
     stage = [torch.empty((n_max, words), dtype=torch.int64).pin_memory() for _ in range(2)]
     dsyn = [torch.empty((n_max, words), dtype=torch.int64, device=dev) for _ in range(2)]
-    if noise_mode == MLD_NOISE_DEPOL:
+    if per_syn is not None:
         nstage = [torch.empty((n_max,), dtype=torch.float32).pin_memory() for _ in range(2)]
         dnoise = [torch.empty((n_max,), dtype=torch.float32, device=dev) for _ in range(2)]
     out_lp = torch.empty((n_max, 4), dtype=torch.float64, device=dev)
@@ -139,11 +192,11 @@ def decode_to_files(code, noise, syndromes: np.ndarray, chi: int, prefix: str, c
         n = min(chunk, B - s0)
         j = k & 1
         stage[j][:n].numpy()[:] = syndromes[s0:s0 + n].view(np.int64)
-        if noise_mode == MLD_NOISE_DEPOL:
-            nstage[j][:n].numpy()[:] = noise[s0:s0 + n]
+        if per_syn is not None:
+            nstage[j][:n].numpy()[:] = per_syn[s0:s0 + n]
         with torch.cuda.stream(copy_s):
             dsyn[j][:n].copy_(stage[j][:n], non_blocking=True)
-            if noise_mode == MLD_NOISE_DEPOL:
+            if per_syn is not None:
                 dnoise[j][:n].copy_(nstage[j][:n], non_blocking=True)
             copied[j].record(copy_s)
 
@@ -152,8 +205,7 @@ def decode_to_files(code, noise, syndromes: np.ndarray, chi: int, prefix: str, c
         n = min(chunk, B - s0)
         j = k & 1
         comp_s.wait_event(copied[j])
-        nz = dnoise[j] if noise_mode == MLD_NOISE_DEPOL else noise
-        mld_decode(code.handle, nz, noise_mode, dsyn[j], n, chi, precision, out_lp, out_am, comp_s.cuda_stream)
+        launch(dsyn[j], dnoise[j] if per_syn is not None else None, n, out_lp, out_am, comp_s.cuda_stream)
         with torch.cuda.stream(comp_s):
             host_lp[:n].copy_(out_lp[:n], non_blocking=True)
             host_am[:n].copy_(out_am[:n], non_blocking=True)

@@ -101,3 +101,36 @@ def test_truncated_job_resumes_to_the_same_bits(mld, tmp_path):
     lp, _ = stream.decode_to_files(code, noise, syn, chi, prefix, chunk=chunk)
     np.testing.assert_array_equal(np.asarray(lp), ref.cpu().numpy())
     code.close()
+
+
+@pytest.mark.parametrize("bitflip", [False, True])
+def test_kac_ward_job_resumes_to_the_same_bits(mld, tmp_path, bitflip):
+    """decode_xz_to_files: a Kac-Ward job (d = 17, the block kernel)
+    interrupted after one chunk and resumed ends with the bits of one
+    decode_xz of the whole batch; a record made with other rates is refused."""
+    from paper_2605_17230_gb300 import stream
+    d, B, chunk = 17, 700, 256
+    n = d * d
+    px = torch.full((n,), 0.09, device="cuda")
+    pz = None if bitflip else torch.full((n,), 0.07, device="cuda")
+    pzn = np.zeros(n) if bitflip else np.full(n, 0.07)
+    table = synth.independent_xz(np.full(n, 0.09), pzn)
+    syn = synth.syndromes_of(d, synth.sample_errors(d, table, B, seed=17))
+    code = mld.Code(d)
+    ref, ram = code.decode_xz(px, pz, torch.tensor(syn.view(np.int64), device="cuda"))
+    torch.cuda.synchronize()
+    prefix = str(tmp_path / "kw")
+
+    def stop(start, count):
+        raise Stop()
+
+    with pytest.raises(Stop):
+        stream.decode_xz_to_files(code, px, pz, syn, prefix, chunk=chunk, on_chunk=stop)
+    with open(prefix + ".progress.json") as f:
+        assert json.load(f)["done"] == chunk
+    lp, am = stream.decode_xz_to_files(code, px, pz, syn, prefix, chunk=chunk)
+    np.testing.assert_array_equal(np.asarray(lp), ref.cpu().numpy())
+    np.testing.assert_array_equal(np.asarray(am), ram.cpu().numpy())
+    with pytest.raises(ValueError):
+        stream.decode_xz_to_files(code, px * 0.5, pz, syn, prefix, chunk=chunk)
+    code.close()
