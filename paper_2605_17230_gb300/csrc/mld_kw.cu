@@ -718,6 +718,9 @@ __host__ __device__ inline KwLayoutLA kw_layout_la(int WR, int RS, int n, size_t
 // exchange, the pivot's squared modulus into the mantissa, the multipliers
 // of the rows below (band rows, then the border rows at slots BR, BR+1) into
 // the lists of buffer b, column j of those rows zeroed, their extents grown.
+// Lane l holds the rows at offsets l, l + 32, l + 64 from j (slot and column
+// j entry) from the pivot search to the multipliers; the exchange swaps two
+// of them between lanes.
 template <typename T, typename C>
 __device__ __forceinline__ void kw_la_pivot(const KwArgs& a, C* A, C* mult, int* map, int* ext, int* act, int* ctl,
                                             int j, int colj, int kmodj, int b, int lane, T& mant, int& expo,
@@ -726,16 +729,26 @@ __device__ __forceinline__ void kw_la_pivot(const KwArgs& a, C* A, C* mult, int*
     const int WR = a.WR, RS = a.RS, Nb = a.Nb, BR = a.WR + 1;
     const C zero = C{T(0), T(0)};
     const int kend = (j + a.bl < Nb - 1) ? j + a.bl : Nb - 1;
+    const int span = kend - j;                       // offsets 0..span
+    int sl[kKwMaxChunks];
+    C vv[kKwMaxChunks];
     T best = T(-1);
     int boff = 0;
-    for (int off = lane; off <= kend - j; off += 32) {
-        int mp = kmodj + off;
-        if (mp >= WR) mp -= WR;
-        const C v = A[(size_t)map[mp] * RS + colj];
-        const T m2 = v.x * v.x + v.y * v.y;
-        if (m2 > best) {
-            best = m2;
-            boff = off;
+#pragma unroll
+    for (int c = 0; c < kKwMaxChunks; ++c) {
+        const int off = lane + 32 * c;
+        sl[c] = 0;
+        vv[c] = zero;
+        if (off <= span) {
+            int mp = kmodj + off;
+            if (mp >= WR) mp -= WR;
+            sl[c] = map[mp];
+            vv[c] = A[(size_t)sl[c] * RS + colj];
+            const T m2 = vv[c].x * vv[c].x + vv[c].y * vv[c].y;
+            if (m2 > best) {
+                best = m2;
+                boff = off;
+            }
         }
     }
 #pragma unroll
@@ -751,16 +764,33 @@ __device__ __forceinline__ void kw_la_pivot(const KwArgs& a, C* A, C* mult, int*
         if (lane == 0) ctl[b * 4 + 3] = 1;
         return;
     }
-    if (lane == 0 && boff != 0) {
-        int mp = kmodj + boff;
-        if (mp >= WR) mp -= WR;
-        const int t0 = map[kmodj];
-        map[kmodj] = map[mp];
-        map[mp] = t0;
+    if (boff != 0) {
+        // exchange offsets 0 and boff in the map and in the lanes' registers
+        const int lb = boff & 31, cb = boff >> 5;
+        const int s_b = __shfl_sync(FULL, cb == 0 ? sl[0] : (cb == 1 ? sl[1] : sl[2]), lb);
+        const C v_b = cb == 0 ? vv[0] : (cb == 1 ? vv[1] : vv[2]);
+        const T vbx = __shfl_sync(FULL, v_b.x, lb), vby = __shfl_sync(FULL, v_b.y, lb);
+        const int s_0 = __shfl_sync(FULL, sl[0], 0);
+        const T v0x = __shfl_sync(FULL, vv[0].x, 0), v0y = __shfl_sync(FULL, vv[0].y, 0);
+        if (lane == 0) {
+            int mp = kmodj + boff;
+            if (mp >= WR) mp -= WR;
+            map[kmodj] = s_b;
+            map[mp] = s_0;
+            sl[0] = s_b;
+            vv[0] = C{vbx, vby};
+        }
+        if (lane == lb) {
+#pragma unroll
+            for (int c = 0; c < kKwMaxChunks; ++c)
+                if (c == cb) {
+                    sl[c] = s_0;
+                    vv[c] = C{v0x, v0y};
+                }
+        }
     }
-    __syncwarp();
-    const int ps = map[kmodj];
-    const C u = A[(size_t)ps * RS + colj];
+    const int ps = __shfl_sync(FULL, sl[0], 0);
+    const C u = C{__shfl_sync(FULL, vv[0].x, 0), __shfl_sync(FULL, vv[0].y, 0)};
     const T inv2 = T(1) / best;
     const C inv = C{u.x * inv2, -u.y * inv2};
     if (lane == 0) {
@@ -770,30 +800,36 @@ __device__ __forceinline__ void kw_la_pivot(const KwArgs& a, C* A, C* mult, int*
         expo += e;
     }
     const int extp = ext[ps];
-    const int cnt1 = kend - j, ncand = cnt1 + 2;
     int* actb = act + b * (WR + 2);
     C* multb = mult + b * (WR + 2);
     int nact = 0;
-    for (int base_i = 0; base_i < ncand; base_i += 32) {
-        const int idx = base_i + lane;
-        int s = 0;
-        C v = zero;
-        if (idx < cnt1) {
-            int mp = kmodj + 1 + idx;
-            if (mp >= WR) mp -= WR;
-            s = map[mp];
-        } else if (idx < ncand) {
-            s = BR + (idx - cnt1);
-        }
-        if (idx < ncand) v = A[(size_t)s * RS + colj];
-        const bool nz = v.x != T(0) || v.y != T(0);
+    // band rows: offsets 1..span, from the registers
+#pragma unroll
+    for (int c = 0; c < kKwMaxChunks; ++c) {
+        const int off = lane + 32 * c;
+        const bool nz = off >= 1 && off <= span && (vv[c].x != T(0) || vv[c].y != T(0));
         const unsigned bal = __ballot_sync(FULL, nz);
         if (nz) {
             const int q = nact + __popc(bal & ((1u << lane) - 1u));
+            const int s = sl[c];
             actb[q] = s;
-            multb[q] = C{v.x * inv.x - v.y * inv.y, v.x * inv.y + v.y * inv.x};
+            multb[q] = C{vv[c].x * inv.x - vv[c].y * inv.y, vv[c].x * inv.y + vv[c].y * inv.x};
             A[(size_t)s * RS + colj] = zero;
-            if (s < BR && ext[s] < extp) ext[s] = extp;
+            if (ext[s] < extp) ext[s] = extp;
+        }
+        nact += __popc(bal);
+    }
+    // the border rows
+    {
+        C v = zero;
+        if (lane < 2) v = A[(size_t)(BR + lane) * RS + colj];
+        const bool nz = lane < 2 && (v.x != T(0) || v.y != T(0));
+        const unsigned bal = __ballot_sync(FULL, nz);
+        if (nz) {
+            const int q = nact + __popc(bal & ((1u << lane) - 1u));
+            actb[q] = BR + lane;
+            multb[q] = C{v.x * inv.x - v.y * inv.y, v.x * inv.y + v.y * inv.x};
+            A[(size_t)(BR + lane) * RS + colj] = zero;
         }
         nact += __popc(bal);
     }
