@@ -1167,7 +1167,7 @@ mld_status launch_kw_kernel(K kernel, int threads, size_t bytes, const KwArgs& a
 // One warp per syndrome while the window is small (up to 3 pivot-row columns
 // per lane, d <= 13: measured faster there, 1.77 M against 1.15 M syndromes/s
 // for four warps at d = 9); the look-ahead block of kKwWarps warps per
-// syndrome above (d = 17: 272 k against 148 k for one warp; d = 25: 65 k
+// syndrome above (d = 17: 277 k against 148 k for one warp; d = 25: 69 k
 // against 26 k).
 template <typename T, int NT>
 mld_status launch_kw_nt(const KwArgs& a, cudaStream_t s) {
