@@ -56,3 +56,33 @@ def test_fingerprint_tells_arrays_apart():
     c[-1, 1] ^= np.uint64(2)
     assert stream.fingerprint(a) != stream.fingerprint(c)
     assert stream.fingerprint(a[:9999]) != stream.fingerprint(a)
+
+
+def test_kac_ward_job_input_checks(tmp_path):
+    """decode_xz_to_files refuses malformed syndrome arrays and chunk sizes
+    before it touches the rates or a device."""
+    class FakeCode:
+        words, d = 2, 9
+    bad_rates = object()                   # never read on these paths
+    with pytest.raises(ValueError):
+        stream.decode_xz_to_files(FakeCode(), bad_rates, None, np.zeros((4, 3), np.uint64), str(tmp_path / "a"))
+    with pytest.raises(ValueError):
+        stream.decode_xz_to_files(FakeCode(), bad_rates, None, np.zeros((4,), np.uint64), str(tmp_path / "b"))
+    with pytest.raises(ValueError):
+        stream.decode_xz_to_files(FakeCode(), bad_rates, None, np.zeros((4, 2), np.float32), str(tmp_path / "c"))
+    with pytest.raises(ValueError):
+        stream.decode_xz_to_files(FakeCode(), bad_rates, None, np.zeros((4, 2), np.uint64), str(tmp_path / "d"),
+                                  chunk=0)
+    assert not os.path.exists(str(tmp_path / "d.progress.json"))
+
+
+def test_kac_ward_record_is_another_job(tmp_path):
+    """A record written for the boundary-MPS decoder is not a Kac-Ward job's:
+    the two configurations differ (method, rates), so resuming one as the
+    other is refused."""
+    path = str(tmp_path / "job.progress.json")
+    stream.Progress(path, _config()).save(100)
+    kw = {"method": "kac-ward", "d": 9, "precision": 0, "bitflip": False, "rates_sha1": "r", "B": 1000,
+          "words": 2, "syndromes_sha1": "x"}
+    with pytest.raises(ValueError):
+        stream.Progress(path, kw).load()
